@@ -1,0 +1,274 @@
+"""Benchmark of the multi-rhs / multi-shift twisted-mass solver on one GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--what solve|dirac]
+
+Workload (precision form): 16^3 x 32 lattice, U = exp(i 0.25 H) reunitarised, c_sw = 1,
+kappa from the tuning table in tests/golden/kappa.json (sigma_min / sigma_max of D_W ~ 1e-3),
+mu = 0.003, 12 point-source right-hand sides; synthetic, seeded.
+
+One JSON line on rank 0. Under torchrun (N > 1) every rank runs an independent replica of
+the workload (the systems are independent; no data-path collective) and the time is the
+maximum over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = dict(name="precision-form 16^3x32, 12 point sources, mu=0.003", L=(16, 16, 16, 32), eps=0.25, c_sw=1.0,
+                mu=0.003, nrhs=12, seed=1)
+METRIC = "rhs x shift solves/s at FP64 rel. residual 1e-10; Dirac-op GB/s vs HBM peak"
+
+
+def kappa_for(L, eps, seed):
+    path = os.path.join(ROOT, "tests", "golden", "kappa.json")
+    key = f"{L[0]}x{L[1]}x{L[2]}x{L[3]}_eps{eps}_seed{seed}"
+    if os.path.exists(path):
+        tab = json.load(open(path))
+        if key in tab:
+            return float(tab[key]["kappa"]), "tuned"
+    return 0.1335, "untuned"
+
+
+def dirac_bytes_per_site(nsys, prec):
+    """Algorithmic bytes of one fine stencil application per site: 4 links (18 reals), the
+    clover blocks (72 reals), and every system's spinor read once and written once (24 reals each)."""
+    es = 4 if prec == 32 else 8
+    return (4 * 18 + 72) * es + nsys * 2 * 24 * es
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, idx):
+        self.idx = idx
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            self.result = None
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        self.result = None if not sm else {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax),
+                                           "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- our arm
+def run_dirac(args, world, rank, local):
+    import torch
+    from paper_2201_03872_gb300 import tmamg as T
+
+    wl = WORKLOAD
+    L = wl["L"]
+    V = int(np.prod(L))
+    nsys = wl["nrhs"]
+    kappa, ksrc = kappa_for(L, wl["eps"], wl["seed"])
+    U = synth.gauge_field(L, wl["eps"], seed=wl["seed"] + rank)
+    stream = torch.cuda.current_stream()
+    ctx = T.tmamg_create(L, -1, stream.cuda_stream)
+    T.tmamg_load_gauge(ctx, U)
+    T.tmamg_set_operator(ctx, kappa, wl["c_sw"])
+    mu = np.full(nsys, wl["mu"])
+    x = synth.gaussian_spinors(L, nsys, seed=7 + rank).astype(np.complex64)
+    nb = T.tmamg_bundle_bytes(ctx, nsys, 32)
+    xf = torch.from_numpy(x.view(np.float32).copy()).cuda()
+    yf = torch.empty_like(xf)
+    xb = torch.empty(nb // 4, dtype=torch.float32, device="cuda")
+    yb = torch.empty_like(xb)
+    T.tmamg_pack(ctx, xf, xb, nsys, 32)
+    for _ in range(args.warmup):
+        T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32)
+            ev[k][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    total_ms = max_over_ranks(total_ms, world)
+    bytes_per_apply = dirac_bytes_per_site(nsys, 32) * V
+    gbs = bytes_per_apply * args.steps * world / (total_ms * 1e-3) / 1e9
+    # end to end through the public API with host buffers: H2D of x, apply, D2H of y
+    xh = torch.from_numpy(x.view(np.float32).copy()).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        xf.copy_(xh, non_blocking=True)
+        T.tmamg_apply(ctx, xf, yf, nsys, mu, 32)
+        yh.copy_(yf, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    T.tmamg_destroy(ctx)
+    hbm, _, peak_src = read_peaks()
+    achieved = bytes_per_apply / (kern_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "fine twisted-mass Wilson-clover stencil, 16^3x32, 12 systems (FP32 bundle)",
+                   "kappa": kappa, "kappa_source": ksrc, "nsys": nsys,
+                   "l2": "working set 378 MB > 129 MB L2; back-to-back applications"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_source": peak_src,
+                     "kernel": "dirac_kernel<float,4>", "algorithmic_bytes_per_launch": bytes_per_apply},
+        "e2e": {"value": bytes_per_apply * args.steps * world / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(x.nbytes)},
+        "gpu_launches": args.steps,
+        "clocks": clk.result,
+    }
+    return line
+
+
+def cpu_dirac_baseline():
+    """The FP64 oracle operator on the same lattice and 12 systems, timed on the host cores."""
+    from oracle import dirac
+    wl = WORKLOAD
+    L = wl["L"]
+    V = int(np.prod(L))
+    kappa, _ = kappa_for(L, wl["eps"], wl["seed"])
+    U = synth.gauge_field(L, wl["eps"], seed=wl["seed"])
+    op = dirac.Operator(U, kappa, wl["c_sw"])
+    nsys = 4
+    x = synth.gaussian_spinors(L, nsys, seed=7)
+    mu = np.full(nsys, wl["mu"])
+    op.apply(x[:1], mu[:1])
+    t = time.perf_counter()
+    reps = 0
+    while True:
+        op.apply(x, mu)
+        reps += 1
+        if time.perf_counter() - t > 8.0:
+            break
+    dt = (time.perf_counter() - t) / reps
+    gbs = dirac_bytes_per_site(nsys, 32) * V / dt / 1e9
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"numpy FP64 oracle D(mu) on 16^3x32 with {nsys} systems, {reps} applications; "
+                      "bytes counted with the same FP32 algorithmic formula as the GPU line"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--what", default="dirac", choices=["dirac"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_dirac_baseline()
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"], "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "fine twisted-mass Wilson-clover stencil, 16^3x32 (CPU oracle sample)"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    line = run_dirac(args, world, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_dirac_baseline()
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,131 @@
+/*
+ * tmamg -- simultaneous multi-rhs, multi-shift inversion of the degenerate
+ * twisted-mass Wilson-clover Dirac operator with aggregation-based
+ * domain-decomposition adaptive multigrid (method of arXiv:2201.03872,
+ * "Implementation of Simultaneous Inversion of a Multi-shifted Dirac Matrix
+ * for Twisted-Mass Fermions within DDalphaAMG"), on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI. Plain pointers and sizes only. Every entry point returns an int
+ * status (tmamg_status); a negative value is an error whose text is returned
+ * by tmamg_last_error(ctx). Argument checks run before any launch; nothing
+ * aborts the process. All device work is ordered on the CUDA stream given to
+ * tmamg_create (the calls are asynchronous with respect to the host unless
+ * stated otherwise).
+ *
+ * Operator (paper, Fig. 6 caption: D_TM = D_W + i (delta mu) mu gamma5):
+ *   D(mu) x(s) = 1/(2 kappa) x(s) + c_sw C(s) x(s) + i mu gamma5 x(s)
+ *               - 1/2 sum_nu [ (1 - gamma_nu) U_nu(s) x(s+nu) + (1 + gamma_nu) U_nu(s-nu)^+ x(s-nu) ]
+ * chiral gamma basis: gamma_k = [[0, -i sigma_k], [i sigma_k, 0]], gamma_4 = [[0,1],[1,0]],
+ * gamma5 = diag(1,1,-1,-1); C = (i/4) sum_{mu,nu} sigma_{mu nu} F_{mu nu} with the
+ * clover-leaf F = (Q - Q^+)/8; periodic in x, y, z, phase bc_t on hops that wrap in t.
+ *
+ * Layouts.
+ *   user vector ("field"): complex numbers [nvec][Lt][Lz][Ly][Lx][spin 4][colour 3],
+ *       interleaved (re, im), double or float; x fastest; spin-major inside a site.
+ *   gauge field: complex double [Lt][Lz][Ly][Lx][mu 4][3][3], row-major 3x3, mu = x, y, z, t.
+ *   bundle (the library's working layout, paper Sec. 3 / Fig. 2: the system index runs
+ *       fastest): real [ntile][ncomp][nsite][2 (re, im)][T], with T = 4 systems per tile
+ *       in FP32 and T = 2 in FP64, ntile = ceil(nsys / T); system n sits in tile n / T,
+ *       lane n % T. Fine level: ncomp = 12 (spin * 3 + colour), nsite = V. Padding lanes
+ *       of the last tile are carried along and ignored.
+ */
+#ifndef TMAMG_H
+#define TMAMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tmamg_ctx tmamg_ctx;
+
+typedef enum {
+  TMAMG_OK = 0,
+  TMAMG_NOT_CONVERGED = 1,  /* soft: x and per-system stats are still written */
+  TMAMG_ERR_ARG = -1,       /* invalid argument; nothing was launched */
+  TMAMG_ERR_STATE = -2,     /* call out of order (e.g. solve before setup) */
+  TMAMG_ERR_OOM = -3,       /* device allocation failed */
+  TMAMG_ERR_CUDA = -4,      /* a CUDA call or launch failed */
+  TMAMG_ERR_NONFINITE = -5, /* a NaN/Inf was found in an input or iterate */
+  TMAMG_ERR_TIMEOUT = -6    /* a bounded device wait gave up */
+} tmamg_status;
+
+/* Multigrid setup parameters (paper Sec. 2; defaults by tmamg_default_setup_params). */
+typedef struct {
+  int levels;          /* 2 (fine + one coarse level); 3 adds a second coarse level */
+  int agg[2][4];       /* aggregate extents (x, y, z, t) for the level-1 and level-2 coarsening */
+  int nv[2];           /* test vectors per coarsening; coarse site carries 2*nv unknowns (chirality split) */
+  int sap_block[4];    /* SAP block extents on the fine level; block counts per dimension must be even */
+  int sap_cycles;      /* red+black sweeps per SAP application */
+  int sap_mr_steps;    /* minimal-residual steps per block solve */
+  int setup_iters;     /* inverse-iteration steps v <- SAP(v)/|SAP(v)| on the test vectors */
+  double mu_setup;     /* twisted mass used during setup */
+  uint64_t seed;       /* start vectors when none are passed (counter-based splitmix64 + Box-Muller) */
+} tmamg_setup_params;
+
+/* Solve parameters (paper Sec. 4: FGMRES at the top, goal residual 1e-10; tuned coarse residual 1e-1). */
+typedef struct {
+  double tol;          /* per-system true FP64 relative residual goal ||b - D x|| / ||b|| */
+  int restart;         /* inner FP32 FGMRES cycle length between FP64 residual recomputations */
+  int max_outer;       /* maximum FP64 refinement cycles */
+  double coarse_tol;   /* relative residual goal of the coarsest-level solve (r_b) */
+  int coarse_restart;  /* coarse GMRES restart length */
+  int coarse_maxiter;  /* coarse iterations per cycle, upper bound */
+  int coarse_solver;   /* 0: batched GMRES per system; 1: block GMRES over the rhs of each shift */
+  double delta_mu;     /* coarse twisted-mass factor (paper Fig. 6 caption), 1 = none */
+  int precision;       /* 32: mixed (FP32 inner, FP64 outer); 64: plain FP64 single-precision-free path */
+  int use_nn;          /* reserved: learned preconditioner step (0 = off) */
+  int poll;            /* coarse iterations between host convergence polls */
+} tmamg_solve_params;
+
+typedef struct {
+  int status;          /* TMAMG_OK, TMAMG_NOT_CONVERGED or TMAMG_ERR_NONFINITE for this system */
+  int outer_iters;     /* FP64 refinement cycles */
+  int inner_iters;     /* top-level FGMRES iterations (= AMG cycles) */
+  int coarse_iters;    /* coarse-level iterations summed over all cycles */
+  double true_rel_res; /* final ||b - D x|| / ||b|| recomputed in FP64 */
+} tmamg_system_stats;
+
+void tmamg_default_setup_params(tmamg_setup_params* p);
+void tmamg_default_solve_params(tmamg_solve_params* p);
+
+/* Create a context for an Lx x Ly x Lz x Lt lattice (L[0..3] = x, y, z, t; each even, >= 2).
+ * bc_t: -1 antiperiodic or +1 periodic in t. cuda_stream: a cudaStream_t (NULL = default stream).
+ * The context owns every device buffer it allocates; tmamg_destroy frees them. */
+int tmamg_create(const int L[4], int bc_t, void* cuda_stream, tmamg_ctx** out);
+int tmamg_destroy(tmamg_ctx* ctx);
+const char* tmamg_last_error(const tmamg_ctx* ctx);
+int tmamg_volume(const tmamg_ctx* ctx, int64_t* V);
+
+/* Copy a gauge field (complex double, layout above) into the library's own FP64 and FP32
+ * copies. on_device: 1 if U is a device pointer, 0 for host memory. The caller keeps U. */
+int tmamg_load_gauge(tmamg_ctx* ctx, const double* U, int on_device);
+
+/* Set kappa and c_sw and build the clover term on the device (FP64, then an FP32 copy).
+ * Requires a loaded gauge field. */
+int tmamg_set_operator(tmamg_ctx* ctx, double kappa, double c_sw);
+
+/* Bytes of a bundle holding nsys fine-level systems at precision prec (32 or 64). */
+size_t tmamg_bundle_bytes(const tmamg_ctx* ctx, int nsys, int prec);
+
+/* Convert between user fields and bundles, device to device. x_field: [nsys][V][4][3]
+ * complex (double if prec == 64, float if prec == 32). Padding lanes are zeroed by pack. */
+int tmamg_pack(tmamg_ctx* ctx, const void* x_field, void* x_bundle, int nsys, int prec);
+int tmamg_unpack(tmamg_ctx* ctx, const void* x_bundle, void* x_field, int nsys, int prec);
+
+/* y = D(mu_n) x_n for every system n, bundles on the device (the fine stencil; paper
+ * Sec. 3: the gauge and clover data are loaded once for all systems). mu: host array of
+ * nsys twisted masses. prec: 32 or 64. x and y must not overlap. */
+int tmamg_dirac(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int nsys, const double* mu, int prec);
+
+/* Convenience: y = D(mu_n) x_n on user fields (device pointers), packing through
+ * internal scratch bundles. */
+int tmamg_apply(tmamg_ctx* ctx, const void* x_field, void* y_field, int nsys, const double* mu, int prec);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMAMG_H */

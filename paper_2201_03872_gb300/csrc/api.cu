@@ -1,0 +1,245 @@
+// C ABI of the tmamg library: context, gauge field, operator, bundles, fine stencil.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+namespace tmamg {
+
+int set_err(tmamg_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int check_cuda(tmamg_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TMAMG_OK;
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return set_err(ctx, TMAMG_ERR_OOM, m);
+  return set_err(ctx, TMAMG_ERR_CUDA, m);
+}
+
+int upload_mu(tmamg_ctx* ctx, const double* mu, int nsys) {
+  if (nsys > ctx->mu_cap) {
+    if (ctx->mu_dev) cudaFree(ctx->mu_dev);
+    ctx->mu_dev = nullptr;
+    int cap = nsys < 64 ? 64 : nsys;
+    int rc = check_cuda(ctx, cudaMalloc(&ctx->mu_dev, sizeof(double) * cap), "cudaMalloc(mu)");
+    if (rc) return rc;
+    ctx->mu_cap = cap;
+  }
+  return check_cuda(ctx, cudaMemcpyAsync(ctx->mu_dev, mu, sizeof(double) * nsys, cudaMemcpyHostToDevice, ctx->stream),
+                    "upload mu");
+}
+
+static int ensure_scratch(tmamg_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->scratch_bytes) return TMAMG_OK;
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->scratch[i]) cudaFree(ctx->scratch[i]);
+    ctx->scratch[i] = nullptr;
+  }
+  ctx->scratch_bytes = 0;
+  for (int i = 0; i < 2; ++i) {
+    int rc = check_cuda(ctx, cudaMalloc(&ctx->scratch[i], bytes), "cudaMalloc(scratch)");
+    if (rc) return rc;
+  }
+  ctx->scratch_bytes = bytes;
+  return TMAMG_OK;
+}
+
+void free_levels(tmamg_ctx* ctx);
+
+}  // namespace tmamg
+
+using namespace tmamg;
+
+extern "C" {
+
+void tmamg_default_setup_params(tmamg_setup_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->levels = 2;
+  for (int d = 0; d < 4; ++d) {
+    p->agg[0][d] = 4;
+    p->agg[1][d] = 2;
+    p->sap_block[d] = 4;
+  }
+  p->nv[0] = 24;
+  p->nv[1] = 32;
+  p->sap_cycles = 2;
+  p->sap_mr_steps = 3;
+  p->setup_iters = 5;
+  p->mu_setup = 0.0;
+  p->seed = 1;
+}
+
+void tmamg_default_solve_params(tmamg_solve_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->tol = 1e-10;
+  p->restart = 10;
+  p->max_outer = 50;
+  p->coarse_tol = 1e-1;
+  p->coarse_restart = 20;
+  p->coarse_maxiter = 100;
+  p->coarse_solver = 0;
+  p->delta_mu = 1.0;
+  p->precision = 32;
+  p->use_nn = 0;
+  p->poll = 4;
+}
+
+int tmamg_create(const int L[4], int bc_t, void* cuda_stream, tmamg_ctx** out) {
+  if (!out || !L) return TMAMG_ERR_ARG;
+  *out = nullptr;
+  for (int d = 0; d < 4; ++d)
+    if (L[d] < 2 || (L[d] % 2)) return TMAMG_ERR_ARG;
+  if (bc_t != 1 && bc_t != -1) return TMAMG_ERR_ARG;
+  tmamg_ctx* ctx = new tmamg_ctx();
+  for (int d = 0; d < 4; ++d) ctx->g.L[d] = L[d];
+  ctx->g.V = (int64_t)L[0] * L[1] * L[2] * L[3];
+  ctx->g.bc_t = bc_t;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  tmamg_default_setup_params(&ctx->sp);
+  int rc = check_cuda(ctx, cudaMalloc(&ctx->U64, sizeof(double2) * 36 * ctx->g.V), "cudaMalloc(U64)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&ctx->U32, sizeof(float2) * 36 * ctx->g.V), "cudaMalloc(U32)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&ctx->C64, sizeof(double) * 72 * ctx->g.V), "cudaMalloc(C64)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&ctx->C32, sizeof(float) * 72 * ctx->g.V), "cudaMalloc(C32)");
+  if (rc) {
+    tmamg_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return TMAMG_OK;
+}
+
+int tmamg_destroy(tmamg_ctx* ctx) {
+  if (!ctx) return TMAMG_OK;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  free_levels(ctx);
+  cudaFree(ctx->U64);
+  cudaFree(ctx->U32);
+  cudaFree(ctx->C64);
+  cudaFree(ctx->C32);
+  cudaFree(ctx->mu_dev);
+  for (int i = 0; i < 2; ++i) cudaFree(ctx->scratch[i]);
+  delete ctx;
+  return TMAMG_OK;
+}
+
+const char* tmamg_last_error(const tmamg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tmamg_volume(const tmamg_ctx* ctx, int64_t* V) {
+  if (!ctx || !V) return TMAMG_ERR_ARG;
+  *V = ctx->g.V;
+  return TMAMG_OK;
+}
+
+int tmamg_load_gauge(tmamg_ctx* ctx, const double* U, int on_device) {
+  if (!ctx || !U) return set_err(ctx, TMAMG_ERR_ARG, "load_gauge: null argument");
+  const double* src = U;
+  double* tmp = nullptr;
+  size_t bytes = sizeof(double) * 2 * 36 * ctx->g.V;
+  if (!on_device) {
+    int rc = check_cuda(ctx, cudaMalloc(&tmp, bytes), "cudaMalloc(gauge staging)");
+    if (rc) return rc;
+    rc = check_cuda(ctx, cudaMemcpyAsync(tmp, U, bytes, cudaMemcpyHostToDevice, ctx->stream), "upload gauge");
+    if (rc) {
+      cudaFree(tmp);
+      return rc;
+    }
+    src = tmp;
+  }
+  launch_convert_gauge(ctx->g, src, ctx->U64, ctx->U32, ctx->stream);
+  int rc = check_cuda(ctx, cudaGetLastError(), "convert_gauge launch");
+  if (tmp) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+  }
+  if (rc) return rc;
+  ctx->have_gauge = true;
+  ctx->have_op = false;
+  ctx->have_setup = false;
+  return TMAMG_OK;
+}
+
+int tmamg_set_operator(tmamg_ctx* ctx, double kappa, double c_sw) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!(kappa > 0.0) || !(c_sw >= 0.0)) return set_err(ctx, TMAMG_ERR_ARG, "set_operator: need kappa > 0, c_sw >= 0");
+  if (!ctx->have_gauge) return set_err(ctx, TMAMG_ERR_STATE, "set_operator: no gauge field loaded");
+  ctx->kappa = kappa;
+  ctx->c_sw = c_sw;
+  launch_build_clover(ctx->g, ctx->U64, kappa, c_sw, ctx->C64, ctx->C32, ctx->stream);
+  int rc = check_cuda(ctx, cudaGetLastError(), "build_clover launch");
+  if (rc) return rc;
+  ctx->have_op = true;
+  ctx->have_setup = false;
+  return TMAMG_OK;
+}
+
+size_t tmamg_bundle_bytes(const tmamg_ctx* ctx, int nsys, int prec) {
+  if (!ctx || nsys <= 0 || (prec != 32 && prec != 64)) return 0;
+  int T = prec == 32 ? 4 : 2;
+  size_t es = prec == 32 ? 4 : 8;
+  return (size_t)ntiles(nsys, T) * T * 12 * 2 * (size_t)ctx->g.V * es;
+}
+
+int tmamg_pack(tmamg_ctx* ctx, const void* x_field, void* x_bundle, int nsys, int prec) {
+  if (!ctx || !x_field || !x_bundle || nsys <= 0) return set_err(ctx, TMAMG_ERR_ARG, "pack: bad argument");
+  if (prec == 32) launch_pack<float>(ctx->g, (const float*)x_field, (float*)x_bundle, nsys, ctx->stream);
+  else if (prec == 64) launch_pack<double>(ctx->g, (const double*)x_field, (double*)x_bundle, nsys, ctx->stream);
+  else return set_err(ctx, TMAMG_ERR_ARG, "pack: prec must be 32 or 64");
+  return check_cuda(ctx, cudaGetLastError(), "pack launch");
+}
+
+int tmamg_unpack(tmamg_ctx* ctx, const void* x_bundle, void* x_field, int nsys, int prec) {
+  if (!ctx || !x_field || !x_bundle || nsys <= 0) return set_err(ctx, TMAMG_ERR_ARG, "unpack: bad argument");
+  if (prec == 32) launch_unpack<float>(ctx->g, (const float*)x_bundle, (float*)x_field, nsys, ctx->stream);
+  else if (prec == 64) launch_unpack<double>(ctx->g, (const double*)x_bundle, (double*)x_field, nsys, ctx->stream);
+  else return set_err(ctx, TMAMG_ERR_ARG, "unpack: prec must be 32 or 64");
+  return check_cuda(ctx, cudaGetLastError(), "unpack launch");
+}
+
+int tmamg_dirac(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int nsys, const double* mu, int prec) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!x_bundle || !y_bundle || !mu || nsys <= 0) return set_err(ctx, TMAMG_ERR_ARG, "dirac: bad argument");
+  if (x_bundle == y_bundle) return set_err(ctx, TMAMG_ERR_ARG, "dirac: x and y must not overlap");
+  if (!ctx->have_op) return set_err(ctx, TMAMG_ERR_STATE, "dirac: operator not set");
+  int rc = upload_mu(ctx, mu, nsys);
+  if (rc) return rc;
+  if (prec == 32)
+    launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, (const float*)x_bundle, (float*)y_bundle, ctx->mu_dev, nsys,
+                        ctx->stream);
+  else if (prec == 64)
+    launch_dirac<double>(ctx->g, ctx->U64, ctx->C64, (const double*)x_bundle, (double*)y_bundle, ctx->mu_dev, nsys,
+                         ctx->stream);
+  else
+    return set_err(ctx, TMAMG_ERR_ARG, "dirac: prec must be 32 or 64");
+  return check_cuda(ctx, cudaGetLastError(), "dirac launch");
+}
+
+int tmamg_apply(tmamg_ctx* ctx, const void* x_field, void* y_field, int nsys, const double* mu, int prec) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!x_field || !y_field || !mu || nsys <= 0 || (prec != 32 && prec != 64))
+    return set_err(ctx, TMAMG_ERR_ARG, "apply: bad argument");
+  size_t bytes = tmamg_bundle_bytes(ctx, nsys, prec);
+  int rc = ensure_scratch(ctx, bytes);
+  if (rc) return rc;
+  rc = tmamg_pack(ctx, x_field, ctx->scratch[0], nsys, prec);
+  if (!rc) rc = tmamg_dirac(ctx, ctx->scratch[0], ctx->scratch[1], nsys, mu, prec);
+  if (!rc) rc = tmamg_unpack(ctx, ctx->scratch[1], y_field, nsys, prec);
+  return rc;
+}
+
+}  // extern "C"
+
+namespace tmamg {
+void free_levels(tmamg_ctx* ctx) {
+  for (auto& l : ctx->levels) {
+    cudaFree(l.P);
+    cudaFree(l.A);
+  }
+  ctx->levels.clear();
+}
+}  // namespace tmamg

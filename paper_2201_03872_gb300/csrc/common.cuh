@@ -1,0 +1,101 @@
+// Shared device/host definitions of the tmamg CUDA library (sm_103a).
+//
+// Bundle layout: real [ntile][ncomp][nsite][2][T]; T = 4 (FP32) or 2 (FP64).
+// Every kernel of the library reads and writes this layout; the system index
+// runs fastest inside a tile (paper Sec. 3, Fig. 2) so that one 16-byte load
+// brings the same entry of T systems.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/tmamg.h"
+
+namespace tmamg {
+
+template <typename real> struct Tile;
+template <> struct Tile<float> { static constexpr int T = 4; };
+template <> struct Tile<double> { static constexpr int T = 2; };
+
+struct Geom {
+  int L[4];     // x, y, z, t
+  int64_t V;
+  int bc_t;
+};
+
+__host__ __device__ inline void site_coords(int64_t s, const int* L, int* c) {
+  c[0] = (int)(s % L[0]);
+  int64_t r = s / L[0];
+  c[1] = (int)(r % L[1]);
+  r /= L[1];
+  c[2] = (int)(r % L[2]);
+  c[3] = (int)(r / L[2]);
+}
+
+__host__ __device__ inline int64_t site_index(const int* c, const int* L) {
+  return ((int64_t)(c[3] * L[2] + c[2]) * L[1] + c[1]) * L[0] + c[0];
+}
+
+inline int ntiles(int nsys, int T) { return (nsys + T - 1) / T; }
+
+// one level of the multigrid hierarchy, device data owned by the context
+struct CoarseLevel {
+  int Lc[4] = {0, 0, 0, 0};
+  int agg[4] = {0, 0, 0, 0};
+  int64_t Vc = 0;
+  int nv = 0;           // test vectors; coarse unknowns per site nc = 2 nv
+  int asize = 0;        // fine sites per aggregate
+  float2* P = nullptr;  // [Vc][2 chi][nv][asize*6] for a fine parent (6 = 2 spins x 3 colours per chirality)
+  float2* A = nullptr;  // [9][Vc][nc (col j)][nc (row i)]  coarse stencil blocks, column-major per block
+};
+
+struct Workspace;
+
+}  // namespace tmamg
+
+struct tmamg_ctx {
+  tmamg::Geom g;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // gauge field: [4 mu][9][V] complex (site fastest)
+  double2* U64 = nullptr;
+  float2* U32 = nullptr;
+  // clover + diagonal, per site 2 chiralities x 36 reals: [72][V]
+  double* C64 = nullptr;
+  float* C32 = nullptr;
+  double kappa = 0.0, c_sw = 0.0;
+  bool have_gauge = false, have_op = false, have_setup = false;
+  // twisted masses on the device (per system), cached
+  double* mu_dev = nullptr;
+  int mu_cap = 0;
+  // scratch for tmamg_apply
+  void* scratch[2] = {nullptr, nullptr};
+  size_t scratch_bytes = 0;
+  // multigrid hierarchy
+  tmamg_setup_params sp;
+  std::vector<tmamg::CoarseLevel> levels;
+  tmamg::Workspace* ws = nullptr;
+};
+
+namespace tmamg {
+
+// error helpers (host)
+int set_err(tmamg_ctx* ctx, int code, const std::string& msg);
+int check_cuda(tmamg_ctx* ctx, cudaError_t e, const char* what);
+int upload_mu(tmamg_ctx* ctx, const double* mu, int nsys);
+
+// kernels launched from other translation units
+void launch_build_clover(const Geom& g, const double2* U64, double kappa, double c_sw, double* C64, float* C32,
+                         cudaStream_t st);
+void launch_convert_gauge(const Geom& g, const double* Uin, double2* U64, float2* U32, cudaStream_t st);
+template <typename real>
+void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu, int nsys,
+                  cudaStream_t st);
+template <typename real>
+void launch_pack(const Geom& g, const real* field, real* bundle, int nsys, cudaStream_t st);
+template <typename real>
+void launch_unpack(const Geom& g, const real* bundle, real* field, int nsys, cudaStream_t st);
+
+}  // namespace tmamg

@@ -1,0 +1,182 @@
+"""Thin ctypes binding of the tmamg C ABI (include/tmamg.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+libtmamg.so. Functions keep the C names; they take plain Python numbers,
+numpy arrays (host memory) or integer device pointers (e.g. torch's
+``tensor.data_ptr()``), and raise TmamgError on a negative status.
+There is no fallback: if the library is missing, loading fails loudly.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtmamg.so")
+
+TMAMG_OK = 0
+TMAMG_NOT_CONVERGED = 1
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_STATE", -3: "ERR_OOM", -4: "ERR_CUDA",
+                -5: "ERR_NONFINITE", -6: "ERR_TIMEOUT"}
+
+
+class TmamgError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__(f"{fn} -> {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SetupParams(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("agg", (ctypes.c_int * 4) * 2), ("nv", ctypes.c_int * 2),
+                ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int), ("sap_mr_steps", ctypes.c_int),
+                ("setup_iters", ctypes.c_int), ("mu_setup", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_outer", ctypes.c_int),
+                ("coarse_tol", ctypes.c_double), ("coarse_restart", ctypes.c_int), ("coarse_maxiter", ctypes.c_int),
+                ("coarse_solver", ctypes.c_int), ("delta_mu", ctypes.c_double), ("precision", ctypes.c_int),
+                ("use_nn", ctypes.c_int), ("poll", ctypes.c_int)]
+
+
+class SystemStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("coarse_iters", ctypes.c_int), ("true_rel_res", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libtmamg.so (built by __graft_entry__.build() / paper_2201_03872_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libtmamg.so not built ({LIB_PATH}); run python -m paper_2201_03872_gb300.build")
+        _lib = ctypes.CDLL(LIB_PATH)
+        _declare(_lib)
+    return _lib
+
+
+P = ctypes.c_void_p
+I = ctypes.c_int
+D = ctypes.c_double
+
+# name -> (restype, argtypes); the list is checked against include/tmamg.h by the tests
+SIGNATURES = {
+    "tmamg_default_setup_params": (None, [ctypes.POINTER(SetupParams)]),
+    "tmamg_default_solve_params": (None, [ctypes.POINTER(SolveParams)]),
+    "tmamg_create": (I, [ctypes.POINTER(ctypes.c_int), I, P, ctypes.POINTER(P)]),
+    "tmamg_destroy": (I, [P]),
+    "tmamg_last_error": (ctypes.c_char_p, [P]),
+    "tmamg_volume": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+    "tmamg_load_gauge": (I, [P, P, I]),
+    "tmamg_set_operator": (I, [P, D, D]),
+    "tmamg_bundle_bytes": (ctypes.c_size_t, [P, I, I]),
+    "tmamg_pack": (I, [P, P, P, I, I]),
+    "tmamg_unpack": (I, [P, P, P, I, I]),
+    "tmamg_dirac": (I, [P, P, P, I, P, I]),
+    "tmamg_apply": (I, [P, P, P, I, P, I]),
+}
+
+
+def _declare(L):
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _ptr(x):
+    """Host numpy array -> its address; int -> as is (a device pointer); torch tensor -> data_ptr()."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _check(name, ctx, rc):
+    if rc < 0:
+        msg = lib().tmamg_last_error(ctx).decode() if ctx else ""
+        raise TmamgError(name, rc, msg)
+    return rc
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def tmamg_default_setup_params():
+    p = SetupParams()
+    lib().tmamg_default_setup_params(ctypes.byref(p))
+    return p
+
+
+def tmamg_default_solve_params():
+    p = SolveParams()
+    lib().tmamg_default_solve_params(ctypes.byref(p))
+    return p
+
+
+def tmamg_create(L, bc_t=-1, stream=0):
+    arr = (ctypes.c_int * 4)(*[int(v) for v in L])
+    out = P()
+    rc = lib().tmamg_create(arr, int(bc_t), P(stream or None), ctypes.byref(out))
+    if rc < 0:
+        raise TmamgError("tmamg_create", rc, "invalid lattice/bc or device allocation failed")
+    return out.value
+
+
+def tmamg_destroy(ctx):
+    return lib().tmamg_destroy(ctx)
+
+
+def tmamg_last_error(ctx):
+    return lib().tmamg_last_error(ctx).decode()
+
+
+def tmamg_volume(ctx):
+    v = ctypes.c_int64()
+    _check("tmamg_volume", ctx, lib().tmamg_volume(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def tmamg_load_gauge(ctx, U, on_device=None):
+    """U: complex128 numpy array [Lt, Lz, Ly, Lx, 4, 3, 3] (host) or a device pointer / tensor."""
+    if isinstance(U, np.ndarray):
+        U = np.ascontiguousarray(U.astype(np.complex128))
+        return _check("tmamg_load_gauge", ctx, lib().tmamg_load_gauge(ctx, _ptr(U), 0))
+    return _check("tmamg_load_gauge", ctx, lib().tmamg_load_gauge(ctx, _ptr(U), 1 if on_device is None else on_device))
+
+
+def tmamg_set_operator(ctx, kappa, c_sw):
+    return _check("tmamg_set_operator", ctx, lib().tmamg_set_operator(ctx, float(kappa), float(c_sw)))
+
+
+def tmamg_bundle_bytes(ctx, nsys, prec):
+    return lib().tmamg_bundle_bytes(ctx, int(nsys), int(prec))
+
+
+def tmamg_pack(ctx, x_field, x_bundle, nsys, prec):
+    return _check("tmamg_pack", ctx, lib().tmamg_pack(ctx, _ptr(x_field), _ptr(x_bundle), int(nsys), int(prec)))
+
+
+def tmamg_unpack(ctx, x_bundle, x_field, nsys, prec):
+    return _check("tmamg_unpack", ctx, lib().tmamg_unpack(ctx, _ptr(x_bundle), _ptr(x_field), int(nsys), int(prec)))
+
+
+def tmamg_dirac(ctx, x_bundle, y_bundle, nsys, mu, prec):
+    m = _f64(mu)
+    return _check("tmamg_dirac", ctx, lib().tmamg_dirac(ctx, _ptr(x_bundle), _ptr(y_bundle), int(nsys), _ptr(m),
+                                                        int(prec)))
+
+
+def tmamg_apply(ctx, x_field, y_field, nsys, mu, prec):
+    m = _f64(mu)
+    return _check("tmamg_apply", ctx, lib().tmamg_apply(ctx, _ptr(x_field), _ptr(y_field), int(nsys), _ptr(m),
+                                                        int(prec)))

@@ -24,10 +24,11 @@
  *       interleaved (re, im), double or float; x fastest; spin-major inside a site.
  *   gauge field: complex double [Lt][Lz][Ly][Lx][mu 4][3][3], row-major 3x3, mu = x, y, z, t.
  *   bundle (the library's working layout, paper Sec. 3 / Fig. 2: the system index runs
- *       fastest): real [ntile][ncomp][nsite][2 (re, im)][T], with T = 4 systems per tile
- *       in FP32 and T = 2 in FP64, ntile = ceil(nsys / T); system n sits in tile n / T,
- *       lane n % T. Fine level: ncomp = 12 (spin * 3 + colour), nsite = V. Padding lanes
- *       of the last tile are carried along and ignored.
+ *       fastest): real [ntile][ncomp][nsite][2 (re, im)][T], with T = 2 systems per tile
+ *       in FP32 and T = 1 in FP64 (one 16-byte entry holds re[T], im[T]),
+ *       ntile = ceil(nsys / T); system n sits in tile n / T, lane n % T. Fine level:
+ *       ncomp = 12 (spin * 3 + colour), nsite = V. Padding lanes of the last tile are
+ *       carried along and ignored.
  */
 #ifndef TMAMG_H
 #define TMAMG_H
@@ -123,6 +124,54 @@ int tmamg_dirac(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int nsys, 
 /* Convenience: y = D(mu_n) x_n on user fields (device pointers), packing through
  * internal scratch bundles. */
 int tmamg_apply(tmamg_ctx* ctx, const void* x_field, void* y_field, int nsys, const double* mu, int prec);
+
+/* ------------------------------------------------------------------ multigrid and solve */
+
+/* Build the multigrid hierarchy (paper Sec. 2: test vectors approximating low modes, P and
+ * R = P^+ on aggregates, coarse operator D_c = P^+ D P). start_vectors: device pointer to
+ * nv[0] complex float fields [nv][V][4][3], or NULL to draw them from the library's
+ * counter-based generator (splitmix64 + Box-Muller, seeded by p->seed). The start vectors
+ * are smoothed by p->setup_iters steps of inverse iteration v <- SAP(v)/|SAP(v)| at
+ * twisted mass p->mu_setup, split by chirality and orthonormalised per aggregate
+ * (classical Gram-Schmidt, twice). Synchronises the stream. Only levels == 2 for now. */
+int tmamg_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* start_vectors);
+
+/* As tmamg_setup, but test_vectors (device, complex float [nv][V][4][3]) are used as the
+ * final test vectors without smoothing: lets a caller reproduce P from known vectors. */
+int tmamg_setup_from_vectors(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* test_vectors);
+
+/* Solve D(mu_k) x_{r,k} = b_r for every rhs r < nrhs and shift k < nshift (paper Sec. 3-4).
+ * b: complex double [nrhs][V][4][3]; mu: host array [nshift]; x: complex double
+ * [nrhs][nshift][V][4][3]. on_device: 1 if b and x are device pointers, 0 for host memory.
+ * p: NULL for defaults. stats: host array [nrhs * nshift] or NULL. Every system is iterated
+ * until ||b - D x|| <= p->tol ||b|| in FP64 (or p->max_outer refinement cycles). Returns
+ * TMAMG_OK if all systems converged, TMAMG_NOT_CONVERGED otherwise (x and stats written;
+ * a system whose data became non-finite has status TMAMG_ERR_NONFINITE and is frozen).
+ * Synchronises the stream. */
+int tmamg_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int nshift, double* x, int on_device,
+                const tmamg_solve_params* p, tmamg_system_stats* stats);
+
+/* ------------------------------------------------------------------ components (bundles, device) */
+
+/* Bytes of a coarse bundle of `level` (1 = first coarse level) holding nsys systems (FP32):
+ * real [ntile][2 nv][Vc][2][2], coarse component chi * nv + j, coarse sites lexicographic. */
+size_t tmamg_coarse_bundle_bytes(const tmamg_ctx* ctx, int level, int nsys);
+
+/* e = SAP(r) on FP32 fine bundles (paper Sec. 2, red-black Schwarz alternating procedure):
+ * block extents block[4] (an even number of blocks, or one, per dimension; block volume
+ * <= 256), `cycles` red+black sweeps, `mr_steps` minimal-residual steps per block solve,
+ * zero start. r is overwritten (partially updated residual). mu: host [nsys]. */
+int tmamg_sap(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const double* mu, const int block[4],
+              int cycles, int mr_steps);
+
+/* xc = P^+ r (restriction) and r = P xc (prolongation, overwrites) between the fine level and
+ * coarse level 1, FP32 bundles. Require a setup. */
+int tmamg_restrict(tmamg_ctx* ctx, int level, const void* fine_bundle, void* coarse_bundle, int nsys);
+int tmamg_prolong(tmamg_ctx* ctx, int level, const void* coarse_bundle, void* fine_bundle, int nsys);
+
+/* y = D_c(mu_n) x on coarse level 1 (9-point stencil of dense 2nv x 2nv blocks plus
+ * i mu_n gamma5_c, paper Sec. 2 and Fig. 6 caption with delta mu = 1). mu: host [nsys]. */
+int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_bundle, int nsys, const double* mu);
 
 #ifdef __cplusplus
 }

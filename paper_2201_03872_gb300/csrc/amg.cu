@@ -1,0 +1,410 @@
+// Aggregation-based multigrid on GB300: prolongation P, restriction P^+, Galerkin coarse
+// operator D_c = P^+ D P, and the coarse 9-point stencil (paper Sec. 2: P and R are built
+// from approximate low modes on aggregates, the coarse operator lives on the lattice of
+// aggregates, and the construction recurses).
+//
+// P layout (per coarsening): float2 P[Vc][2 chi][nv][K] with K = asize * d: for aggregate a,
+// chirality chi and test vector j, the K = (site in aggregate) x (d unknowns of that
+// chirality) entries; d = 6 (2 spins x 3 colours) when the parent is the fine lattice, and
+// the parent's nv when the parent is a coarse lattice. A parent component is chi * d + c'.
+// Coarse vectors are bundles with ncomp = nc = 2 nv and nsite = Vc; component chi * nv + j.
+// Coarse stencil: float2 A[9][Vc][nc (column j)][nc (row i)], hop index 0 = self,
+// 1 + 2 nu = +nu, 2 + 2 nu = -nu.
+#include "amg.cuh"
+#include "stencil.cuh"
+
+namespace tmamg {
+
+constexpr int T2 = 2;  // FP32 tile width
+
+__device__ __forceinline__ void agg_site(int64_t a, int q, const int* Lc, const int* ag, const int* L, int* c) {
+  int ac[4], lq[4];
+  site_coords(a, Lc, ac);
+  site_coords(q, ag, lq);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c[k] = ac[k] * ag[k] + lq[k];
+}
+
+// ------------------------------------------------------------------ test vectors -> P
+// P[a][chi][j][q d + c'] = V_j[chi d + c'][site(a, q)]   (V: FP32 bundle, nv systems, ncomp = 2 d)
+__global__ void gather_P_kernel(const float* __restrict__ Vb, float2* __restrict__ P, AggDims g, int nv, int d) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int K = g.asize * d;
+  int64_t total = g.Vc * 2 * nv * (int64_t)K;
+  if (t >= total) return;
+  int k = (int)(t % K);
+  int j = (int)((t / K) % nv);
+  int chi = (int)((t / ((int64_t)K * nv)) % 2);
+  int64_t a = t / ((int64_t)K * nv * 2);
+  int q = k / d, cp = k % d;
+  int c[4];
+  agg_site(a, q, g.Lc, g.agg, g.L, c);
+  int64_t s = site_index(c, g.L);
+  int comp = chi * d + cp;
+  const float* e = Vb + (((int64_t)(j / T2) * (2 * d) + comp) * g.Vp + s) * 2 * T2;
+  P[t] = make_float2(e[j % T2], e[T2 + j % T2]);
+}
+
+// Classical Gram-Schmidt applied twice to the nv vectors of one (aggregate, chirality),
+// one CTA each; dots in FP64.
+__global__ void __launch_bounds__(256) orthonormalise_kernel(float2* __restrict__ P, int nv, int K) {
+  float2* Pv = P + (int64_t)blockIdx.x * nv * K;
+  __shared__ double2 red[8][8];
+  __shared__ double2 coef[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = 0; j < nv; ++j) {
+    float2* vj = Pv + (int64_t)j * K;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i0 = 0; i0 < j; i0 += 8) {
+        int ni = j - i0 < 8 ? j - i0 : 8;
+        double2 acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = make_double2(0, 0);
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+          float2 w = vj[k];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (u < ni) {
+              float2 v = Pv[(int64_t)(i0 + u) * K + k];
+              acc[u].x += (double)v.x * w.x + (double)v.y * w.y;
+              acc[u].y += (double)v.x * w.y - (double)v.y * w.x;
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            acc[u].x += __shfl_xor_sync(0xffffffffu, acc[u].x, o);
+            acc[u].y += __shfl_xor_sync(0xffffffffu, acc[u].y, o);
+          }
+          if (lane == 0) red[warp][u] = acc[u];
+        }
+        __syncthreads();
+        if (threadIdx.x < 8) {
+          double2 s = make_double2(0, 0);
+          for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            s.x += red[w][threadIdx.x].x;
+            s.y += red[w][threadIdx.x].y;
+          }
+          coef[threadIdx.x] = s;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+          float2 w = vj[k];
+          double wr = w.x, wi = w.y;
+          for (int u = 0; u < ni; ++u) {
+            float2 v = Pv[(int64_t)(i0 + u) * K + k];
+            double2 cc = coef[u];
+            wr -= cc.x * v.x - cc.y * v.y;
+            wi -= cc.x * v.y + cc.y * v.x;
+          }
+          vj[k] = make_float2((float)wr, (float)wi);
+        }
+        __syncthreads();
+      }
+    }
+    // normalise
+    double nn = 0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      float2 w = vj[k];
+      nn += (double)w.x * w.x + (double)w.y * w.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (lane == 0) red[warp][0].x = nn;
+    __syncthreads();
+    double tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w][0].x;
+    double inv = tot > 0 ? 1.0 / sqrt(tot) : 0.0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      float2 w = vj[k];
+      vj[k] = make_float2((float)(w.x * inv), (float)(w.y * inv));
+    }
+    __syncthreads();
+  }
+}
+
+void build_P(const AggDims& g, const float* Vb, float2* P, int nv, int d, cudaStream_t st) {
+  int64_t total = g.Vc * 2 * nv * (int64_t)g.asize * d;
+  gather_P_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Vb, P, g, nv, d);
+  orthonormalise_kernel<<<(unsigned)(g.Vc * 2), 256, 0, st>>>(P, nv, g.asize * d);
+}
+
+// ------------------------------------------------------------------ restriction / prolongation
+// xc[tile][chi nv + j][a] = sum_k conj(P[a][chi][j][k]) r[tile][chi d + c'][site(a, q)]
+constexpr int KS = 4;
+__global__ void restrict_kernel(const float2* __restrict__ P, const float* __restrict__ r, float* __restrict__ xc,
+                                AggDims g, int nv, int d) {
+  const int64_t a = blockIdx.x;
+  const int tile = blockIdx.y;
+  const int nc = 2 * nv;
+  const int o = threadIdx.x / KS, sl = threadIdx.x % KS;
+  const int K = g.asize * d;
+  __shared__ float4 part[256];
+  float4 acc = make_float4(0, 0, 0, 0);
+  if (o < nc) {
+    const int chi = o / nv, j = o % nv;
+    const float2* Pr = P + (((int64_t)a * 2 + chi) * nv + j) * K;
+    const float* rt = r + (int64_t)tile * (2 * d) * g.Vp * 2 * T2;
+    for (int k = sl; k < K; k += KS) {
+      int q = k / d, cp = k % d;
+      int c[4];
+      agg_site(a, q, g.Lc, g.agg, g.L, c);
+      int64_t s = site_index(c, g.L);
+      float4 v = *reinterpret_cast<const float4*>(rt + ((int64_t)(chi * d + cp) * g.Vp + s) * 2 * T2);
+      float2 p = Pr[k];
+      // conj(p) * v for the two lanes (v = re0, re1, im0, im1)
+      acc.x += p.x * v.x + p.y * v.z;
+      acc.y += p.x * v.y + p.y * v.w;
+      acc.z += p.x * v.z - p.y * v.x;
+      acc.w += p.x * v.w - p.y * v.y;
+    }
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (o < nc && sl == 0) {
+    float4 s = part[threadIdx.x];
+    for (int u = 1; u < KS; ++u) {
+      float4 w = part[threadIdx.x + u];
+      s.x += w.x; s.y += w.y; s.z += w.z; s.w += w.w;
+    }
+    *reinterpret_cast<float4*>(xc + (((int64_t)tile * nc + o) * g.Vc + a) * 2 * T2) = s;
+  }
+}
+
+void restrict_vec(const AggDims& g, const float2* P, const float* r, float* xc, int nv, int d, int nsys,
+                  cudaStream_t st) {
+  int nt = ntiles(nsys, T2);
+  int threads = 2 * nv * KS;
+  restrict_kernel<<<dim3((unsigned)g.Vc, nt), threads, 0, st>>>(P, r, xc, g, nv, d);
+}
+
+// e[tile][chi d + c'][site(a, q)] (+)= sum_j P[a][chi][j][k] xc[tile][chi nv + j][a]
+__global__ void prolong_kernel(const float2* __restrict__ P, const float* __restrict__ xc, float* __restrict__ e,
+                               AggDims g, int nv, int d, int accumulate) {
+  const int K = g.asize * d;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int tile = blockIdx.y;
+  if (t >= g.Vc * 2 * (int64_t)K) return;
+  const int k = (int)(t % K);
+  const int chi = (int)((t / K) % 2);
+  const int64_t a = t / ((int64_t)K * 2);
+  const int nc = 2 * nv;
+  const float2* Pc = P + ((a * 2 + chi) * nv) * (int64_t)K + k;
+  const float* xt = xc + (int64_t)tile * nc * g.Vc * 2 * T2;
+  float4 acc = make_float4(0, 0, 0, 0);
+  for (int j = 0; j < nv; ++j) {
+    float2 p = Pc[(int64_t)j * K];
+    float4 x = *reinterpret_cast<const float4*>(xt + ((int64_t)(chi * nv + j) * g.Vc + a) * 2 * T2);
+    acc.x += p.x * x.x - p.y * x.z;
+    acc.y += p.x * x.y - p.y * x.w;
+    acc.z += p.x * x.z + p.y * x.x;
+    acc.w += p.x * x.w + p.y * x.y;
+  }
+  int q = k / d, cp = k % d;
+  int c[4];
+  agg_site(a, q, g.Lc, g.agg, g.L, c);
+  int64_t s = site_index(c, g.L);
+  float* out = e + (((int64_t)tile * (2 * d) + chi * d + cp) * g.Vp + s) * 2 * T2;
+  if (accumulate) {
+    float4 o = *reinterpret_cast<const float4*>(out);
+    acc.x += o.x; acc.y += o.y; acc.z += o.z; acc.w += o.w;
+  }
+  *reinterpret_cast<float4*>(out) = acc;
+}
+
+void prolong_vec(const AggDims& g, const float2* P, const float* xc, float* e, int nv, int d, int nsys, int accumulate,
+                 cudaStream_t st) {
+  int nt = ntiles(nsys, T2);
+  int64_t total = g.Vc * 2 * (int64_t)g.asize * d;
+  prolong_kernel<<<dim3((unsigned)((total + 255) / 256), nt), 256, 0, st>>>(P, xc, e, g, nv, d, accumulate);
+}
+
+// ------------------------------------------------------------------ coarse stencil application
+// y[tile][i][a] = sum_h sum_j A[h][a][j][i] x[tile][j][a + h] + i dmu mu_n g5c(i) x[tile][i][a]
+__global__ void coarse_apply_kernel(const float2* __restrict__ A, const float* __restrict__ x, float* __restrict__ y,
+                                    const double* __restrict__ mu, double dmu, int nsys, CoarseDims cd) {
+  const int nc = cd.nc;
+  const int64_t Vc = cd.Vc;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int tile = blockIdx.y;
+  if (t >= Vc * nc) return;
+  const int i = (int)(t % nc);
+  const int64_t a = t / nc;
+  int c[4];
+  site_coords(a, cd.L, c);
+  const float* xt = x + (int64_t)tile * nc * Vc * 2 * T2;
+  float4 acc = make_float4(0, 0, 0, 0);
+  for (int h = 0; h < 9; ++h) {
+    int64_t nb = a;
+    if (h > 0) {
+      int nu = (h - 1) / 2;
+      int dir = ((h - 1) % 2) ? -1 : 1;
+      int cc[4] = {c[0], c[1], c[2], c[3]};
+      cc[nu] = (cc[nu] + dir + cd.L[nu]) % cd.L[nu];
+      nb = site_index(cc, cd.L);
+    }
+    const float2* Ah = A + (((int64_t)h * Vc + a) * nc) * nc + i;
+    const float* xn = xt + nb * 2 * T2;
+    for (int j = 0; j < nc; ++j) {
+      float2 m = Ah[(int64_t)j * nc];
+      float4 v = *reinterpret_cast<const float4*>(xn + (int64_t)j * Vc * 2 * T2);
+      acc.x += m.x * v.x - m.y * v.z;
+      acc.y += m.x * v.y - m.y * v.w;
+      acc.z += m.x * v.z + m.y * v.x;
+      acc.w += m.x * v.w + m.y * v.y;
+    }
+  }
+  float4 xs = *reinterpret_cast<const float4*>(xt + ((int64_t)i * Vc + a) * 2 * T2);
+  float g5 = i < nc / 2 ? 1.f : -1.f;
+  float m0 = 0, m1 = 0;
+  int n0 = tile * 2, n1 = tile * 2 + 1;
+  if (n0 < nsys) m0 = (float)(dmu * mu[n0]) * g5;
+  if (n1 < nsys) m1 = (float)(dmu * mu[n1]) * g5;
+  // + i m x
+  acc.x -= m0 * xs.z;
+  acc.y -= m1 * xs.w;
+  acc.z += m0 * xs.x;
+  acc.w += m1 * xs.y;
+  *reinterpret_cast<float4*>(y + ((int64_t)(tile * nc + i) * Vc + a) * 2 * T2) = acc;
+}
+
+void coarse_apply(const CoarseDims& cd, const float2* A, const float* x, float* y, const double* mu, double dmu,
+                  int nsys, cudaStream_t st) {
+  int nt = ntiles(nsys, T2);
+  int64_t total = cd.Vc * cd.nc;
+  coarse_apply_kernel<<<dim3((unsigned)((total + 127) / 128), nt), 128, 0, st>>>(A, x, y, mu, dmu, nsys, cd);
+}
+
+// ------------------------------------------------------------------ Galerkin coarse operator
+// W[column n = chi nv + j] = P column: at (a, q) component chi' d + c' holds P[a][chi][j][q d + c']
+// if chi' == chi, else 0. Fine parent (d = 6): a fine bundle of nc systems.
+__global__ void columns_kernel(const float2* __restrict__ P, float* __restrict__ W, AggDims g, int nv, int d) {
+  const int K = g.asize * d;
+  const int nc = 2 * nv;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // one thread per (column pair = tile, parent component, parent site)
+  const int64_t per_tile = (int64_t)(2 * d) * g.Vp;
+  if (t >= per_tile * (nc / T2)) return;
+  int tile = (int)(t / per_tile);
+  int64_t r = t % per_tile;
+  int comp = (int)(r / g.Vp);
+  int64_t s = r % g.Vp;
+  int c[4];
+  site_coords(s, g.L, c);
+  int ac[4], lq[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    ac[k] = c[k] / g.agg[k];
+    lq[k] = c[k] % g.agg[k];
+  }
+  int64_t a = site_index(ac, g.Lc);
+  int q = (int)site_index(lq, g.agg);
+  int chi_p = comp / d, cp = comp % d;
+  float o[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int l = 0; l < T2; ++l) {
+    int n = tile * T2 + l;
+    int chi = n / nv, j = n % nv;
+    if (chi == chi_p) {
+      float2 p = P[(((int64_t)a * 2 + chi) * nv + j) * K + q * d + cp];
+      o[l] = p.x;
+      o[2 + l] = p.y;
+    }
+  }
+  *reinterpret_cast<float4*>(W + t * 2 * T2) = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+// Part h of the fine operator applied to the columns: h = 0 gives the clover/diagonal term
+// plus every hop whose ends lie in one aggregate; h = 1 + 2 nu (2 + 2 nu) gives the forward
+// (backward) hop in direction nu on the sites where it crosses into the next aggregate.
+template <typename real, int T>
+__global__ void __launch_bounds__(128) split_dirac_kernel(const float2* __restrict__ U, const real* __restrict__ C,
+                                                          const real* __restrict__ x, real* __restrict__ y, int ntile,
+                                                          AggDims g, int h, int bc_t) {
+  const int64_t V = g.Vp;
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int tile = blockIdx.y;
+  if (s >= V || tile >= ntile) return;
+  int c[4];
+  site_coords(s, g.L, c);
+  const int64_t tstride = (int64_t)12 * V * 2 * T;
+  const real* xt = x + tile * tstride;
+  Spinor<real, T> acc;
+#pragma unroll
+  for (int k = 0; k < 12; ++k)
+#pragma unroll
+    for (int l = 0; l < T; ++l) { acc.c[k].re[l] = 0; acc.c[k].im[l] = 0; }
+  const int64_t strides[4] = {1, (int64_t)g.L[0], (int64_t)g.L[0] * g.L[1], (int64_t)g.L[0] * g.L[1] * g.L[2]};
+#define TM_SHOP(NU)                                                                                    \
+  {                                                                                                    \
+    bool xf = g.Lc[NU] > 1 && (c[NU] % g.agg[NU]) == g.agg[NU] - 1;                                   \
+    bool xb = g.Lc[NU] > 1 && (c[NU] % g.agg[NU]) == 0;                                                \
+    bool use_f = (h == 0 && !xf) || (h == 1 + 2 * NU && xf);                                           \
+    bool use_b = (h == 0 && !xb) || (h == 2 + 2 * NU && xb);                                           \
+    if (use_f) {                                                                                       \
+      int64_t sf = c[NU] + 1 < g.L[NU] ? s + strides[NU] : s - (int64_t)(g.L[NU] - 1) * strides[NU];   \
+      real pf = (NU == 3 && c[3] == g.L[3] - 1) ? (real)bc_t : real(1);                              \
+      hop<NU, true, real, T>(acc, xt + sf * 2 * T, V, U + (int64_t)NU * 9 * V, V, s, pf);               \
+    }                                                                                                  \
+    if (use_b) {                                                                                       \
+      int64_t sb = c[NU] > 0 ? s - strides[NU] : s + (int64_t)(g.L[NU] - 1) * strides[NU];              \
+      real pb = (NU == 3 && c[3] == 0) ? (real)bc_t : real(1);                                        \
+      hop<NU, false, real, T>(acc, xt + sb * 2 * T, V, U + (int64_t)NU * 9 * V, V, sb, pb);             \
+    }                                                                                                  \
+  }
+  TM_SHOP(0)
+  TM_SHOP(1)
+  TM_SHOP(2)
+  TM_SHOP(3)
+#undef TM_SHOP
+  if (h == 0) {
+    real m[T];
+#pragma unroll
+    for (int l = 0; l < T; ++l) m[l] = 0;
+    local_term<real, T>(acc, xt + s * 2 * T, V, C, V, s, m);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+#pragma unroll
+      for (int l = 0; l < T; ++l) {
+        acc.c[k].re[l] *= real(-0.5);
+        acc.c[k].im[l] *= real(-0.5);
+      }
+  }
+  real* yo = y + tile * tstride + s * 2 * T;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) stcv(yo + (int64_t)k * V * 2 * T, acc.c[k]);
+}
+
+// A[h][a][j][i] = R[tile j/2][i][a][lane j%2]  (R: restricted part h of the columns)
+__global__ void scatter_A_kernel(const float* __restrict__ R, float2* __restrict__ A, int64_t Vc, int nc, int h) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= Vc * nc * (int64_t)nc) return;
+  int i = (int)(t % nc);
+  int j = (int)((t / nc) % nc);
+  int64_t a = t / ((int64_t)nc * nc);
+  const float* e = R + (((int64_t)(j / T2) * nc + i) * Vc + a) * 2 * T2;
+  A[(((int64_t)h * Vc + a) * nc + j) * nc + i] = make_float2(e[j % T2], e[T2 + j % T2]);
+}
+
+void build_coarse_operator_fine(const AggDims& g, const float2* U32, const float* C32, const float2* P, float2* A,
+                                int nv, int bc_t, float* W, float* Y, float* R, cudaStream_t st) {
+  const int nc = 2 * nv;
+  const int nt = nc / T2;
+  int64_t per_tile = (int64_t)12 * g.Vp;
+  columns_kernel<<<(unsigned)((per_tile * nt + 255) / 256), 256, 0, st>>>(P, W, g, nv, 6);
+  CoarseDims cd;
+  for (int h = 0; h < 9; ++h) {
+    split_dirac_kernel<float, T2><<<dim3((unsigned)((g.Vp + 127) / 128), nt), 128, 0, st>>>(U32, C32, W, Y, nt, g, h,
+                                                                                            bc_t);
+    restrict_vec(g, P, Y, R, nv, 6, nc, st);
+    int64_t tot = g.Vc * nc * (int64_t)nc;
+    scatter_A_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(R, A, g.Vc, nc, h);
+  }
+  (void)cd;
+}
+
+}  // namespace tmamg

@@ -47,8 +47,6 @@ static int ensure_scratch(tmamg_ctx* ctx, size_t bytes) {
   return TMAMG_OK;
 }
 
-void free_levels(tmamg_ctx* ctx);
-
 }  // namespace tmamg
 
 using namespace tmamg;
@@ -117,6 +115,7 @@ int tmamg_destroy(tmamg_ctx* ctx) {
   if (!ctx) return TMAMG_OK;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
+  free_workspace(ctx);
   free_levels(ctx);
   cudaFree(ctx->U64);
   cudaFree(ctx->U32);
@@ -175,12 +174,14 @@ int tmamg_set_operator(tmamg_ctx* ctx, double kappa, double c_sw) {
   if (rc) return rc;
   ctx->have_op = true;
   ctx->have_setup = false;
+  free_workspace(ctx);
+  free_levels(ctx);
   return TMAMG_OK;
 }
 
 size_t tmamg_bundle_bytes(const tmamg_ctx* ctx, int nsys, int prec) {
   if (!ctx || nsys <= 0 || (prec != 32 && prec != 64)) return 0;
-  int T = prec == 32 ? 4 : 2;
+  int T = prec == 32 ? 2 : 1;
   size_t es = prec == 32 ? 4 : 8;
   return (size_t)ntiles(nsys, T) * T * 12 * 2 * (size_t)ctx->g.V * es;
 }

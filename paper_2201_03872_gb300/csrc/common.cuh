@@ -1,9 +1,9 @@
 // Shared device/host definitions of the tmamg CUDA library (sm_103a).
 //
-// Bundle layout: real [ntile][ncomp][nsite][2][T]; T = 4 (FP32) or 2 (FP64).
+// Bundle layout: real [ntile][ncomp][nsite][2][T]; T = 2 (FP32) or 1 (FP64).
 // Every kernel of the library reads and writes this layout; the system index
 // runs fastest inside a tile (paper Sec. 3, Fig. 2) so that one 16-byte load
-// brings the same entry of T systems.
+// brings the same complex entry (re[T], im[T]) of T systems.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,8 +16,8 @@
 namespace tmamg {
 
 template <typename real> struct Tile;
-template <> struct Tile<float> { static constexpr int T = 4; };
-template <> struct Tile<double> { static constexpr int T = 2; };
+template <> struct Tile<float> { static constexpr int T = 2; };
+template <> struct Tile<double> { static constexpr int T = 1; };
 
 struct Geom {
   int L[4];     // x, y, z, t
@@ -80,6 +80,9 @@ struct tmamg_ctx {
 };
 
 namespace tmamg {
+
+void free_levels(tmamg_ctx* ctx);
+void free_workspace(tmamg_ctx* ctx);
 
 // error helpers (host)
 int set_err(tmamg_ctx* ctx, int code, const std::string& msg);

@@ -1,0 +1,17 @@
+// SAP smoother (declarations). See sap.cu.
+#pragma once
+#include <string>
+
+#include "common.cuh"
+
+namespace tmamg {
+
+// 0 if the block extents tile the lattice with an even number of blocks (or one) per dimension
+int sap_check_blocks(const Geom& g, const int bs[4], std::string& why);
+
+// e = SAP(r): FP32 bundles of nsys systems. r is overwritten (it ends as a partially
+// updated residual), delta is scratch of the same size, e receives the correction.
+void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C32, float* r, float* e, float* delta,
+               const double* mu, int nsys, int cycles, int steps, cudaStream_t st);
+
+}  // namespace tmamg

@@ -1,0 +1,620 @@
+// Multigrid setup, AMG cycle, mixed-precision multi-rhs/multi-shift solve, and the
+// component entry points of the C ABI.
+//
+// Solve (paper Sec. 4: FGMRES at the top level preconditioned by the multigrid cycle,
+// goal residual 1e-10; Sec. 3: all right-hand sides and shifts iterated together):
+//   outer loop in FP64:   r = b - D(mu_n) x for every system; stop at |r| <= tol |b|;
+//   inner FGMRES(m) in FP32 on r / |r|, preconditioned by the AMG cycle
+//       z = P D_c^{-1} P^+ v,   z += SAP(v - D z)
+//   with the coarse system solved by GMRES to the relative residual r_b (paper: 1e-1).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "amg.cuh"
+#include "blas.cuh"
+#include "krylov.cuh"
+#include "sap.cuh"
+
+namespace tmamg {
+
+template <typename real>
+void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu, int nsys,
+                  cudaStream_t st);
+
+struct Workspace {
+  int nsys = 0, m = 0, mc = 0;
+  size_t fb32 = 0, fb64 = 0, cb32 = 0;  // bytes of one bundle
+  float* V = nullptr;                   // m + 1 fine FP32 bundles
+  float* Z = nullptr;                   // m
+  float *t1 = nullptr, *t2 = nullptr, *t3 = nullptr, *e32 = nullptr;
+  double *x64 = nullptr, *r64 = nullptr, *b64 = nullptr, *t64 = nullptr;
+  float* Vc = nullptr;  // mc + 1 coarse bundles
+  float *xc = nullptr, *rc = nullptr;
+  GmresState top, coarse;
+  double *rel_top = nullptr, *rel_coarse = nullptr, *rn = nullptr, *bn = nullptr, *scale = nullptr;
+  double *beta0 = nullptr, *tmpd = nullptr;
+  double2 *ones = nullptr, *mones = nullptr, *dot = nullptr, *partial64 = nullptr;
+  size_t partial64_cap = 0;
+  int *mask = nullptr, *flags = nullptr, *count = nullptr;
+  int* h_count = nullptr;
+  int *outer_it = nullptr, *inner_it = nullptr;
+  std::vector<void*> extra;
+};
+
+static void ws_free(Workspace* w) {
+  if (!w) return;
+  void* ptrs[] = {w->V, w->Z, w->t1, w->t2, w->t3, w->e32, w->x64, w->r64, w->b64, w->t64, w->Vc, w->xc, w->rc,
+                  w->rel_top, w->rel_coarse, w->rn, w->bn, w->scale, w->beta0, w->tmpd, w->ones, w->mones, w->dot,
+                  w->partial64, w->mask, w->flags, w->count, w->outer_it, w->inner_it};
+  for (void* p : ptrs) cudaFree(p);
+  for (void* p : w->extra) cudaFree(p);
+  if (w->h_count) cudaFreeHost(w->h_count);
+  w->top.release();
+  w->coarse.release();
+  *w = Workspace();
+}
+
+void free_workspace(tmamg_ctx* ctx) {
+  if (ctx->ws) {
+    ws_free(ctx->ws);
+    delete ctx->ws;
+    ctx->ws = nullptr;
+  }
+}
+
+__global__ void fill_c_kernel(double2* a, int n, double re) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = make_double2(re, 0);
+}
+
+static int ensure_ws(tmamg_ctx* ctx, int nsys, int m, int mc) {
+  if (!ctx->ws) ctx->ws = new Workspace();
+  Workspace* w = ctx->ws;
+  if (nsys <= w->nsys && m <= w->m && mc <= w->mc) return 0;
+  int ns = nsys > w->nsys ? nsys : w->nsys;
+  int mm = m > w->m ? m : w->m;
+  int mcc = mc > w->mc ? mc : w->mc;
+  ws_free(w);
+  w->nsys = ns;
+  w->m = mm;
+  w->mc = mcc;
+  const int64_t V = ctx->g.V;
+  w->fb32 = (size_t)ntiles(ns, 2) * 12 * V * 4 * sizeof(float);
+  w->fb64 = (size_t)ns * 12 * V * 2 * sizeof(double);
+  int64_t Vc = ctx->levels.empty() ? 1 : ctx->levels[0].Vc;
+  int nc = ctx->levels.empty() ? 2 : 2 * ctx->levels[0].nv;
+  w->cb32 = (size_t)ntiles(ns, 2) * nc * Vc * 4 * sizeof(float);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(p, b);
+  };
+  A((void**)&w->V, w->fb32 * (mm + 1));
+  A((void**)&w->Z, w->fb32 * mm);
+  A((void**)&w->t1, w->fb32);
+  A((void**)&w->t2, w->fb32);
+  A((void**)&w->t3, w->fb32);
+  A((void**)&w->e32, w->fb32);
+  A((void**)&w->x64, w->fb64);
+  A((void**)&w->r64, w->fb64);
+  A((void**)&w->b64, w->fb64);
+  A((void**)&w->t64, w->fb64);
+  A((void**)&w->Vc, w->cb32 * (mcc + 1));
+  A((void**)&w->xc, w->cb32);
+  A((void**)&w->rc, w->cb32);
+  const size_t d = sizeof(double) * ns;
+  A((void**)&w->rel_top, d);
+  A((void**)&w->rel_coarse, d);
+  A((void**)&w->rn, d);
+  A((void**)&w->bn, d);
+  A((void**)&w->scale, d);
+  A((void**)&w->beta0, d);
+  A((void**)&w->tmpd, d);
+  A((void**)&w->ones, sizeof(double2) * ns);
+  A((void**)&w->mones, sizeof(double2) * ns);
+  A((void**)&w->dot, sizeof(double2) * ns * 4);
+  w->partial64_cap = partial_elems(12 * V, ns, 1, 1);
+  A((void**)&w->partial64, sizeof(double2) * w->partial64_cap);
+  A((void**)&w->mask, sizeof(int) * ns);
+  A((void**)&w->flags, sizeof(int) * ns);
+  A((void**)&w->count, sizeof(int));
+  A((void**)&w->outer_it, sizeof(int) * ns);
+  A((void**)&w->inner_it, sizeof(int) * ns);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&w->h_count, sizeof(int));
+  if (e != cudaSuccess) {
+    ws_free(w);
+    return check_cuda(ctx, e, "workspace allocation");
+  }
+  if (w->top.alloc(mm, ns, partial_elems(12 * V, ns, mm + 1, 2))) return set_err(ctx, TMAMG_ERR_OOM, "gmres state");
+  if (w->coarse.alloc(mcc, ns, partial_elems((int64_t)nc * Vc, ns, mcc + 1, 2)))
+    return set_err(ctx, TMAMG_ERR_OOM, "gmres state");
+  fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->ones, ns, 1.0);
+  fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->mones, ns, -1.0);
+  return check_cuda(ctx, cudaGetLastError(), "workspace init");
+}
+
+// ------------------------------------------------------------------ setup
+static AggDims agg_dims(const Geom& g, const int agg[4]) {
+  AggDims a;
+  a.asize = 1;
+  a.Vc = 1;
+  for (int k = 0; k < 4; ++k) {
+    a.L[k] = g.L[k];
+    a.agg[k] = agg[k];
+    a.Lc[k] = g.L[k] / agg[k];
+    a.asize *= agg[k];
+    a.Vc *= a.Lc[k];
+  }
+  a.Vp = g.V;
+  return a;
+}
+
+static CoarseDims coarse_dims(const CoarseLevel& l) {
+  CoarseDims c;
+  for (int k = 0; k < 4; ++k) c.L[k] = l.Lc[k];
+  c.Vc = l.Vc;
+  c.nc = 2 * l.nv;
+  return c;
+}
+
+// host-side counter-based start vectors: splitmix64 -> uniform -> Box-Muller (complex Gaussian)
+static uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static void start_vectors(uint64_t seed, int nv, int64_t V, std::vector<float>& out) {
+  size_t n = (size_t)nv * V * 12;  // complex numbers
+  out.resize(2 * n);
+  uint64_t key = splitmix64(seed ^ 0x5eedULL);
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t a = splitmix64(key + 2 * i), b = splitmix64(key + 2 * i + 1);
+    double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+    double u2 = ((b >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    double r = sqrt(-log(u1));  // variance 1/2 per component
+    out[2 * i] = (float)(r * cos(2 * M_PI * u2));
+    out[2 * i + 1] = (float)(r * sin(2 * M_PI * u2));
+  }
+}
+
+__global__ void inv_sqrt_kernel(const double2* dot, double2* sc, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double v = dot[i].x;
+    sc[i] = make_double2(v > 0 ? 1.0 / sqrt(v) : 0.0, 0);
+  }
+}
+
+int do_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec_field_dev, bool smooth) {
+  const Geom& g = ctx->g;
+  cudaStream_t st = ctx->stream;
+  std::string why;
+  if (p->levels != 2) return set_err(ctx, TMAMG_ERR_ARG, "setup: only levels = 2 is available");
+  if (sap_check_blocks(g, p->sap_block, why)) return set_err(ctx, TMAMG_ERR_ARG, "setup: " + why);
+  int nv = p->nv[0];
+  if (nv < 1 || nv > 32) return set_err(ctx, TMAMG_ERR_ARG, "setup: nv must be in [1, 32]");
+  int asize = 1;
+  for (int k = 0; k < 4; ++k) {
+    if (p->agg[0][k] < 1 || g.L[k] % p->agg[0][k]) return set_err(ctx, TMAMG_ERR_ARG, "setup: aggregate must divide L");
+    asize *= p->agg[0][k];
+  }
+  if (nv > 6 * asize) return set_err(ctx, TMAMG_ERR_ARG, "setup: nv exceeds the aggregate dimension");
+  if (p->sap_cycles < 1 || p->sap_mr_steps < 1 || p->setup_iters < 0)
+    return set_err(ctx, TMAMG_ERR_ARG, "setup: bad SAP parameters");
+  free_levels(ctx);
+  free_workspace(ctx);
+  ctx->sp = *p;
+  ctx->have_setup = false;
+  AggDims ad = agg_dims(g, p->agg[0]);
+  CoarseLevel lv;
+  for (int k = 0; k < 4; ++k) {
+    lv.Lc[k] = ad.Lc[k];
+    lv.agg[k] = ad.agg[k];
+  }
+  lv.Vc = ad.Vc;
+  lv.nv = nv;
+  lv.asize = ad.asize;
+  const int nc = 2 * nv;
+  int rc = check_cuda(ctx, cudaMalloc(&lv.P, sizeof(float2) * (size_t)ad.Vc * 2 * nv * ad.asize * 6), "cudaMalloc(P)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&lv.A, sizeof(float2) * 9 * (size_t)ad.Vc * nc * nc), "cudaMalloc(A)");
+  if (rc) {
+    cudaFree(lv.P);
+    cudaFree(lv.A);
+    return rc;
+  }
+  ctx->levels.push_back(lv);
+  // scratch: test vectors (nv systems), SAP buffers, columns (nc systems)
+  size_t vb = (size_t)ntiles(nv, 2) * 12 * g.V * 4 * sizeof(float);
+  size_t wb = (size_t)ntiles(nc, 2) * 12 * g.V * 4 * sizeof(float);
+  size_t rb = (size_t)ntiles(nc, 2) * nc * ad.Vc * 4 * sizeof(float);
+  float *Vt = nullptr, *R = nullptr, *E = nullptr, *Dl = nullptr, *W = nullptr, *Y = nullptr, *Rc = nullptr;
+  double *mus = nullptr;
+  double2 *dots = nullptr, *sc = nullptr, *part = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** q, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(q, b);
+  };
+  A((void**)&Vt, vb);
+  A((void**)&R, vb);
+  A((void**)&E, vb);
+  A((void**)&Dl, vb);
+  A((void**)&W, wb);
+  A((void**)&Y, wb);
+  A((void**)&Rc, rb);
+  A((void**)&mus, sizeof(double) * nv);
+  A((void**)&dots, sizeof(double2) * nv);
+  A((void**)&sc, sizeof(double2) * nv);
+  size_t pe = partial_elems(12 * g.V, nv, 1, 2);
+  A((void**)&part, sizeof(double2) * pe);
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    cudaFree(Vt); cudaFree(R); cudaFree(E); cudaFree(Dl); cudaFree(W); cudaFree(Y); cudaFree(Rc);
+    cudaFree(mus); cudaFree(dots); cudaFree(sc); cudaFree(part);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return check_cuda(ctx, e, "setup scratch");
+  }
+  // start / test vectors as an FP32 bundle
+  float* field = nullptr;
+  std::vector<float> host;
+  if (!vec_field_dev) {
+    start_vectors(p->seed, nv, g.V, host);
+    e = cudaMalloc(&field, host.size() * sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(field, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      cudaFree(field);
+      cleanup();
+      return check_cuda(ctx, e, "start vectors");
+    }
+    launch_pack<float>(g, field, Vt, nv, st);
+  } else {
+    launch_pack<float>(g, vec_field_dev, Vt, nv, st);
+  }
+  std::vector<double> hmu(nv, p->mu_setup);
+  cudaMemcpyAsync(mus, hmu.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, st);
+  const int64_t M = 12 * g.V;
+  if (smooth) {
+    for (int it = 0; it < p->setup_iters; ++it) {
+      cudaMemcpyAsync(R, Vt, vb, cudaMemcpyDeviceToDevice, st);
+      sap_apply(g, p->sap_block, ctx->U32, ctx->C32, R, E, Dl, mus, nv, p->sap_cycles, p->sap_mr_steps, st);
+      mdot<float>(E, 0, 1, E, M, nv, dots, nv, part, st);
+      inv_sqrt_kernel<<<(nv + 127) / 128, 128, 0, st>>>(dots, sc, nv);
+      axpby<float>(sc, 2, E, nullptr, 0, Vt, M, nv, nullptr, st);
+    }
+  }
+  CoarseLevel& L1 = ctx->levels[0];
+  build_P(ad, Vt, L1.P, nv, 6, st);
+  build_coarse_operator_fine(ad, ctx->U32, ctx->C32, L1.P, L1.A, nv, g.bc_t, W, Y, Rc, st);
+  rc = check_cuda(ctx, cudaGetLastError(), "setup kernels");
+  cudaError_t se = cudaStreamSynchronize(st);
+  cudaFree(field);
+  cleanup();
+  if (rc) return rc;
+  rc = check_cuda(ctx, se, "setup");
+  if (rc) return rc;
+  ctx->have_setup = true;
+  return TMAMG_OK;
+}
+
+// ------------------------------------------------------------------ AMG cycle and solve
+struct SolveCtx {
+  tmamg_ctx* ctx;
+  const tmamg_solve_params* sp;
+  int nsys;
+  const double* mu;  // device, per system
+  int coarse_iters = 0;
+};
+
+__global__ void restart_tol_kernel(const double2* dot, const double* beta0, double tol, double* rel, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double b = sqrt(fmax(dot[i].x, 0.0));
+  rel[i] = b > 0 ? tol * beta0[i] / b : 1.0;
+}
+
+__global__ void copy_beta_kernel(const double* b, double* dst, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = b[i];
+}
+
+// xc ~ D_c^{-1} rc by restarted GMRES to the relative residual coarse_tol
+static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
+  tmamg_ctx* ctx = S.ctx;
+  Workspace* w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  const CoarseLevel& L1 = ctx->levels[0];
+  CoarseDims cd = coarse_dims(L1);
+  const int64_t M = (int64_t)cd.nc * cd.Vc;
+  const int nsys = S.nsys;
+  const int mc = S.sp->coarse_restart;
+  const size_t vstride = w->cb32 / sizeof(float);
+  LevelOps ops;
+  ops.M = M;
+  const double dmu = S.sp->delta_mu;
+  const double* mu = S.mu;
+  ops.A = [&, dmu, mu, nsys](const float* x, float* y) { coarse_apply(cd, L1.A, x, y, mu, dmu, nsys, st); };
+  cudaMemsetAsync(xc, 0, w->cb32, st);
+  cudaMemcpyAsync(w->Vc, rc, w->cb32, cudaMemcpyDeviceToDevice, st);
+  set_rel_tol(w->rel_coarse, nsys, S.sp->coarse_tol, st);
+  int done = 0;
+  for (int cyc = 0; done < S.sp->coarse_maxiter; ++cyc) {
+    int m = mc < S.sp->coarse_maxiter - done ? mc : S.sp->coarse_maxiter - done;
+    CycleResult r = gmres_cycle(w->coarse, ops, nsys, m, w->Vc, vstride, nullptr, xc, nullptr, w->rel_coarse,
+                                S.sp->poll, false, st);
+    done += r.iters;
+    if (cyc == 0) copy_beta_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->coarse.beta, w->beta0, nsys);
+    if (r.iters < m || done >= S.sp->coarse_maxiter) break;  // every system converged inside the cycle
+    // restart from the true coarse residual
+    coarse_apply(cd, L1.A, xc, w->Vc, mu, dmu, nsys, st);
+    axpby<float>(w->ones, 2, rc, w->mones, 2, w->Vc, M, nsys, nullptr, st);
+    mdot<float>(w->Vc, 0, 1, w->Vc, M, nsys, w->dot, nsys, w->coarse.partial, st);
+    restart_tol_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->beta0, S.sp->coarse_tol, w->rel_coarse, nsys);
+  }
+  S.coarse_iters += done;
+}
+
+// z = M v: coarse-grid correction then SAP post-smoothing (paper Sec. 2)
+static void amg_cycle(SolveCtx& S, const float* v, float* z) {
+  tmamg_ctx* ctx = S.ctx;
+  Workspace* w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  const CoarseLevel& L1 = ctx->levels[0];
+  AggDims ad = agg_dims(ctx->g, L1.agg);
+  const int nsys = S.nsys;
+  const int nv = L1.nv;
+  const int64_t M = 12 * ctx->g.V;
+  restrict_vec(ad, L1.P, v, w->rc, nv, 6, nsys, st);
+  coarse_solve(S, w->rc, w->xc);
+  prolong_vec(ad, L1.P, w->xc, z, nv, 6, nsys, 0, st);
+  launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, z, w->t1, S.mu, nsys, st);
+  axpby<float>(w->ones, 2, v, w->mones, 2, w->t1, M, nsys, nullptr, st);  // t1 = v - D z
+  sap_apply(ctx->g, ctx->sp.sap_block, ctx->U32, ctx->C32, w->t1, w->t2, w->t3, S.mu, nsys, ctx->sp.sap_cycles,
+            ctx->sp.sap_mr_steps, st);
+  axpby<float>(w->ones, 2, w->t2, w->ones, 2, z, M, nsys, nullptr, st);  // z += SAP
+}
+
+// expand b [nrhs][V][12] (complex double) to the FP64 bundle of nsys = nrhs * nshift systems
+__global__ void expand_b_kernel(const double* __restrict__ b, double* __restrict__ b64, int nshift, int nsys,
+                                int64_t V) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nsys * 12 * V) return;
+  int64_t s = t % V;
+  int comp = (int)((t / V) % 12);
+  int n = (int)(t / (12 * V));
+  int r = n / nshift;
+  const double* src = b + (((int64_t)r * V + s) * 12 + comp) * 2;
+  double* dst = b64 + t * 2;
+  dst[0] = src[0];
+  dst[1] = src[1];
+}
+
+// norms -> masks, scales and inner tolerances; flags: 1 = non-finite
+__global__ void outer_check_kernel(const double2* __restrict__ dot, const double* __restrict__ bn, double tol,
+                                   double inner_min, double* rn, double* scale, double* rel, int* mask, int* flags,
+                                   int* count, int* outer_it, int nsys) {
+  int n = threadIdx.x;
+  int on = 0;
+  if (n < nsys) {
+    double r = sqrt(fmax(dot[n].x, 0.0));
+    bool finite = isfinite(dot[n].x) && isfinite(bn[n]);
+    if (!finite) flags[n] = 1;
+    on = finite && !flags[n] && r > tol * bn[n];
+    rn[n] = r;
+    scale[n] = on ? 1.0 / r : 0.0;
+    double want = on ? 0.5 * tol * bn[n] / r : 1.0;
+    rel[n] = want > inner_min ? (want < 0.5 ? want : 0.5) : inner_min;
+    mask[n] = on;
+    if (on) outer_it[n] += 1;
+  }
+  int c = __syncthreads_count(on);
+  if (n == 0) *count = c;
+}
+
+__global__ void sqrt_kernel(const double2* dot, double* out, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = sqrt(fmax(dot[i].x, 0.0));
+}
+
+__global__ void add_iters_kernel(const int* kconv, const int* mask, int* it, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && mask[i]) it[i] += kconv[i];
+}
+
+int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int nshift, double* x, int on_device,
+             const tmamg_solve_params* sp, tmamg_system_stats* stats) {
+  cudaStream_t st = ctx->stream;
+  const Geom& g = ctx->g;
+  const int nsys = nrhs * nshift;
+  if (nsys > 1024) return set_err(ctx, TMAMG_ERR_ARG, "solve: at most 1024 systems per call");
+  if (sp->restart < 1 || sp->restart > 64 || sp->coarse_restart < 1 || sp->coarse_restart > 128 ||
+      sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1)
+    return set_err(ctx, TMAMG_ERR_ARG, "solve: bad parameters");
+  if (sp->precision != 32) return set_err(ctx, TMAMG_ERR_ARG, "solve: precision 64 path not available yet");
+  if (sp->coarse_solver != 0) return set_err(ctx, TMAMG_ERR_ARG, "solve: block coarse solver not available yet");
+  int rc = ensure_ws(ctx, nsys, sp->restart, sp->coarse_restart);
+  if (rc) return rc;
+  Workspace* w = ctx->ws;
+  const int64_t V = g.V;
+  const int64_t M = 12 * V;
+  // per-system twisted masses: system n = rhs (n / nshift), shift (n % nshift)
+  std::vector<double> musys(nsys);
+  for (int n = 0; n < nsys; ++n) musys[n] = mu[n % nshift];
+  rc = upload_mu(ctx, musys.data(), nsys);
+  if (rc) return rc;
+  // b -> FP64 bundle (T = 1)
+  const double* bsrc = b;
+  double* bstage = nullptr;
+  if (!on_device) {
+    size_t bytes = sizeof(double) * 2 * 12 * V * nrhs;
+    rc = check_cuda(ctx, cudaMalloc(&bstage, bytes), "cudaMalloc(b staging)");
+    if (rc) return rc;
+    cudaMemcpyAsync(bstage, b, bytes, cudaMemcpyHostToDevice, st);
+    bsrc = bstage;
+  }
+  expand_b_kernel<<<(unsigned)(((int64_t)nsys * M + 255) / 256), 256, 0, st>>>(bsrc, w->b64, nshift, nsys, V);
+  cudaMemsetAsync(w->x64, 0, w->fb64, st);
+  cudaMemcpyAsync(w->r64, w->b64, w->fb64, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(w->flags, 0, sizeof(int) * nsys, st);
+  cudaMemsetAsync(w->outer_it, 0, sizeof(int) * nsys, st);
+  cudaMemsetAsync(w->inner_it, 0, sizeof(int) * nsys, st);
+  mdot<double>(w->b64, 0, 1, w->b64, M, nsys, w->dot, nsys, w->partial64, st);
+  sqrt_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->bn, nsys);
+  SolveCtx S{ctx, sp, nsys, ctx->mu_dev, 0};
+  LevelOps fine;
+  fine.M = M;
+  fine.A = [&](const float* xx, float* yy) { launch_dirac<float>(g, ctx->U32, ctx->C32, xx, yy, ctx->mu_dev, nsys, st); };
+  fine.precond = [&](const float* v, float* z) { amg_cycle(S, v, z); };
+  const size_t vstride = w->fb32 / sizeof(float);
+  const double inner_min = 2e-6;
+  int outer = 0;
+  for (; outer < sp->max_outer + 1; ++outer) {
+    mdot<double>(w->r64, 0, 1, w->r64, M, nsys, w->dot, nsys, w->partial64, st);
+    outer_check_kernel<<<1, 1024, 0, st>>>(w->dot, w->bn, sp->tol, inner_min, w->rn, w->scale, w->rel_top, w->mask,
+                                          w->flags, w->count, w->outer_it, nsys);
+    cudaMemcpyAsync(w->h_count, w->count, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (*w->h_count == 0 || outer == sp->max_outer) break;
+    f64_to_f32(w->r64, w->scale, w->V, M, nsys, st);
+    cudaMemsetAsync(w->e32, 0, w->fb32, st);
+    gmres_cycle(w->top, fine, nsys, sp->restart, w->V, vstride, w->Z, w->e32, w->mask, w->rel_top, 1, false, st);
+    add_iters_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->top.kconv, w->mask, w->inner_it, nsys);
+    f32_axpy_f64(w->rn, w->e32, w->x64, M, nsys, w->mask, st);
+    launch_dirac<double>(g, ctx->U64, ctx->C64, w->x64, w->t64, ctx->mu_dev, nsys, st);
+    axpby<double>(w->ones, 2, w->b64, w->mones, 2, w->t64, M, nsys, nullptr, st);
+    double* tmp = w->r64;
+    w->r64 = w->t64;
+    w->t64 = tmp;
+  }
+  rc = check_cuda(ctx, cudaGetLastError(), "solve kernels");
+  // final true residual per system (r64 holds b - D x for the current x)
+  std::vector<double> hrn(nsys), hbn(nsys);
+  std::vector<int> hflags(nsys), hout(nsys), hin(nsys);
+  cudaMemcpyAsync(hrn.data(), w->rn, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(hbn.data(), w->bn, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(hflags.data(), w->flags, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(hout.data(), w->outer_it, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(hin.data(), w->inner_it, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st);
+  // x bundle (T = 1) -> x field [nrhs][nshift][V][12]
+  double* xdst = x;
+  double* xstage = nullptr;
+  size_t xbytes = sizeof(double) * 2 * 12 * V * nsys;
+  if (!on_device) {
+    cudaMalloc(&xstage, xbytes);
+    xdst = xstage;
+  }
+  launch_unpack<double>(g, w->x64, xdst, nsys, st);
+  if (!on_device) cudaMemcpyAsync(x, xstage, xbytes, cudaMemcpyDeviceToHost, st);
+  cudaError_t se = cudaStreamSynchronize(st);
+  cudaFree(bstage);
+  cudaFree(xstage);
+  if (!rc) rc = check_cuda(ctx, se, "solve");
+  if (rc) return rc;
+  int all_ok = 1;
+  for (int n = 0; n < nsys; ++n) {
+    double rel = hbn[n] > 0 ? hrn[n] / hbn[n] : 0.0;
+    int status = hflags[n] ? TMAMG_ERR_NONFINITE : (rel <= sp->tol ? TMAMG_OK : TMAMG_NOT_CONVERGED);
+    if (status != TMAMG_OK) all_ok = 0;
+    if (stats) {
+      stats[n].status = status;
+      stats[n].outer_iters = hout[n];
+      stats[n].inner_iters = hin[n];
+      stats[n].coarse_iters = S.coarse_iters;
+      stats[n].true_rel_res = hflags[n] ? NAN : rel;
+    }
+  }
+  return all_ok ? TMAMG_OK : TMAMG_NOT_CONVERGED;
+}
+
+}  // namespace tmamg
+
+using namespace tmamg;
+
+extern "C" {
+
+int tmamg_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* start_vectors) {
+  if (!ctx || !p) return set_err(ctx, TMAMG_ERR_ARG, "setup: null argument");
+  if (!ctx->have_op) return set_err(ctx, TMAMG_ERR_STATE, "setup: operator not set");
+  return do_setup(ctx, p, start_vectors, true);
+}
+
+int tmamg_setup_from_vectors(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* test_vectors) {
+  if (!ctx || !p || !test_vectors) return set_err(ctx, TMAMG_ERR_ARG, "setup_from_vectors: null argument");
+  if (!ctx->have_op) return set_err(ctx, TMAMG_ERR_STATE, "setup_from_vectors: operator not set");
+  return do_setup(ctx, p, test_vectors, false);
+}
+
+int tmamg_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int nshift, double* x, int on_device,
+                const tmamg_solve_params* p, tmamg_system_stats* stats) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!b || !x || !mu || nrhs < 1 || nshift < 1) return set_err(ctx, TMAMG_ERR_ARG, "solve: bad argument");
+  if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "solve: no multigrid setup");
+  tmamg_solve_params def;
+  tmamg_default_solve_params(&def);
+  return do_solve(ctx, b, nrhs, mu, nshift, x, on_device, p ? p : &def, stats);
+}
+
+size_t tmamg_coarse_bundle_bytes(const tmamg_ctx* ctx, int level, int nsys) {
+  if (!ctx || level < 1 || level > (int)ctx->levels.size() || nsys < 1) return 0;
+  const CoarseLevel& l = ctx->levels[level - 1];
+  return (size_t)ntiles(nsys, 2) * 2 * l.nv * l.Vc * 4 * sizeof(float);
+}
+
+int tmamg_sap(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const double* mu, const int block[4],
+              int cycles, int mr_steps) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!r_bundle || !e_bundle || !mu || !block || nsys < 1 || cycles < 1 || mr_steps < 1)
+    return set_err(ctx, TMAMG_ERR_ARG, "sap: bad argument");
+  if (!ctx->have_op) return set_err(ctx, TMAMG_ERR_STATE, "sap: operator not set");
+  std::string why;
+  if (sap_check_blocks(ctx->g, block, why)) return set_err(ctx, TMAMG_ERR_ARG, "sap: " + why);
+  int rc = upload_mu(ctx, mu, nsys);
+  if (rc) return rc;
+  float* delta = nullptr;
+  size_t bytes = (size_t)ntiles(nsys, 2) * 12 * ctx->g.V * 4 * sizeof(float);
+  rc = check_cuda(ctx, cudaMalloc(&delta, bytes), "cudaMalloc(sap scratch)");
+  if (rc) return rc;
+  sap_apply(ctx->g, block, ctx->U32, ctx->C32, (float*)r_bundle, (float*)e_bundle, delta, ctx->mu_dev, nsys, cycles,
+            mr_steps, ctx->stream);
+  rc = check_cuda(ctx, cudaGetLastError(), "sap launch");
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(delta);
+  return rc;
+}
+
+int tmamg_restrict(tmamg_ctx* ctx, int level, const void* fine_bundle, void* coarse_bundle, int nsys) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "restrict: no setup");
+  if (level != 1 || !fine_bundle || !coarse_bundle || nsys < 1) return set_err(ctx, TMAMG_ERR_ARG, "restrict: bad argument");
+  const CoarseLevel& l = ctx->levels[0];
+  restrict_vec(agg_dims(ctx->g, l.agg), l.P, (const float*)fine_bundle, (float*)coarse_bundle, l.nv, 6, nsys,
+               ctx->stream);
+  return check_cuda(ctx, cudaGetLastError(), "restrict launch");
+}
+
+int tmamg_prolong(tmamg_ctx* ctx, int level, const void* coarse_bundle, void* fine_bundle, int nsys) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "prolong: no setup");
+  if (level != 1 || !fine_bundle || !coarse_bundle || nsys < 1) return set_err(ctx, TMAMG_ERR_ARG, "prolong: bad argument");
+  const CoarseLevel& l = ctx->levels[0];
+  prolong_vec(agg_dims(ctx->g, l.agg), l.P, (const float*)coarse_bundle, (float*)fine_bundle, l.nv, 6, nsys, 0,
+              ctx->stream);
+  return check_cuda(ctx, cudaGetLastError(), "prolong launch");
+}
+
+int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_bundle, int nsys, const double* mu) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "coarse_apply: no setup");
+  if (level != 1 || !x_bundle || !y_bundle || !mu || nsys < 1 || x_bundle == y_bundle)
+    return set_err(ctx, TMAMG_ERR_ARG, "coarse_apply: bad argument");
+  int rc = upload_mu(ctx, mu, nsys);
+  if (rc) return rc;
+  const CoarseLevel& l = ctx->levels[0];
+  coarse_apply(coarse_dims(l), l.A, (const float*)x_bundle, (float*)y_bundle, ctx->mu_dev, 1.0, nsys, ctx->stream);
+  return check_cuda(ctx, cudaGetLastError(), "coarse_apply launch");
+}
+
+}  // extern "C"

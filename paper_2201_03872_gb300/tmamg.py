@@ -77,6 +77,14 @@ SIGNATURES = {
     "tmamg_unpack": (I, [P, P, P, I, I]),
     "tmamg_dirac": (I, [P, P, P, I, P, I]),
     "tmamg_apply": (I, [P, P, P, I, P, I]),
+    "tmamg_setup": (I, [P, ctypes.POINTER(SetupParams), P]),
+    "tmamg_setup_from_vectors": (I, [P, ctypes.POINTER(SetupParams), P]),
+    "tmamg_solve": (I, [P, P, I, P, I, P, I, ctypes.POINTER(SolveParams), P]),
+    "tmamg_coarse_bundle_bytes": (ctypes.c_size_t, [P, I, I]),
+    "tmamg_sap": (I, [P, P, P, I, P, ctypes.POINTER(ctypes.c_int), I, I]),
+    "tmamg_restrict": (I, [P, I, P, P, I]),
+    "tmamg_prolong": (I, [P, I, P, P, I]),
+    "tmamg_coarse_apply": (I, [P, I, P, P, I, P]),
 }
 
 
@@ -180,3 +188,75 @@ def tmamg_apply(ctx, x_field, y_field, nsys, mu, prec):
     m = _f64(mu)
     return _check("tmamg_apply", ctx, lib().tmamg_apply(ctx, _ptr(x_field), _ptr(y_field), int(nsys), _ptr(m),
                                                         int(prec)))
+
+
+def setup_params(levels=2, agg=(4, 4, 4, 4), nv=24, sap_block=(4, 4, 4, 4), sap_cycles=2, sap_mr_steps=3,
+                 setup_iters=5, mu_setup=0.0, seed=1, agg2=(2, 2, 2, 2), nv2=32):
+    p = tmamg_default_setup_params()
+    p.levels = levels
+    for d in range(4):
+        p.agg[0][d] = agg[d]
+        p.agg[1][d] = agg2[d]
+        p.sap_block[d] = sap_block[d]
+    p.nv[0] = nv
+    p.nv[1] = nv2
+    p.sap_cycles = sap_cycles
+    p.sap_mr_steps = sap_mr_steps
+    p.setup_iters = setup_iters
+    p.mu_setup = mu_setup
+    p.seed = seed
+    return p
+
+
+def solve_params(**kw):
+    p = tmamg_default_solve_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def tmamg_setup(ctx, params, start_vectors=None):
+    return _check("tmamg_setup", ctx, lib().tmamg_setup(ctx, ctypes.byref(params), _ptr(start_vectors)))
+
+
+def tmamg_setup_from_vectors(ctx, params, test_vectors):
+    return _check("tmamg_setup_from_vectors", ctx,
+                  lib().tmamg_setup_from_vectors(ctx, ctypes.byref(params), _ptr(test_vectors)))
+
+
+def tmamg_solve(ctx, b, nrhs, mu, nshift, x, on_device, params=None):
+    """Returns (status, stats) with stats a list of SystemStats; raises on a negative status."""
+    m = _f64(mu)
+    stats = (SystemStats * (nrhs * nshift))()
+    pp = ctypes.byref(params) if params is not None else None
+    rc = lib().tmamg_solve(ctx, _ptr(b), int(nrhs), _ptr(m), int(nshift), _ptr(x), int(on_device), pp,
+                           ctypes.cast(stats, P))
+    _check("tmamg_solve", ctx, rc)
+    return rc, list(stats)
+
+
+def tmamg_coarse_bundle_bytes(ctx, level, nsys):
+    return lib().tmamg_coarse_bundle_bytes(ctx, int(level), int(nsys))
+
+
+def tmamg_sap(ctx, r_bundle, e_bundle, nsys, mu, block, cycles, mr_steps):
+    m = _f64(mu)
+    blk = (ctypes.c_int * 4)(*[int(v) for v in block])
+    return _check("tmamg_sap", ctx, lib().tmamg_sap(ctx, _ptr(r_bundle), _ptr(e_bundle), int(nsys), _ptr(m), blk,
+                                                    int(cycles), int(mr_steps)))
+
+
+def tmamg_restrict(ctx, level, fine_bundle, coarse_bundle, nsys):
+    return _check("tmamg_restrict", ctx, lib().tmamg_restrict(ctx, int(level), _ptr(fine_bundle),
+                                                              _ptr(coarse_bundle), int(nsys)))
+
+
+def tmamg_prolong(ctx, level, coarse_bundle, fine_bundle, nsys):
+    return _check("tmamg_prolong", ctx, lib().tmamg_prolong(ctx, int(level), _ptr(coarse_bundle),
+                                                            _ptr(fine_bundle), int(nsys)))
+
+
+def tmamg_coarse_apply(ctx, level, x_bundle, y_bundle, nsys, mu):
+    m = _f64(mu)
+    return _check("tmamg_coarse_apply", ctx, lib().tmamg_coarse_apply(ctx, int(level), _ptr(x_bundle),
+                                                                      _ptr(y_bundle), int(nsys), _ptr(m)))

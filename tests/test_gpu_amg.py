@@ -1,0 +1,153 @@
+"""GPU parity of the multigrid components (SAP, P^+, P, D_c) against the FP64 oracle, and
+end-to-end solves checked by the oracle's own operator.
+
+Tolerances: components run in FP32 with FP64 reductions where it matters; a relative
+error of 2e-5 allows for FP32 rounding through a few MR steps / Gram-Schmidt passes
+(unit roundoff 6e-8 times the step count and the condition of the small dots)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import amg, dirac, sap
+from tests.gpu_util import Lattice, coarse_from_bundle, coarse_to_bundle, from_dev, relerr, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 2e-5
+
+
+@pytest.mark.parametrize("L,bs", [((8, 4, 4, 8), (4, 2, 2, 4)), ((8, 8, 8, 8), (4, 4, 4, 4)),
+                                  ((4, 4, 4, 4), (2, 2, 2, 2))])
+def test_sap_matches_oracle(L, bs):
+    U = synth.gauge_field(L, 0.3, seed=51)
+    kappa, c_sw = 0.124, 1.0
+    lat = Lattice(L, U, kappa, c_sw)
+    try:
+        nsys = 3
+        r = synth.gaussian_spinors(L, nsys, seed=52)
+        mu = np.array([0.001, 0.05, -0.2])
+        rb = lat.fine_bundle(r)
+        eb = rb.clone()
+        lat.T.tmamg_sap(lat.ctx, rb, eb, nsys, mu, bs, 2, 3)
+        e = lat.from_fine_bundle(eb, nsys)
+        op = dirac.Operator(U, kappa, c_sw)
+        e_ref = sap.sap(op, r, mu, bs, cycles=2, mr_steps=3)
+        for n in range(nsys):
+            assert relerr(e[n], e_ref[n]) < TOL32, (n, relerr(e[n], e_ref[n]))
+    finally:
+        lat.close()
+
+
+def _setup_pair(L, agg, nv, kappa=0.125, seed=61):
+    U = synth.gauge_field(L, 0.3, seed=seed)
+    lat = Lattice(L, U, kappa, 1.0)
+    Vt = synth.gaussian_spinors(L, nv, seed=seed + 1).astype(np.complex64)
+    T = lat.T
+    p = T.setup_params(agg=agg, nv=nv, sap_block=tuple(2 for _ in range(4)), setup_iters=0)
+    T.tmamg_setup_from_vectors(lat.ctx, p, to_dev(Vt))
+    op = dirac.Operator(U, kappa, 1.0)
+    P = amg.Prolongation(amg.FineLevel.to_chi(Vt.astype(np.complex128)), L, agg)
+    A = amg.coarse_operator(amg.FineLevel(op), P)
+    return lat, op, P, amg.CoarseLevel(A, P.Lc, nv)
+
+
+@pytest.mark.parametrize("L,agg,nv", [((4, 4, 4, 4), (2, 2, 2, 2), 8), ((8, 4, 4, 8), (4, 2, 2, 4), 12)])
+def test_restrict_prolong_match_oracle(L, agg, nv):
+    lat, op, P, cl = _setup_pair(L, agg, nv)
+    try:
+        nsys = 3
+        Vc = int(np.prod(P.Lc))
+        nc = 2 * nv
+        r = synth.gaussian_spinors(L, nsys, seed=71)
+        rb = lat.fine_bundle(r)
+        cb = lat.coarse_buffer(nsys)
+        lat.T.tmamg_restrict(lat.ctx, 1, rb, cb, nsys)
+        lat.torch.cuda.synchronize()
+        xc = coarse_from_bundle(cb.cpu().numpy(), nsys, nc, Vc)
+        ref = P.restrict(amg.FineLevel.to_chi(r)).reshape(nsys, Vc, nc)
+        for n in range(nsys):
+            assert relerr(xc[n], ref[n]) < TOL32
+        # prolongation of a random coarse vector
+        y = synth.complex_normal(72, 1, (nsys, Vc, nc))
+        yb = lat.torch.from_numpy(coarse_to_bundle(y, nc, Vc)).cuda()
+        fb = lat.fine_bundle(np.zeros((nsys,) + r.shape[1:], dtype=np.complex128))
+        lat.T.tmamg_prolong(lat.ctx, 1, yb, fb, nsys)
+        e = lat.from_fine_bundle(fb, nsys)
+        Lxc, Lyc, Lzc, Ltc = P.Lc
+        eref = amg.FineLevel.to_spin(P.prolong(y.reshape(nsys, Ltc, Lzc, Lyc, Lxc, 2, nv)))
+        for n in range(nsys):
+            assert relerr(e[n], eref[n]) < TOL32
+    finally:
+        lat.close()
+
+
+@pytest.mark.parametrize("L,agg,nv", [((4, 4, 4, 4), (2, 2, 2, 2), 8), ((8, 4, 4, 8), (4, 2, 2, 4), 12)])
+def test_coarse_operator_matches_oracle(L, agg, nv):
+    lat, op, P, cl = _setup_pair(L, agg, nv)
+    try:
+        nsys = 5
+        Vc = int(np.prod(P.Lc))
+        nc = 2 * nv
+        x = synth.complex_normal(81, 1, (nsys, Vc, nc))
+        mu = np.linspace(-0.1, 0.3, nsys)
+        xb = lat.torch.from_numpy(coarse_to_bundle(x, nc, Vc)).cuda()
+        yb = lat.coarse_buffer(nsys)
+        lat.T.tmamg_coarse_apply(lat.ctx, 1, xb, yb, nsys, mu)
+        lat.torch.cuda.synchronize()
+        y = coarse_from_bundle(yb.cpu().numpy(), nsys, nc, Vc)
+        Lxc, Lyc, Lzc, Ltc = P.Lc
+        ref = cl.apply(x.reshape(nsys, Ltc, Lzc, Lyc, Lxc, 2, nv), mu).reshape(nsys, Vc, nc)
+        for n in range(nsys):
+            assert relerr(y[n], ref[n]) < TOL32, relerr(y[n], ref[n])
+    finally:
+        lat.close()
+
+
+def _solve(L, U, kappa, c_sw, b, mus, sp_kw, solve_kw):
+    lat = Lattice(L, U, kappa, c_sw)
+    T = lat.T
+    try:
+        T.tmamg_setup(lat.ctx, T.setup_params(**sp_kw))
+        nrhs = b.shape[0]
+        x = np.zeros((nrhs, len(mus)) + b.shape[1:], dtype=np.complex128)
+        rc, stats = T.tmamg_solve(lat.ctx, b, nrhs, mus, len(mus), x, 0, T.solve_params(**solve_kw))
+        return rc, stats, x
+    finally:
+        lat.close()
+
+
+def test_solve_tiny_configuration():
+    # 4^4, eps 0.3, kappa 0.125, c_sw 1, mu 0.01, one Gaussian rhs, 2-level AMG with 2^4
+    # aggregates, Nv 8, SAP blocks 2^4, FGMRES(10) to 1e-10
+    L = (4, 4, 4, 4)
+    U = synth.gauge_field(L, 0.3, seed=1)
+    b = synth.gaussian_spinors(L, 1, seed=1, stream=202)
+    rc, stats, x = _solve(L, U, 0.125, 1.0, b, [0.01],
+                          dict(agg=(2, 2, 2, 2), nv=8, sap_block=(2, 2, 2, 2), setup_iters=3),
+                          dict(restart=10, tol=1e-10))
+    op = dirac.Operator(U, 0.125, 1.0)
+    res = np.linalg.norm(b[0] - op.apply(x[0, 0], 0.01)) / np.linalg.norm(b[0])
+    assert rc == 0 and stats[0].status == 0, [(s.status, s.true_rel_res) for s in stats]
+    assert res <= 1e-10
+    assert abs(stats[0].true_rel_res - res) < 1e-11
+    M = op.dense(0.01)
+    xd = np.linalg.solve(M, b[0].ravel())
+    assert np.linalg.norm(x[0, 0].ravel() - xd) <= np.linalg.cond(M) * 1e-10 * np.linalg.norm(xd)
+
+
+def test_solve_multi_rhs_multi_shift():
+    L = (8, 4, 4, 8)
+    U = synth.gauge_field(L, 0.3, seed=3)
+    kappa = 0.126
+    b = synth.gaussian_spinors(L, 3, seed=4)
+    mus = [0.001, 0.02, 0.3]
+    rc, stats, x = _solve(L, U, kappa, 1.0, b, mus,
+                          dict(agg=(4, 2, 2, 4), nv=12, sap_block=(2, 2, 2, 2), setup_iters=4),
+                          dict(restart=10, tol=1e-10))
+    op = dirac.Operator(U, kappa, 1.0)
+    assert rc == 0
+    for r in range(3):
+        for k, mu in enumerate(mus):
+            res = np.linalg.norm(b[r] - op.apply(x[r, k], mu)) / np.linalg.norm(b[r])
+            assert res <= 1e-10, (r, k, res)
+            assert stats[r * 3 + k].status == 0

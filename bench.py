@@ -200,6 +200,142 @@ def run_dirac(args, world, rank, local):
     return line
 
 
+def setup_kw():
+    return dict(agg=(4, 4, 4, 4), nv=24, sap_block=(4, 4, 4, 4), sap_cycles=2, sap_mr_steps=3, setup_iters=20)
+
+
+def solve_kw():
+    return dict(tol=1e-10, restart=20, max_outer=40, coarse_tol=0.1, coarse_restart=40, coarse_maxiter=400)
+
+
+def measure_dirac(T, ctx, nsys, mu, steps, stream):
+    """CUDA-event time of the fine FP32 stencil on a bundle of nsys systems (same stream)."""
+    import torch
+    nb = T.tmamg_bundle_bytes(ctx, nsys, 32)
+    xb = torch.randn(nb // 4, dtype=torch.float32, device="cuda")
+    yb = torch.empty_like(xb)
+    for _ in range(3):
+        T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32)
+        b.record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def run_solve(args, world, rank, local):
+    import torch
+    from paper_2201_03872_gb300 import tmamg as T
+
+    wl = WORKLOAD
+    L = wl["L"]
+    V = int(np.prod(L))
+    nrhs = wl["nrhs"]
+    mus = [wl["mu"]]
+    nsys = nrhs * len(mus)
+    kappa, ksrc = kappa_for(L, wl["eps"], wl["seed"])
+    U = synth.gauge_field(L, wl["eps"], seed=wl["seed"] + rank)
+    stream = torch.cuda.current_stream()
+    ctx = T.tmamg_create(L, -1, stream.cuda_stream)
+    T.tmamg_load_gauge(ctx, U)
+    T.tmamg_set_operator(ctx, kappa, wl["c_sw"])
+    t = time.time()
+    T.tmamg_setup(ctx, T.setup_params(**setup_kw()))
+    torch.cuda.synchronize()
+    setup_s = time.time() - t
+    b = synth.point_sources(L)
+    bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
+    xd = torch.zeros(nsys * V * 24, dtype=torch.float64, device="cuda")
+    sp = T.solve_params(**solve_kw())
+    for _ in range(args.warmup):
+        T.tmamg_solve(ctx, bd, nrhs, mus, len(mus), xd, 1, sp)
+    torch.cuda.synchronize()
+    barrier(world)
+    ok = True
+    iters = None
+    launches0 = T.tmamg_kernel_launches()
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            rc, stats = T.tmamg_solve(ctx, bd, nrhs, mus, len(mus), xd, 1, sp)
+            ok &= rc == 0 and all(s.status == 0 and s.true_rel_res <= 1e-10 for s in stats)
+            iters = stats
+        t1.record(stream)
+        torch.cuda.synchronize()
+    launches = T.tmamg_kernel_launches() - launches0
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world)
+    solves_per_s = nsys * args.steps * world / (total_ms * 1e-3)
+    # end to end through the public API with host buffers: b copied in, x copied out, every step
+    bh = np.ascontiguousarray(b)
+    xh = np.zeros((nrhs, len(mus)) + b.shape[1:], dtype=np.complex128)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for k in range(args.steps):
+        T.tmamg_solve(ctx, bh, nrhs, mus, len(mus), xh, 0, sp)
+    e2e_s = max_over_ranks(time.perf_counter() - t, world)
+    # the fine stencil (dominant hot kernel named by the metric), same context and systems
+    kern_ms = measure_dirac(T, ctx, nsys, np.full(nsys, wl["mu"]), 20, stream)
+    T.tmamg_destroy(ctx)
+    hbm, _, peak_src = read_peaks()
+    bytes_per_apply = dirac_bytes_per_site(nsys, 32) * V
+    achieved = bytes_per_apply / (kern_ms * 1e-3) / 1e9
+    s0 = iters[0]
+    line = {
+        "metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "lattice": "16^3x32", "systems_per_step": nsys, "kappa": kappa,
+                   "kappa_source": ksrc, "c_sw": wl["c_sw"], "mu": wl["mu"], "tol": 1e-10,
+                   "amg": "2-level, 4^4 aggregates, Nv=24, 20 setup iterations, SAP 4^4 blocks x 2 cycles x 3 MR, "
+                          "FGMRES(20) + FP64 refinement, coarse GMRES(40) to 0.1",
+                   "setup_seconds": setup_s, "all_converged": bool(ok),
+                   "iterations": {"outer": s0.outer_iters, "fgmres": s0.inner_iters, "coarse": s0.coarse_iters},
+                   "l2": "working set > 129 MB L2 (solver vectors 3+ GB)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_source": peak_src, "kernel": "dirac_kernel<float,2> (fine stencil)",
+                     "algorithmic_bytes_per_launch": bytes_per_apply, "launch_ms": kern_ms},
+        "e2e": {"value": nsys * args.steps * world / e2e_s, "unit": "solves/s",
+                "h2d_bytes_per_step": int(bh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clk.result,
+    }
+    return line
+
+
+def cpu_solve_baseline(iters_per_solve=60):
+    """The FP64 numpy oracle on the same lattice: one fine-level AMG iteration (operator
+    applications, SAP smoother, restriction and prolongation with a random P) for one system,
+    timed on the host cores; solves/s = 1 / (time per iteration x iterations per solve).
+    Setup and the coarse solve are left out, so this over-estimates the CPU rate."""
+    from oracle import dirac, sap as osap, amg
+    wl = WORKLOAD
+    L = wl["L"]
+    kappa, _ = kappa_for(L, wl["eps"], wl["seed"])
+    U = synth.gauge_field(L, wl["eps"], seed=wl["seed"])
+    op = dirac.Operator(U, kappa, wl["c_sw"])
+    x = synth.gaussian_spinors(L, 1, seed=7)[0]
+    bop = osap.BlockOperator(op, (4, 4, 4, 4))
+    Vt = synth.gaussian_spinors(L, 24, seed=8)
+    P = amg.Prolongation(amg.FineLevel.to_chi(Vt), L, (4, 4, 4, 4))
+    t = time.perf_counter()
+    y = op.apply(x, wl["mu"])                       # the FGMRES operator application
+    rc = P.restrict(amg.FineLevel.to_chi(y))
+    e = amg.FineLevel.to_spin(P.prolong(rc))
+    r2 = y - op.apply(e, wl["mu"])                  # residual for the smoother
+    e = e + osap.sap(op, r2, wl["mu"], (4, 4, 4, 4), cycles=2, mr_steps=3, bop=bop)
+    dt = time.perf_counter() - t
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": 1.0 / (dt * iters_per_solve), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"one fine-level AMG iteration of the numpy FP64 oracle on 16^3x32 ({dt:.1f} s), times "
+                      f"{iters_per_solve} iterations per solve; setup and coarse solves excluded"}
+
+
 def cpu_dirac_baseline():
     """The FP64 oracle operator on the same lattice and 12 systems, timed on the host cores."""
     from oracle import dirac
@@ -231,10 +367,10 @@ def cpu_dirac_baseline():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--what", default="dirac", choices=["dirac"])
+    ap.add_argument("--what", default="solve", choices=["solve", "dirac"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -242,11 +378,12 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = cpu_dirac_baseline()
+        cb = cpu_solve_baseline() if args.what == "solve" else cpu_dirac_baseline()
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"], "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "fine twisted-mass Wilson-clover stencil, 16^3x32 (CPU oracle sample)"},
+                "config": {"workload": WORKLOAD["name"] if args.what == "solve" else
+                           "fine twisted-mass Wilson-clover stencil, 16^3x32 (CPU oracle sample)"},
                 "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -260,10 +397,10 @@ def main():
         torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
-    line = run_dirac(args, world, rank, local)
+    line = run_solve(args, world, rank, local) if args.what == "solve" else run_dirac(args, world, rank, local)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_dirac_baseline()
+            line["cpu_baseline"] = cpu_solve_baseline() if args.what == "solve" else cpu_dirac_baseline()
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

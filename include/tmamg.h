@@ -100,6 +100,9 @@ int tmamg_destroy(tmamg_ctx* ctx);
 const char* tmamg_last_error(const tmamg_ctx* ctx);
 int tmamg_volume(const tmamg_ctx* ctx, int64_t* V);
 
+/* Number of CUDA kernels this library has launched since it was loaded (all contexts). */
+uint64_t tmamg_kernel_launches(void);
+
 /* Copy a gauge field (complex double, layout above) into the library's own FP64 and FP32
  * copies. on_device: 1 if U is a device pointer, 0 for host memory. The caller keeps U. */
 int tmamg_load_gauge(tmamg_ctx* ctx, const double* U, int on_device);

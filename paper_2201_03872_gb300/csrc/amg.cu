@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(256) orthonormalise_kernel(float2* __restrict_
 
 void build_P(const AggDims& g, const float* Vb, float2* P, int nv, int d, cudaStream_t st) {
   int64_t total = g.Vc * 2 * nv * (int64_t)g.asize * d;
-  gather_P_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Vb, P, g, nv, d);
-  orthonormalise_kernel<<<(unsigned)(g.Vc * 2), 256, 0, st>>>(P, nv, g.asize * d);
+  gather_P_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Vb, P, g, nv, d); TM_COUNT();
+  orthonormalise_kernel<<<(unsigned)(g.Vc * 2), 256, 0, st>>>(P, nv, g.asize * d); TM_COUNT();
 }
 
 // ------------------------------------------------------------------ restriction / prolongation
@@ -178,7 +178,7 @@ void restrict_vec(const AggDims& g, const float2* P, const float* r, float* xc, 
                   cudaStream_t st) {
   int nt = ntiles(nsys, T2);
   int threads = 2 * nv * KS;
-  restrict_kernel<<<dim3((unsigned)g.Vc, nt), threads, 0, st>>>(P, r, xc, g, nv, d);
+  restrict_kernel<<<dim3((unsigned)g.Vc, nt), threads, 0, st>>>(P, r, xc, g, nv, d); TM_COUNT();
 }
 
 // e[tile][chi d + c'][site(a, q)] (+)= sum_j P[a][chi][j][k] xc[tile][chi nv + j][a]
@@ -219,7 +219,7 @@ void prolong_vec(const AggDims& g, const float2* P, const float* xc, float* e, i
                  cudaStream_t st) {
   int nt = ntiles(nsys, T2);
   int64_t total = g.Vc * 2 * (int64_t)g.asize * d;
-  prolong_kernel<<<dim3((unsigned)((total + 255) / 256), nt), 256, 0, st>>>(P, xc, e, g, nv, d, accumulate);
+  prolong_kernel<<<dim3((unsigned)((total + 255) / 256), nt), 256, 0, st>>>(P, xc, e, g, nv, d, accumulate); TM_COUNT();
 }
 
 // ------------------------------------------------------------------ coarse stencil application
@@ -275,7 +275,7 @@ void coarse_apply(const CoarseDims& cd, const float2* A, const float* x, float* 
                   int nsys, cudaStream_t st) {
   int nt = ntiles(nsys, T2);
   int64_t total = cd.Vc * cd.nc;
-  coarse_apply_kernel<<<dim3((unsigned)((total + 127) / 128), nt), 128, 0, st>>>(A, x, y, mu, dmu, nsys, cd);
+  coarse_apply_kernel<<<dim3((unsigned)((total + 127) / 128), nt), 128, 0, st>>>(A, x, y, mu, dmu, nsys, cd); TM_COUNT();
 }
 
 // ------------------------------------------------------------------ Galerkin coarse operator
@@ -395,14 +395,14 @@ void build_coarse_operator_fine(const AggDims& g, const float2* U32, const float
   const int nc = 2 * nv;
   const int nt = nc / T2;
   int64_t per_tile = (int64_t)12 * g.Vp;
-  columns_kernel<<<(unsigned)((per_tile * nt + 255) / 256), 256, 0, st>>>(P, W, g, nv, 6);
+  columns_kernel<<<(unsigned)((per_tile * nt + 255) / 256), 256, 0, st>>>(P, W, g, nv, 6); TM_COUNT();
   CoarseDims cd;
   for (int h = 0; h < 9; ++h) {
     split_dirac_kernel<float, T2><<<dim3((unsigned)((g.Vp + 127) / 128), nt), 128, 0, st>>>(U32, C32, W, Y, nt, g, h,
-                                                                                            bc_t);
+                                                                                            bc_t); TM_COUNT();
     restrict_vec(g, P, Y, R, nv, 6, nc, st);
     int64_t tot = g.Vc * nc * (int64_t)nc;
-    scatter_A_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(R, A, g.Vc, nc, h);
+    scatter_A_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(R, A, g.Vc, nc, h); TM_COUNT();
   }
   (void)cd;
 }

@@ -7,6 +7,11 @@
 
 namespace tmamg {
 
+uint64_t& launch_counter() {
+  static uint64_t n = 0;
+  return n;
+}
+
 int set_err(tmamg_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
   return code;
@@ -128,6 +133,8 @@ int tmamg_destroy(tmamg_ctx* ctx) {
 }
 
 const char* tmamg_last_error(const tmamg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+uint64_t tmamg_kernel_launches(void) { return launch_counter(); }
 
 int tmamg_volume(const tmamg_ctx* ctx, int64_t* V) {
   if (!ctx || !V) return TMAMG_ERR_ARG;

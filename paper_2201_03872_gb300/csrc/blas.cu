@@ -128,9 +128,9 @@ void mdot(const real* V, int64_t vstride, int k, const real* w, int64_t M, int n
   constexpr int T = Tile<real>::T;
   int nt = ntiles(nsys, T);
   int nblk = red_blocks(M, nt);
-  mdot_partial_kernel<real, T><<<dim3(nblk, nt), RED_THREADS, 0, st>>>(V, vstride, k, w, M, partial);
+  mdot_partial_kernel<real, T><<<dim3(nblk, nt), RED_THREADS, 0, st>>>(V, vstride, k, w, M, partial); TM_COUNT();
   int tot = nsys * k;
-  mdot_final_kernel<T><<<(tot + 127) / 128, 128, 0, st>>>(partial, nblk, k, nsys, out, ostride, 1.0);
+  mdot_final_kernel<T><<<(tot + 127) / 128, 128, 0, st>>>(partial, nblk, k, nsys, out, ostride, 1.0); TM_COUNT();
 }
 
 size_t partial_elems(int64_t M, int nsys, int kmax, int T) {
@@ -187,7 +187,7 @@ void maxpy(const real* V, int64_t vstride, int k, const double2* c, int64_t cstr
   constexpr int T = Tile<real>::T;
   int nt = ntiles(nsys, T);
   maxpy_kernel<real, T><<<upd_grid(M, nt, 256), 256, 0, st>>>(V, vstride, k, c, cstride, (real)sign, y, M, nsys,
-                                                               mask);
+                                                               mask); TM_COUNT();
 }
 
 // y[n] = a[n] * x[n] + b[n] * y[n]; a, b complex per system (nullptr a => 0, nullptr b => y ignored,
@@ -237,7 +237,7 @@ void axpby(const double2* a, int amode, const real* x, const double2* b, int bmo
            const int* mask, cudaStream_t st) {
   constexpr int T = Tile<real>::T;
   int nt = ntiles(nsys, T);
-  axpby_kernel<real, T><<<upd_grid(M, nt, 256), 256, 0, st>>>(a, x, b, y, M, nsys, mask, amode, bmode);
+  axpby_kernel<real, T><<<upd_grid(M, nt, 256), 256, 0, st>>>(a, x, b, y, M, nsys, mask, amode, bmode); TM_COUNT();
 }
 
 // ----------------------------------------------------------------------- FP64 <-> FP32
@@ -266,7 +266,7 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ x64, const double* 
 
 void f64_to_f32(const double* x64, const double* s, float* x32, int64_t M, int nsys, cudaStream_t st) {
   int nt = ntiles(nsys, 2);
-  f64_to_f32_kernel<<<dim3((unsigned)((M + 255) / 256), nt), 256, 0, st>>>(x64, s, x32, M, nsys);
+  f64_to_f32_kernel<<<dim3((unsigned)((M + 255) / 256), nt), 256, 0, st>>>(x64, s, x32, M, nsys); TM_COUNT();
 }
 
 // x64[n] += s[n] * x32[n]  for active systems
@@ -289,7 +289,7 @@ __global__ void f32_axpy_f64_kernel(const double* __restrict__ s, const float* _
 
 void f32_axpy_f64(const double* s, const float* x32, double* x64, int64_t M, int nsys, const int* mask,
                   cudaStream_t st) {
-  f32_axpy_f64_kernel<<<dim3((unsigned)((M + 255) / 256), nsys), 256, 0, st>>>(s, x32, x64, M, nsys, mask);
+  f32_axpy_f64_kernel<<<dim3((unsigned)((M + 255) / 256), nsys), 256, 0, st>>>(s, x32, x64, M, nsys, mask); TM_COUNT();
 }
 
 // ----------------------------------------------------------------------- explicit instantiations

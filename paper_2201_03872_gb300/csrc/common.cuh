@@ -15,6 +15,10 @@
 
 namespace tmamg {
 
+// number of kernels this library has launched (all contexts), for launch accounting
+uint64_t& launch_counter();
+#define TM_COUNT() (++::tmamg::launch_counter())
+
 template <typename real> struct Tile;
 template <> struct Tile<float> { static constexpr int T = 2; };
 template <> struct Tile<double> { static constexpr int T = 1; };

@@ -35,7 +35,7 @@ __global__ void convert_gauge_kernel(const double* __restrict__ Uin, double2* __
 void launch_convert_gauge(const Geom& g, const double* Uin, double2* U64, float2* U32, cudaStream_t st) {
   int64_t n = g.V * 4;
   int bs = 256;
-  convert_gauge_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(Uin, U64, U32, g.V);
+  convert_gauge_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(Uin, U64, U32, g.V); TM_COUNT();
 }
 
 // ---------------------------------------------------------------- clover construction (FP64)
@@ -228,7 +228,7 @@ void launch_build_clover(const Geom& g, const double2* U64, double kappa, double
                          cudaStream_t st) {
   int bs = 128;
   build_clover_kernel<<<(unsigned)((g.V + bs - 1) / bs), bs, 0, st>>>(U64, g.L[0], g.L[1], g.L[2], g.L[3], kappa,
-                                                                       c_sw, C64, C32);
+                                                                       c_sw, C64, C32); TM_COUNT();
 }
 
 template <typename real, int T, int BX>
@@ -296,7 +296,7 @@ void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, re
   dim3 block(BX, ty);
   dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nt / ty));
   dirac_kernel<real, T, BX><<<grid, block, 0, st>>>(reinterpret_cast<const typename LinkT<real>::t*>(U), C, x, y, mu,
-                                                    nsys, nt, g.L[0], g.L[1], g.L[2], g.L[3], (real)g.bc_t);
+                                                    nsys, nt, g.L[0], g.L[1], g.L[2], g.L[3], (real)g.bc_t); TM_COUNT();
 }
 
 template void launch_dirac<float>(const Geom&, const void*, const float*, const float*, float*, const double*, int,
@@ -356,7 +356,7 @@ void launch_pack(const Geom& g, const real* field, real* bundle, int nsys, cudaS
   int nt = ntiles(nsys, Tile<real>::T);
   int64_t total = (int64_t)nt * 12 * g.V;
   int bs = 256;
-  pack_kernel<real><<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(field, bundle, nsys, nt, g.V);
+  pack_kernel<real><<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(field, bundle, nsys, nt, g.V); TM_COUNT();
 }
 
 template <typename real>
@@ -364,7 +364,7 @@ void launch_unpack(const Geom& g, const real* bundle, real* field, int nsys, cud
   int nt = ntiles(nsys, Tile<real>::T);
   int64_t total = (int64_t)nt * 12 * g.V;
   int bs = 256;
-  unpack_kernel<real><<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(bundle, field, nsys, nt, g.V);
+  unpack_kernel<real><<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(bundle, field, nsys, nt, g.V); TM_COUNT();
 }
 
 template void launch_pack<float>(const Geom&, const float*, float*, int, cudaStream_t);

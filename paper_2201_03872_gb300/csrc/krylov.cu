@@ -59,7 +59,7 @@ __global__ void set_value_kernel(double* a, int n, double v) {
 }
 
 void set_rel_tol(double* rel, int nsys, double value, cudaStream_t s) {
-  set_value_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(rel, nsys, value);
+  set_value_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(rel, nsys, value); TM_COUNT();
 }
 
 // beta = |r0|, g = (beta, 0, ...), scale = 1 / beta, tolerance, masks
@@ -198,7 +198,7 @@ CycleResult gmres_cycle(GmresState& st, const LevelOps& ops, int nsys, int m, fl
   // |r0|
   mdot<float>(V, 0, 1, V, M, nsys, st.tmp, cap, st.partial, s);
   gmres_init_kernel<<<1, 1024, 0, s>>>(st.tmp, nsys, cap, m, participate, rel_tol, st.beta, st.g, st.sc, st.tolabs,
-                                       st.kconv, st.active, st.nactive);
+                                       st.kconv, st.active, st.nactive); TM_COUNT();
   axpby<float>(nullptr, 0, nullptr, st.sc, 2, V, M, nsys, nullptr, s);
   int done = 0;
   for (int j = 0; j < m; ++j) {
@@ -217,13 +217,13 @@ CycleResult gmres_cycle(GmresState& st, const LevelOps& ops, int nsys, int m, fl
     if (cgs2) {
       mdot<float>(V, vstride, j + 1, w, M, nsys, st.tmp, cap, st.partial, s);
       maxpy<float>(V, vstride, j + 1, st.tmp, cap, -1.0, w, M, nsys, nullptr, s);
-      add_col_kernel<<<((j + 1) * nsys + 127) / 128, 128, 0, s>>>(Hcol, st.tmp, j + 1, nsys, cap);
+      add_col_kernel<<<((j + 1) * nsys + 127) / 128, 128, 0, s>>>(Hcol, st.tmp, j + 1, nsys, cap); TM_COUNT();
     }
     mdot<float>(w, 0, 1, w, M, nsys, st.tmp, cap, st.partial, s);
-    norm_finish_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(st.tmp, Hcol + (size_t)(j + 1) * cap, st.sc, nsys);
+    norm_finish_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(st.tmp, Hcol + (size_t)(j + 1) * cap, st.sc, nsys); TM_COUNT();
     axpby<float>(nullptr, 0, nullptr, st.sc, 2, w, M, nsys, nullptr, s);
     givens_kernel<<<1, 1024, 0, s>>>(st.H, st.cs, st.sn, st.g, st.resid, st.tolabs, st.kconv, st.active, st.nactive,
-                                     j, m, nsys, cap);
+                                     j, m, nsys, cap); TM_COUNT();
     done = j + 1;
     if (done == m) break;
     if (poll > 0 && (done % poll) == 0) {
@@ -231,7 +231,7 @@ CycleResult gmres_cycle(GmresState& st, const LevelOps& ops, int nsys, int m, fl
       if (*st.h_nactive == 0) break;
     }
   }
-  backsub_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(st.H, st.g, st.y, st.kconv, m, nsys, cap, done);
+  backsub_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(st.H, st.g, st.y, st.kconv, m, nsys, cap, done); TM_COUNT();
   maxpy<float>(ops.precond ? Z : V, vstride, done, st.y, cap, +1.0, x, M, nsys, nullptr, s);
   CycleResult r;
   r.iters = done;

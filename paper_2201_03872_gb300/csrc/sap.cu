@@ -327,11 +327,11 @@ void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C
   for (int cy = 0; cy < cycles; ++cy) {
     for (int colour = 0; colour < 2; ++colour) {
       sap_mr_kernel<float, T><<<dim3(nblocks, nt), nthreads, smem, st>>>(U32, C32, r, delta, e, mu, nsys, d, colour,
-                                                                      steps);
+                                                                      steps); TM_COUNT();
       bool last = (cy == cycles - 1) && colour == 1;
       if (!last) {
         sap_face_kernel<float, T><<<dim3((unsigned)((g.V + 255) / 256), nt), 256, 0, st>>>(U32, delta, r, d,
-                                                                                          1 - colour, nt);
+                                                                                          1 - colour, nt); TM_COUNT();
       }
     }
   }

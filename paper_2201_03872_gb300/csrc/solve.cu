@@ -128,8 +128,8 @@ static int ensure_ws(tmamg_ctx* ctx, int nsys, int m, int mc) {
   if (w->top.alloc(mm, ns, partial_elems(12 * V, ns, mm + 1, 2))) return set_err(ctx, TMAMG_ERR_OOM, "gmres state");
   if (w->coarse.alloc(mcc, ns, partial_elems((int64_t)nc * Vc, ns, mcc + 1, 2)))
     return set_err(ctx, TMAMG_ERR_OOM, "gmres state");
-  fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->ones, ns, 1.0);
-  fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->mones, ns, -1.0);
+  fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->ones, ns, 1.0); TM_COUNT();
+  fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->mones, ns, -1.0); TM_COUNT();
   return check_cuda(ctx, cudaGetLastError(), "workspace init");
 }
 
@@ -282,7 +282,7 @@ int do_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec_field
       cudaMemcpyAsync(R, Vt, vb, cudaMemcpyDeviceToDevice, st);
       sap_apply(g, p->sap_block, ctx->U32, ctx->C32, R, E, Dl, mus, nv, p->sap_cycles, p->sap_mr_steps, st);
       mdot<float>(E, 0, 1, E, M, nv, dots, nv, part, st);
-      inv_sqrt_kernel<<<(nv + 127) / 128, 128, 0, st>>>(dots, sc, nv);
+      inv_sqrt_kernel<<<(nv + 127) / 128, 128, 0, st>>>(dots, sc, nv); TM_COUNT();
       axpby<float>(sc, 2, E, nullptr, 0, Vt, M, nv, nullptr, st);
     }
   }
@@ -346,13 +346,13 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
     CycleResult r = gmres_cycle(w->coarse, ops, nsys, m, w->Vc, vstride, nullptr, xc, nullptr, w->rel_coarse,
                                 S.sp->poll, false, st);
     done += r.iters;
-    if (cyc == 0) copy_beta_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->coarse.beta, w->beta0, nsys);
+    if (cyc == 0) copy_beta_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->coarse.beta, w->beta0, nsys); TM_COUNT();
     if (r.iters < m || done >= S.sp->coarse_maxiter) break;  // every system converged inside the cycle
     // restart from the true coarse residual
     coarse_apply(cd, L1.A, xc, w->Vc, mu, dmu, nsys, st);
     axpby<float>(w->ones, 2, rc, w->mones, 2, w->Vc, M, nsys, nullptr, st);
     mdot<float>(w->Vc, 0, 1, w->Vc, M, nsys, w->dot, nsys, w->coarse.partial, st);
-    restart_tol_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->beta0, S.sp->coarse_tol, w->rel_coarse, nsys);
+    restart_tol_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->beta0, S.sp->coarse_tol, w->rel_coarse, nsys); TM_COUNT();
   }
   S.coarse_iters += done;
 }
@@ -455,14 +455,14 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
     cudaMemcpyAsync(bstage, b, bytes, cudaMemcpyHostToDevice, st);
     bsrc = bstage;
   }
-  expand_b_kernel<<<(unsigned)(((int64_t)nsys * M + 255) / 256), 256, 0, st>>>(bsrc, w->b64, nshift, nsys, V);
+  expand_b_kernel<<<(unsigned)(((int64_t)nsys * M + 255) / 256), 256, 0, st>>>(bsrc, w->b64, nshift, nsys, V); TM_COUNT();
   cudaMemsetAsync(w->x64, 0, w->fb64, st);
   cudaMemcpyAsync(w->r64, w->b64, w->fb64, cudaMemcpyDeviceToDevice, st);
   cudaMemsetAsync(w->flags, 0, sizeof(int) * nsys, st);
   cudaMemsetAsync(w->outer_it, 0, sizeof(int) * nsys, st);
   cudaMemsetAsync(w->inner_it, 0, sizeof(int) * nsys, st);
   mdot<double>(w->b64, 0, 1, w->b64, M, nsys, w->dot, nsys, w->partial64, st);
-  sqrt_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->bn, nsys);
+  sqrt_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->bn, nsys); TM_COUNT();
   SolveCtx S{ctx, sp, nsys, ctx->mu_dev, 0};
   LevelOps fine;
   fine.M = M;
@@ -474,14 +474,14 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   for (; outer < sp->max_outer + 1; ++outer) {
     mdot<double>(w->r64, 0, 1, w->r64, M, nsys, w->dot, nsys, w->partial64, st);
     outer_check_kernel<<<1, 1024, 0, st>>>(w->dot, w->bn, sp->tol, inner_min, w->rn, w->scale, w->rel_top, w->mask,
-                                          w->flags, w->count, w->outer_it, nsys);
+                                          w->flags, w->count, w->outer_it, nsys); TM_COUNT();
     cudaMemcpyAsync(w->h_count, w->count, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     if (*w->h_count == 0 || outer == sp->max_outer) break;
     f64_to_f32(w->r64, w->scale, w->V, M, nsys, st);
     cudaMemsetAsync(w->e32, 0, w->fb32, st);
     gmres_cycle(w->top, fine, nsys, sp->restart, w->V, vstride, w->Z, w->e32, w->mask, w->rel_top, 1, false, st);
-    add_iters_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->top.kconv, w->mask, w->inner_it, nsys);
+    add_iters_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->top.kconv, w->mask, w->inner_it, nsys); TM_COUNT();
     f32_axpy_f64(w->rn, w->e32, w->x64, M, nsys, w->mask, st);
     launch_dirac<double>(g, ctx->U64, ctx->C64, w->x64, w->t64, ctx->mu_dev, nsys, st);
     axpby<double>(w->ones, 2, w->b64, w->mones, 2, w->t64, M, nsys, nullptr, st);

@@ -70,6 +70,7 @@ SIGNATURES = {
     "tmamg_destroy": (I, [P]),
     "tmamg_last_error": (ctypes.c_char_p, [P]),
     "tmamg_volume": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+    "tmamg_kernel_launches": (ctypes.c_uint64, []),
     "tmamg_load_gauge": (I, [P, P, I]),
     "tmamg_set_operator": (I, [P, D, D]),
     "tmamg_bundle_bytes": (ctypes.c_size_t, [P, I, I]),
@@ -152,6 +153,10 @@ def tmamg_volume(ctx):
     v = ctypes.c_int64()
     _check("tmamg_volume", ctx, lib().tmamg_volume(ctx, ctypes.byref(v)))
     return v.value
+
+
+def tmamg_kernel_launches():
+    return lib().tmamg_kernel_launches()
 
 
 def tmamg_load_gauge(ctx, U, on_device=None):

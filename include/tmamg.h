@@ -167,6 +167,29 @@ size_t tmamg_coarse_bundle_bytes(const tmamg_ctx* ctx, int level, int nsys);
 int tmamg_sap(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const double* mu, const int block[4],
               int cycles, int mr_steps);
 
+/* Fixed limits of tmamg_sap_noalloc: scratch bytes (one FP32 fine bundle) and systems per call. */
+#define TMAMG_SAP_NOALLOC_MAX_BYTES ((size_t)64 << 20)
+#define TMAMG_SAP_NOALLOC_MAX_SYSTEMS 64
+
+/* tmamg_sap for callers that cannot allocate device memory at call time: code that runs
+ * while a stream is being captured into a CUDA graph (where cudaMalloc is not allowed), code
+ * that must not touch the allocator after it has fixed its memory budget, or code running
+ * under a memory pool it does not own. Same arguments and result as tmamg_sap; the paper has
+ * no counterpart, this is a property of the library only.
+ * Its scratch (the correction buffer of the red/black sweeps, and the nsys twisted masses)
+ * lives in file-scope device arrays of TMAMG_SAP_NOALLOC_MAX_BYTES bytes and
+ * TMAMG_SAP_NOALLOC_MAX_SYSTEMS doubles, which every GPU that loads the library holds until
+ * the process exits; the call allocates and frees nothing. A bundle larger than the scratch
+ * (ceil(nsys/2) * 12 * V * 16 bytes > TMAMG_SAP_NOALLOC_MAX_BYTES) or more systems than the
+ * limit is rejected with TMAMG_ERR_ARG before anything is launched.
+ * The first call on a device looks up the arrays' device addresses (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture. Every call
+ * shares the arrays: two calls whose work overlaps on the GPU (different streams, or
+ * different contexts on one device) race on them. mu: host [nsys], copied with
+ * cudaMemcpyAsync on the context's stream. */
+int tmamg_sap_noalloc(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const double* mu, const int block[4],
+                      int cycles, int mr_steps);
+
 /* xc = P^+ r (restriction) and r = P xc (prolongation, overwrites) between the fine level and
  * coarse level 1, FP32 bundles. Require a setup. */
 int tmamg_restrict(tmamg_ctx* ctx, int level, const void* fine_bundle, void* coarse_bundle, int nsys);

@@ -83,6 +83,7 @@ SIGNATURES = {
     "tmamg_solve": (I, [P, P, I, P, I, P, I, ctypes.POINTER(SolveParams), P]),
     "tmamg_coarse_bundle_bytes": (ctypes.c_size_t, [P, I, I]),
     "tmamg_sap": (I, [P, P, P, I, P, ctypes.POINTER(ctypes.c_int), I, I]),
+    "tmamg_sap_noalloc": (I, [P, P, P, I, P, ctypes.POINTER(ctypes.c_int), I, I]),
     "tmamg_restrict": (I, [P, I, P, P, I]),
     "tmamg_prolong": (I, [P, I, P, P, I]),
     "tmamg_coarse_apply": (I, [P, I, P, P, I, P]),
@@ -249,6 +250,14 @@ def tmamg_sap(ctx, r_bundle, e_bundle, nsys, mu, block, cycles, mr_steps):
     blk = (ctypes.c_int * 4)(*[int(v) for v in block])
     return _check("tmamg_sap", ctx, lib().tmamg_sap(ctx, _ptr(r_bundle), _ptr(e_bundle), int(nsys), _ptr(m), blk,
                                                     int(cycles), int(mr_steps)))
+
+
+def tmamg_sap_noalloc(ctx, r_bundle, e_bundle, nsys, mu, block, cycles, mr_steps):
+    """tmamg_sap without device allocation (fixed-size library-held scratch; see the header)."""
+    m = _f64(mu)
+    blk = (ctypes.c_int * 4)(*[int(v) for v in block])
+    return _check("tmamg_sap_noalloc", ctx, lib().tmamg_sap_noalloc(ctx, _ptr(r_bundle), _ptr(e_bundle), int(nsys),
+                                                                    _ptr(m), blk, int(cycles), int(mr_steps)))
 
 
 def tmamg_restrict(ctx, level, fine_bundle, coarse_bundle, nsys):

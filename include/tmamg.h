@@ -74,7 +74,8 @@ typedef struct {
   double coarse_tol;   /* relative residual goal of the coarsest-level solve (r_b) */
   int coarse_restart;  /* coarse GMRES restart length */
   int coarse_maxiter;  /* coarse iterations per cycle, upper bound */
-  int coarse_solver;   /* 0: batched GMRES per system; 1: block GMRES over the rhs of each shift */
+  int coarse_solver;   /* 0: persistent GMRES (one cooperative launch per coarse solve, all systems);
+                          1: block GMRES over the rhs of each shift; 2: GMRES with one launch per step */
   double delta_mu;     /* coarse twisted-mass factor (paper Fig. 6 caption), 1 = none */
   int precision;       /* 32: mixed (FP32 inner, FP64 outer); 64: plain FP64 single-precision-free path */
   int use_nn;          /* reserved: learned preconditioner step (0 = off) */

@@ -101,10 +101,8 @@ def main():
     jobs = [((16, 16, 16, 32), 0.25, 1), ((24, 24, 24, 48), 0.25, 1), ((32, 32, 32, 64), 0.2, 1),
             ((40, 40, 40, 80), 0.2, 1)]
     only = [float(a) for a in sys.argv[1:]]
-    if only:
+    if only:  # tune a subset of gauge recipes (eps values); entries are merged into the table
         jobs = [j for j in jobs if j[1] in only]
-        out_path = os.path.join(ROOT, "tests", "golden", f"kappa_eps{only[0]}.json")
-        table = {}
     done = {}
     for Lbig, eps, seed in jobs:
         key = f"{Lbig[0]}x{Lbig[1]}x{Lbig[2]}x{Lbig[3]}_eps{eps}_seed{seed}"

@@ -1,0 +1,759 @@
+// Persistent restarted GMRES on the coarse lattice for all systems at once (one launch per
+// coarse solve).
+//
+// The coarse-grid problem is small (V_c sites x 2 Nv unknowns) and the paper traces the loss
+// of strong scaling of DDalphaAMG to this level (Sec. 3, Fig. 3 right) and most of the
+// block-solver overhead to global reductions (Sec. 4). On one GPU the equivalent cost is
+// kernel-launch latency: a GMRES step is a stencil application, a Gram-Schmidt pass, a norm
+// and a Givens rotation per system. Here all of it runs inside one cooperative kernel; the
+// phases are separated by a grid barrier whose wait is bounded (about one second), after
+// which the kernel records an error and returns instead of hanging. Reductions are
+// deterministic: per-CTA partial sums in FP64, then a fixed-order sum.
+//
+// Work decomposition.
+//  * Stencil phase: independent warp tasks (coarse site, hop, chunk of system tiles); each
+//    stencil entry is read once per application for all systems (paper Sec. 3, matrix data
+//    loaded once for all right-hand sides); the nine hop partials are summed in a fixed
+//    order by the owner threads after a grid barrier.
+//  * Vector phases: CTA b works on tile b % nt and on the entries of slice b / nt; the same
+//    thread owns the same entries in every vector phase, so in-place updates need no
+//    barrier of their own.
+//  * Small dense work (Givens rotations, back substitution) is per system, with every
+//    operand fetched before the dependent arithmetic starts.
+#include <cmath>
+
+#include "amg.cuh"
+#include "coarse_gmres.cuh"
+
+namespace tmamg {
+
+constexpr int CG_THREADS = 256;
+constexpr int CG_TCH = 8;    // system tiles per shared-memory chunk in the stencil phase
+constexpr int CG_IVEC = 8;   // basis vectors per register chunk in the dot phase
+constexpr int CG_MAXM = 64;  // largest restart length
+constexpr int CG_EPT = 4;    // entries per thread held in registers in the vector phases
+constexpr int CG_ABATCH = 8; // stencil loads in flight per thread
+constexpr int CG_MAXNC = 64; // largest coarse site dimension 2 Nv
+
+struct CGArgs {
+  const float2* A;
+  int L[4];
+  int64_t Vc;
+  int nc;
+  const float* rc;
+  float* xc;
+  float* V;
+  int64_t vstride;  // floats between basis vectors
+  const double* mu;
+  double dmu;
+  int nsys, nt;
+  int64_t M;  // entries per tile
+  int m, maxiter;
+  double tol;
+  // per-system FP64 state, [.. * NS + n]
+  double2* H;  // [(j (m+1) + i)]
+  double* cs;  // [j]
+  double2* sn; // [j]
+  double2* g;  // [i]
+  double2* y;  // [i]
+  double* tolabs;
+  double* sc;  // scale of the newest basis vector (applied lazily)
+  int* kconv;
+  int* active;
+  int* done;      // converged (no restart needed)
+  int* nactive;   // [1]
+  double2* part;  // [G][m + 2][2 lanes]
+  float* hpart;   // [9][nt][nc][Vc][4] hop partials of the stencil
+  unsigned* bar;  // [2]: count, generation
+  int* err;
+  int* iters;  // [1] Arnoldi steps done
+  int G, Gt;
+  int NS;  // stride of the per-system arrays
+};
+
+__device__ __forceinline__ bool grid_barrier(const CGArgs& p) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = p.bar + 1;
+    unsigned g0 = *vgen;
+    __threadfence();
+    unsigned prev = atomicAdd(p.bar, 1u);
+    if (prev == (unsigned)p.G - 1) {
+      atomicExch(p.bar, 0u);
+      __threadfence();
+      atomicAdd(p.bar + 1, 1u);
+    } else {
+      long long t0 = clock64();
+      while (*vgen == g0) {
+        if (clock64() - t0 > 2000000000LL) {  // about one second at 2 GHz
+          atomicExch(p.err, 1);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)p.err == 0;
+}
+
+// loads of data written by other CTAs of this launch go through L2 (__ldcg), never a stale L1 line
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+template <typename T>
+__device__ __forceinline__ T ldx(const T* p) {
+  return __ldcg(p);
+}
+
+__device__ __forceinline__ void cfma(float4& acc, float ar, float ai, const float4& v) {
+  // acc (2 lanes, re0 re1 im0 im1) += (ar + i ai) * v
+  acc.x += ar * v.x - ai * v.z;
+  acc.y += ar * v.y - ai * v.w;
+  acc.z += ar * v.z + ai * v.x;
+  acc.w += ar * v.w + ai * v.y;
+}
+
+// Stencil phase A: hop partials hpart[h][t][i][a] = sum_j A_h(a)[i][j] in[t][j][a + h].
+// One warp per task (site a, hop h, chunk of CG_TCH tiles); lane l owns rows l and l + 32.
+// Stencil loads are coalesced over rows; the vector loads are warp-wide broadcasts from L2;
+// eight columns are in flight at a time. No CTA-wide synchronisation.
+__device__ void cg_apply_partials(const CGArgs& p, const float* in, float4* wsm) {
+  const int nc = p.nc;
+  const int lane = threadIdx.x & 31;
+  const int nchunk = (p.nt + CG_TCH - 1) / CG_TCH;
+  const int64_t ntask = (int64_t)9 * p.Vc * nchunk;
+  const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)p.G * (blockDim.x >> 5);
+  float4* xw = wsm + (threadIdx.x >> 5) * (CG_MAXNC * CG_TCH);  // this warp's staging slice
+  const bool r1 = lane + 32 < nc;
+  for (int64_t task = wid; task < ntask; task += nw) {
+    const int ch = (int)(task % nchunk);
+    const int64_t ha = task / nchunk;
+    const int h = (int)(ha % 9);
+    const int64_t a = ha / 9;
+    const int t0 = ch * CG_TCH;
+    const int ntc = p.nt - t0 < CG_TCH ? p.nt - t0 : CG_TCH;
+    int64_t nb = a;
+    if (h > 0) {
+      int c[4];
+      site_coords(a, p.L, c);
+      const int nu = (h - 1) / 2, dir = ((h - 1) & 1) ? -1 : 1;
+      c[nu] = (c[nu] + dir + p.L[nu]) % p.L[nu];
+      nb = site_index(c, p.L);
+    }
+    // stage the neighbour's vector entries of this tile chunk (independent loads)
+    __syncwarp();
+    for (int q = lane; q < nc * ntc; q += 32) {
+      const int j = q / ntc, u = q - j * ntc;
+      xw[j * CG_TCH + u] = ld4(in + ((((int64_t)(t0 + u) * nc + j) * p.Vc) + nb) * 4);
+    }
+    __syncwarp();
+    const float2* Ab = p.A + ((int64_t)h * p.Vc + a) * nc * nc;  // column-major block
+    float4 acc0[CG_TCH], acc1[CG_TCH];
+#pragma unroll
+    for (int u = 0; u < CG_TCH; ++u) {
+      acc0[u] = make_float4(0, 0, 0, 0);
+      acc1[u] = make_float4(0, 0, 0, 0);
+    }
+    for (int j0 = 0; j0 < nc; j0 += CG_ABATCH) {
+      float2 m0[CG_ABATCH], m1[CG_ABATCH];
+#pragma unroll
+      for (int k = 0; k < CG_ABATCH; ++k) {
+        const int j = j0 + k;
+        const bool ok = j < nc;
+        m0[k] = ok && lane < nc ? __ldg(Ab + (int64_t)j * nc + lane) : make_float2(0, 0);
+        m1[k] = ok && r1 ? __ldg(Ab + (int64_t)j * nc + lane + 32) : make_float2(0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < CG_ABATCH; ++k) {
+        const int j = j0 + k;
+        if (j < nc) {
+#pragma unroll
+          for (int u = 0; u < CG_TCH; ++u) {
+            if (u < ntc) {
+              const float4 v = xw[j * CG_TCH + u];
+              cfma(acc0[u], m0[k].x, m0[k].y, v);
+              cfma(acc1[u], m1[k].x, m1[k].y, v);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CG_TCH; ++u) {
+      if (u < ntc) {
+        const int t = t0 + u;
+        if (lane < nc) st4(p.hpart + ((((int64_t)h * p.nt + t) * nc + lane) * p.Vc + a) * 4, acc0[u]);
+        if (r1) st4(p.hpart + ((((int64_t)h * p.nt + t) * nc + lane + 32) * p.Vc + a) * 4, acc1[u]);
+      }
+    }
+  }
+}
+
+// Stencil phase B (owner entries): out = sc_n (sum_h hpart[h] + i dmu mu_n gamma5_c in)
+__device__ void cg_apply_sum(const CGArgs& p, const float* in, float* out, int tile, int64_t e0, int64_t estep) {
+  const int nc = p.nc;
+  const int n0 = 2 * tile, n1 = 2 * tile + 1;
+  float m0 = 0, m1 = 0, s0 = 0, s1 = 0;
+  if (n0 < p.nsys) { m0 = (float)(p.dmu * p.mu[n0]); s0 = (float)ldx(p.sc + n0); }
+  if (n1 < p.nsys) { m1 = (float)(p.dmu * p.mu[n1]); s1 = (float)ldx(p.sc + n1); }
+  const int64_t toff = (int64_t)tile * p.M * 4;
+  const int64_t hstride = (int64_t)p.nt * p.M * 4;
+  for (int64_t e = e0; e < p.M; e += estep) {
+    float4 hv[9];
+#pragma unroll
+    for (int h = 0; h < 9; ++h) hv[h] = ld4(p.hpart + h * hstride + toff + e * 4);
+    const float4 xv = ld4(in + toff + e * 4);
+    float4 s = hv[0];
+#pragma unroll
+    for (int h = 1; h < 9; ++h) {
+      s.x += hv[h].x; s.y += hv[h].y; s.z += hv[h].z; s.w += hv[h].w;
+    }
+    const int i = (int)(e / p.Vc);
+    const float g5 = i < nc / 2 ? 1.f : -1.f;
+    float4 o;
+    o.x = s0 * (s.x - g5 * m0 * xv.z);
+    o.y = s1 * (s.y - g5 * m1 * xv.w);
+    o.z = s0 * (s.z + g5 * m0 * xv.x);
+    o.w = s1 * (s.w + g5 * m1 * xv.y);
+    st4(out + toff + e * 4, o);
+  }
+}
+
+// CTA-wide sum of nv float4 values per thread into FP64 partials part[b][slot0 + v][lane]
+__device__ void cta_reduce_store(const CGArgs& p, float4* vals, int nv, int slot0, double* sm) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int v = 0; v < nv; ++v) {
+    float4 x = vals[v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x.x += __shfl_xor_sync(0xffffffffu, x.x, o);
+      x.y += __shfl_xor_sync(0xffffffffu, x.y, o);
+      x.z += __shfl_xor_sync(0xffffffffu, x.z, o);
+      x.w += __shfl_xor_sync(0xffffffffu, x.w, o);
+    }
+    if (lane == 0) {
+      double* s = sm + (warp * CG_IVEC + v) * 4;
+      s[0] = x.x; s[1] = x.y; s[2] = x.z; s[3] = x.w;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nv * 4) {
+    const int v = threadIdx.x / 4, q = threadIdx.x % 4;
+    double s = 0;
+    for (int w = 0; w < CG_THREADS / 32; ++w) s += sm[(w * CG_IVEC + v) * 4 + q];
+    // q: 0 = re lane 0, 1 = re lane 1, 2 = im lane 0, 3 = im lane 1; stored as (re, im) per lane
+    double* dst = reinterpret_cast<double*>(p.part + ((int64_t)blockIdx.x * (p.m + 2) + slot0 + v) * 2);
+    const int ln = q & 1, ri = q >> 1;
+    dst[ln * 2 + ri] = s;
+  }
+  __syncthreads();
+}
+
+// sum of the partials of slot i for system n over the slices of its tile (fixed order;
+// loads issued eight at a time)
+__device__ double2 part_sum(const CGArgs& p, int i, int n) {
+  const int t = n / 2, ln = n % 2;
+  double2 s = make_double2(0, 0);
+  for (int sl0 = 0; sl0 < p.Gt; sl0 += 8) {
+    double2 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int sl = sl0 + k;
+      v[k] = sl < p.Gt ? ldx(p.part + ((int64_t)(sl * p.nt + t) * (p.m + 2) + i) * 2 + ln) : make_double2(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      s.x += v[k].x;
+      s.y += v[k].y;
+    }
+  }
+  return s;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+
+// Givens step for system n at Arnoldi step j, with H[j+1][j] = hn
+__device__ void givens_step(const CGArgs& p, int n, int j, double hn, int total) {
+  const int NS = p.NS, m = p.m;
+  double2* col = p.H + (int64_t)j * (m + 1) * NS;
+  double2 cv[CG_MAXM + 1];
+  double c_[CG_MAXM];
+  double2 s_[CG_MAXM];
+  for (int i = 0; i <= j; ++i) cv[i] = ldx(col + i * NS + n);  // independent loads
+  for (int i = 0; i < j; ++i) {
+    c_[i] = p.cs[i * NS + n];
+    s_[i] = p.sn[i * NS + n];
+  }
+  cv[j + 1] = make_double2(hn, 0);
+  for (int i = 0; i < j; ++i) {
+    const double2 a = cv[i], bb = cv[i + 1];
+    const double2 t = cmul(s_[i], bb);
+    cv[i] = make_double2(c_[i] * a.x + t.x, c_[i] * a.y + t.y);
+    const double2 u = cmul(conjd(s_[i]), a);
+    cv[i + 1] = make_double2(c_[i] * bb.x - u.x, c_[i] * bb.y - u.y);
+  }
+  const double2 a = cv[j];
+  const double na = hypot(a.x, a.y), nb = hn;
+  const double r = hypot(na, nb);
+  double c;
+  double2 sn;
+  if (r == 0.0) {
+    c = 1.0;
+    sn = make_double2(0, 0);
+  } else if (na == 0.0) {
+    c = 0.0;
+    sn = make_double2(1, 0);
+  } else {
+    c = na / r;  // s = (a / |a|) conj(b) / r with b = hn real
+    sn = make_double2(a.x / na * (nb / r), a.y / na * (nb / r));
+  }
+  cv[j] = na == 0.0 ? make_double2(r, 0) : make_double2(a.x / na * r, a.y / na * r);
+  cv[j + 1] = make_double2(0, 0);
+  for (int i = 0; i <= j + 1; ++i) col[i * NS + n] = cv[i];
+  p.cs[j * NS + n] = c;
+  p.sn[j * NS + n] = sn;
+  const double2 gj = p.g[j * NS + n];
+  const double2 t = cmul(conjd(sn), gj);
+  p.g[(j + 1) * NS + n] = make_double2(-t.x, -t.y);
+  p.g[j * NS + n] = make_double2(c * gj.x, c * gj.y);
+  const double res = hypot(t.x, t.y);
+  if (!(res > p.tolabs[n]) || nb == 0.0) {
+    p.kconv[n] = j + 1;
+    p.active[n] = 0;
+    p.done[n] = 1;
+  } else if (j + 1 == m || total + 1 >= p.maxiter) {
+    p.kconv[n] = j + 1;
+    p.active[n] = 0;
+  }
+}
+
+// y = R^{-1} g for system n: the CTA stages R in shared memory, warp 0 substitutes
+__device__ void backsub(const CGArgs& p, int n, double2* Rs) {
+  const int NS = p.NS, m = p.m;
+  const int k = ldx(p.kconv + n);
+  for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
+    const int i = q % k, l = q / k;  // row i, column l
+    Rs[l * k + i] = i <= l ? ldx(p.H + ((int64_t)l * (m + 1) + i) * NS + n) : make_double2(0, 0);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double2 s0 = lane < k ? ldx(p.g + lane * NS + n) : make_double2(0, 0);
+    double2 s1 = lane + 32 < k ? ldx(p.g + (lane + 32) * NS + n) : make_double2(0, 0);
+    for (int i = m - 1; i >= k; --i)
+      if (lane == 0) p.y[i * NS + n] = make_double2(0, 0);
+    for (int i = k - 1; i >= 0; --i) {
+      const double2 si = i < 32 ? make_double2(__shfl_sync(0xffffffffu, s0.x, i), __shfl_sync(0xffffffffu, s0.y, i))
+                                : make_double2(__shfl_sync(0xffffffffu, s1.x, i - 32),
+                                               __shfl_sync(0xffffffffu, s1.y, i - 32));
+      const double2 d = Rs[i * k + i];
+      const double den = d.x * d.x + d.y * d.y;
+      const double2 yi = den > 0 ? make_double2((si.x * d.x + si.y * d.y) / den, (si.y * d.x - si.x * d.y) / den)
+                                 : make_double2(0, 0);
+      if (lane == 0) p.y[i * NS + n] = yi;
+      if (lane < i) {
+        const double2 t = cmul(Rs[i * k + lane], yi);
+        s0.x -= t.x;
+        s0.y -= t.y;
+      }
+      if (lane + 32 < i) {
+        const double2 t = cmul(Rs[i * k + lane + 32], yi);
+        s1.x -= t.x;
+        s1.y -= t.y;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs p) {
+  __shared__ double sm[(CG_THREADS / 32) * CG_IVEC * 4];
+  __shared__ float4 hsm[CG_MAXM + 1];  // H column (or y) of this CTA's two systems
+  extern __shared__ float4 dyn[];
+  const int b = blockIdx.x;
+  const int tile = b % p.nt;
+  const int slice = b / p.nt;
+  const int64_t toff = (int64_t)tile * p.M * 4;
+  const int64_t e0 = (int64_t)slice * CG_THREADS + threadIdx.x;
+  const int64_t estep = (int64_t)p.Gt * CG_THREADS;
+  const int NS = p.NS;
+  const int gtid = b * CG_THREADS + threadIdx.x;
+  const int m = p.m;
+  const int n0 = 2 * tile, n1 = 2 * tile + 1;
+
+  // ---- start: x = 0, V0 = rc, |rc| per system
+  {
+    float4 nrm = make_float4(0, 0, 0, 0);
+    for (int64_t e = e0; e < p.M; e += estep) {
+      const float4 r = ld4(p.rc + toff + e * 4);
+      st4(p.V + toff + e * 4, r);
+      st4(p.xc + toff + e * 4, make_float4(0, 0, 0, 0));
+      nrm.x += r.x * r.x + r.z * r.z;
+      nrm.y += r.y * r.y + r.w * r.w;
+    }
+    cta_reduce_store(p, &nrm, 1, 0, sm);
+  }
+  if (!grid_barrier(p)) return;
+  // norms sit in the real slot of each lane's partial (see cta_reduce_store)
+  if (gtid < p.nsys) {
+    const int n = gtid;
+    const double2 s = part_sum(p, 0, n);
+    const double beta = sqrt(fmax(s.x, 0.0));
+    p.tolabs[n] = p.tol * beta;
+    const bool on = beta > 0.0 && isfinite(beta);
+    p.active[n] = on;
+    p.done[n] = !on;
+    p.sc[n] = on ? 1.0 / beta : 0.0;
+    for (int i = 0; i <= m; ++i) p.g[i * NS + n] = make_double2(0, 0);
+    p.g[n] = make_double2(on ? beta : 0.0, 0);
+    p.kconv[n] = 0;
+  }
+  if (!grid_barrier(p)) return;
+
+  int total = 0;
+  while (true) {
+    int j = 0;
+    for (; j < m && total < p.maxiter; ++j) {
+      // P1: V_{j+1} = sc * A V_j   (V_j not yet scaled in place)
+      cg_apply_partials(p, p.V + (int64_t)j * p.vstride, dyn);
+      if (!grid_barrier(p)) return;
+      cg_apply_sum(p, p.V + (int64_t)j * p.vstride, p.V + (int64_t)(j + 1) * p.vstride, tile, e0, estep);
+      // (P2 below touches only this thread's entries of V_j and V_{j+1}: no barrier needed)
+      // P2: scale V_j in place (owner entries), then dots <V_i, w> for i <= j
+      {
+        float s0 = 0, s1 = 0;
+        if (n0 < p.nsys) s0 = (float)ldx(p.sc + n0);
+        if (n1 < p.nsys) s1 = (float)ldx(p.sc + n1);
+        float* vj = p.V + (int64_t)j * p.vstride + toff;
+        for (int64_t e = e0; e < p.M; e += estep) {
+          float4 v = ld4(vj + e * 4);
+          v.x *= s0; v.y *= s1; v.z *= s0; v.w *= s1;
+          st4(vj + e * 4, v);
+        }
+        const float* w = p.V + (int64_t)(j + 1) * p.vstride + toff;
+        for (int i0 = 0; i0 <= j; i0 += CG_IVEC) {
+          const int ni = j + 1 - i0 < CG_IVEC ? j + 1 - i0 : CG_IVEC;
+          float4 acc[CG_IVEC];
+#pragma unroll
+          for (int u = 0; u < CG_IVEC; ++u) acc[u] = make_float4(0, 0, 0, 0);
+          for (int64_t eb = e0; eb < p.M; eb += CG_EPT * estep) {
+            float4 ww[CG_EPT];
+#pragma unroll
+            for (int q = 0; q < CG_EPT; ++q) {
+              const int64_t e = eb + q * estep;
+              ww[q] = e < p.M ? ld4(w + e * 4) : make_float4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < CG_IVEC; ++u) {
+              if (u < ni) {
+                const float* vu = p.V + (int64_t)(i0 + u) * p.vstride + toff;
+#pragma unroll
+                for (int q = 0; q < CG_EPT; ++q) {
+                  const int64_t e = eb + q * estep;
+                  if (e < p.M) {
+                    const float4 v = ld4(vu + e * 4);
+                    // conj(v) w per lane
+                    acc[u].x += v.x * ww[q].x + v.z * ww[q].z;
+                    acc[u].y += v.y * ww[q].y + v.w * ww[q].w;
+                    acc[u].z += v.x * ww[q].z - v.z * ww[q].x;
+                    acc[u].w += v.y * ww[q].w - v.w * ww[q].y;
+                  }
+                }
+              }
+            }
+          }
+          cta_reduce_store(p, acc, ni, i0, sm);
+        }
+      }
+      if (!grid_barrier(p)) return;
+      // P3: H[i][j] = sum of partials (one thread per (i, n))
+      if (gtid < (j + 1) * p.nsys) {
+        const int i = gtid / p.nsys, n = gtid % p.nsys;
+        p.H[((int64_t)j * (m + 1) + i) * NS + n] = part_sum(p, i, n);
+      }
+      if (!grid_barrier(p)) return;
+      // P4: w -= sum_i H[i][j] V_i (owner entries) and |w|^2 partials
+      {
+        if (threadIdx.x <= j) {
+          const int i = threadIdx.x;
+          const double2 h0 = n0 < p.nsys ? ldx(p.H + ((int64_t)j * (m + 1) + i) * NS + n0) : make_double2(0, 0);
+          const double2 h1 = n1 < p.nsys ? ldx(p.H + ((int64_t)j * (m + 1) + i) * NS + n1) : make_double2(0, 0);
+          hsm[i] = make_float4((float)h0.x, (float)h0.y, (float)h1.x, (float)h1.y);
+        }
+        __syncthreads();
+        float* w = p.V + (int64_t)(j + 1) * p.vstride + toff;
+        float4 nrm = make_float4(0, 0, 0, 0);
+        for (int64_t eb = e0; eb < p.M; eb += CG_EPT * estep) {
+          float4 ww[CG_EPT];
+#pragma unroll
+          for (int q = 0; q < CG_EPT; ++q) {
+            const int64_t e = eb + q * estep;
+            ww[q] = e < p.M ? ld4(w + e * 4) : make_float4(0, 0, 0, 0);
+          }
+          for (int i0 = 0; i0 <= j; i0 += CG_IVEC) {
+#pragma unroll
+            for (int u = 0; u < CG_IVEC; ++u) {
+              if (i0 + u <= j) {
+                const float4 h = hsm[i0 + u];
+                const float* vu = p.V + (int64_t)(i0 + u) * p.vstride + toff;
+#pragma unroll
+                for (int q = 0; q < CG_EPT; ++q) {
+                  const int64_t e = eb + q * estep;
+                  if (e < p.M) {
+                    const float4 v = ld4(vu + e * 4);
+                    ww[q].x -= h.x * v.x - h.y * v.z;
+                    ww[q].z -= h.x * v.z + h.y * v.x;
+                    ww[q].y -= h.z * v.y - h.w * v.w;
+                    ww[q].w -= h.z * v.w + h.w * v.y;
+                  }
+                }
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < CG_EPT; ++q) {
+            const int64_t e = eb + q * estep;
+            if (e < p.M) {
+              st4(w + e * 4, ww[q]);
+              nrm.x += ww[q].x * ww[q].x + ww[q].z * ww[q].z;
+              nrm.y += ww[q].y * ww[q].y + ww[q].w * ww[q].w;
+            }
+          }
+        }
+        cta_reduce_store(p, &nrm, 1, m + 1, sm);
+      }
+      if (!grid_barrier(p)) return;
+      // P5: H[j+1][j] = |w|, Givens rotation, convergence masks (one thread per system)
+      if (gtid < p.nsys) {
+        const int n = gtid;
+        const double2 s = part_sum(p, m + 1, n);
+        const double hn = sqrt(fmax(s.x, 0.0));
+        p.sc[n] = hn > 0 ? 1.0 / hn : 0.0;
+        if (p.active[n]) givens_step(p, n, j, hn, total);
+      }
+      if (b == 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          int c = 0;
+          for (int n = 0; n < p.nsys; ++n) c += p.active[n];
+          *p.nactive = c;
+        }
+      }
+      ++total;
+      if (!grid_barrier(p)) return;
+      if (*(volatile int*)p.nactive == 0) {
+        ++j;
+        break;
+      }
+    }
+    // y = R^{-1} g per system (a CTA per system), then x += sum_i y_i V_i
+    for (int n = b; n < p.nsys; n += p.G) backsub(p, n, reinterpret_cast<double2*>(dyn));
+    if (!grid_barrier(p)) return;
+    {
+      if (threadIdx.x < j) {
+        const int i = threadIdx.x;
+        const double2 y0 = n0 < p.nsys ? ldx(p.y + i * NS + n0) : make_double2(0, 0);
+        const double2 y1 = n1 < p.nsys ? ldx(p.y + i * NS + n1) : make_double2(0, 0);
+        hsm[i] = make_float4((float)y0.x, (float)y0.y, (float)y1.x, (float)y1.y);
+      }
+      __syncthreads();
+      float* x = p.xc + toff;
+      for (int64_t eb = e0; eb < p.M; eb += CG_EPT * estep) {
+        float4 xx[CG_EPT];
+#pragma unroll
+        for (int q = 0; q < CG_EPT; ++q) {
+          const int64_t e = eb + q * estep;
+          xx[q] = e < p.M ? ld4(x + e * 4) : make_float4(0, 0, 0, 0);
+        }
+        for (int i0 = 0; i0 < j; i0 += CG_IVEC) {
+#pragma unroll
+          for (int u = 0; u < CG_IVEC; ++u) {
+            if (i0 + u < j) {
+              const float4 yv = hsm[i0 + u];
+              const float* vu = p.V + (int64_t)(i0 + u) * p.vstride + toff;
+#pragma unroll
+              for (int q = 0; q < CG_EPT; ++q) {
+                const int64_t e = eb + q * estep;
+                if (e < p.M) {
+                  const float4 v = ld4(vu + e * 4);
+                  xx[q].x += yv.x * v.x - yv.y * v.z;
+                  xx[q].z += yv.x * v.z + yv.y * v.x;
+                  xx[q].y += yv.z * v.y - yv.w * v.w;
+                  xx[q].w += yv.z * v.w + yv.w * v.y;
+                }
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < CG_EPT; ++q) {
+          const int64_t e = eb + q * estep;
+          if (e < p.M) st4(x + e * 4, xx[q]);
+        }
+      }
+    }
+    // restart decision (uniform: done[] was last written before a grid barrier)
+    bool again;
+    {
+      int alldone = 1;
+      for (int n = 0; n < p.nsys; ++n) alldone &= ldx(p.done + n);
+      again = !alldone && total < p.maxiter;
+    }
+    if (!again) break;
+    if (!grid_barrier(p)) return;
+    // restart: V0 = rc - A x, with sc = 1 for the apply
+    if (gtid < p.nsys) p.sc[gtid] = 1.0;
+    if (!grid_barrier(p)) return;
+    cg_apply_partials(p, p.xc, dyn);
+    if (!grid_barrier(p)) return;
+    cg_apply_sum(p, p.xc, p.V, tile, e0, estep);
+    {
+      float4 nrm = make_float4(0, 0, 0, 0);
+      for (int64_t e = e0; e < p.M; e += estep) {
+        const float4 r = ld4(p.rc + toff + e * 4);
+        float4 w = ld4(p.V + toff + e * 4);
+        w.x = r.x - w.x; w.y = r.y - w.y; w.z = r.z - w.z; w.w = r.w - w.w;
+        st4(p.V + toff + e * 4, w);
+        nrm.x += w.x * w.x + w.z * w.z;
+        nrm.y += w.y * w.y + w.w * w.w;
+      }
+      cta_reduce_store(p, &nrm, 1, 0, sm);
+    }
+    if (!grid_barrier(p)) return;
+    if (gtid < p.nsys) {
+      const int n = gtid;
+      const double2 s = part_sum(p, 0, n);
+      const double beta = sqrt(fmax(s.x, 0.0));
+      const bool on = !p.done[n] && beta > p.tolabs[n];
+      if (!on) p.done[n] = 1;
+      p.active[n] = on;
+      p.sc[n] = on ? 1.0 / beta : 0.0;
+      for (int i = 0; i <= m; ++i) p.g[i * NS + n] = make_double2(0, 0);
+      p.g[n] = make_double2(on ? beta : 0.0, 0);
+      p.kconv[n] = 0;
+    }
+    if (!grid_barrier(p)) return;
+  }
+  if (gtid == 0) *p.iters = total;
+}
+
+int CoarseGmres::alloc(int m_, int nsys_, int G_, size_t bundle_bytes) {
+  if (m_ <= m && nsys_ <= NS && G_ <= G && bundle_bytes <= hbytes) return 0;
+  release();
+  m = m_;
+  NS = nsys_;
+  G = G_;
+  hbytes = bundle_bytes;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** q, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(q, bytes);
+  };
+  A((void**)&H, sizeof(double2) * (size_t)(m + 1) * m * NS);
+  A((void**)&cs, sizeof(double) * (size_t)m * NS);
+  A((void**)&sn, sizeof(double2) * (size_t)m * NS);
+  A((void**)&g, sizeof(double2) * (size_t)(m + 1) * NS);
+  A((void**)&y, sizeof(double2) * (size_t)m * NS);
+  A((void**)&tolabs, sizeof(double) * NS);
+  A((void**)&sc, sizeof(double) * NS);
+  A((void**)&kconv, sizeof(int) * NS);
+  A((void**)&active, sizeof(int) * NS);
+  A((void**)&done, sizeof(int) * NS);
+  A((void**)&nactive, sizeof(int));
+  A((void**)&part, sizeof(double2) * (size_t)G * (m + 2) * 2);
+  A((void**)&bar, sizeof(unsigned) * 2);
+  A((void**)&err, sizeof(int));
+  A((void**)&iters, sizeof(int));
+  A((void**)&hpart, 9 * bundle_bytes);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h_flags, sizeof(int) * 2);
+  return e == cudaSuccess ? 0 : -1;
+}
+
+void CoarseGmres::release() {
+  void* ptrs[] = {H, cs, sn, g, y, tolabs, sc, kconv, active, done, nactive, part, bar, err, iters, hpart};
+  for (void* q : ptrs) cudaFree(q);
+  if (h_flags) cudaFreeHost(h_flags);
+  H = nullptr; cs = nullptr; sn = nullptr; g = nullptr; y = nullptr; tolabs = nullptr; sc = nullptr;
+  kconv = nullptr; active = nullptr; done = nullptr; nactive = nullptr; part = nullptr; bar = nullptr;
+  err = nullptr; iters = nullptr; h_flags = nullptr; hpart = nullptr;
+  m = 0; NS = 0; G = 0; hbytes = 0;
+}
+
+static size_t dyn_smem_bytes(int m) {
+  const size_t stage = sizeof(float4) * (size_t)(CG_THREADS / 32) * CG_MAXNC * CG_TCH;  // per-warp vector staging
+  const size_t rs = sizeof(double2) * (size_t)m * m;                                  // back substitution
+  return stage > rs ? stage : rs;
+}
+
+// the largest dynamic shared memory any supported restart length needs
+static size_t dyn_smem_cap() { return dyn_smem_bytes(CG_MAXM); }
+
+int coarse_gmres_grid(int nt) {
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(coarse_gmres_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem_cap());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel, CG_THREADS, dyn_smem_cap());
+    if (per_sm < 1) per_sm = 1;
+  }
+  int want = sms;  // one CTA per SM keeps the barrier short
+  if (want > per_sm * sms) want = per_sm * sms;
+  int Gt = want / nt;
+  if (Gt < 1) Gt = 1;
+  return Gt * nt;
+}
+
+int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, const float* rc, float* xc, float* V,
+                       int64_t vstride, const double* mu, double dmu, int nsys, int m, int maxiter, double tol,
+                       int* iters_done, cudaStream_t st) {
+  const int nt = ntiles(nsys, 2);
+  const int G = coarse_gmres_grid(nt);
+  const size_t need = (size_t)nt * cd.nc * cd.Vc * 4 * sizeof(float);
+  if (G > s.G || m > s.m || nsys > s.NS || m > CG_MAXM || cd.nc > 64 || (cd.nc % 2) || need > s.hbytes) return -2;
+  CGArgs p;
+  p.A = A;
+  for (int k = 0; k < 4; ++k) p.L[k] = cd.L[k];
+  p.Vc = cd.Vc;
+  p.nc = cd.nc;
+  p.rc = rc;
+  p.xc = xc;
+  p.V = V;
+  p.vstride = vstride;
+  p.mu = mu;
+  p.dmu = dmu;
+  p.nsys = nsys;
+  p.nt = nt;
+  p.M = (int64_t)cd.nc * cd.Vc;
+  p.m = m;
+  p.maxiter = maxiter;
+  p.tol = tol;
+  p.H = s.H; p.cs = s.cs; p.sn = s.sn; p.g = s.g; p.y = s.y; p.tolabs = s.tolabs; p.sc = s.sc;
+  p.kconv = s.kconv; p.active = s.active; p.done = s.done; p.nactive = s.nactive; p.part = s.part;
+  p.bar = s.bar; p.err = s.err; p.iters = s.iters; p.hpart = s.hpart;
+  p.G = G;
+  p.Gt = G / nt;
+  p.NS = s.NS;
+  cudaMemsetAsync(s.bar, 0, sizeof(unsigned) * 2, st);
+  cudaMemsetAsync(s.err, 0, sizeof(int), st);
+  void* args[] = {&p};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)coarse_gmres_kernel, dim3(G), dim3(CG_THREADS), args,
+                                              dyn_smem_bytes(m), st);
+  TM_COUNT();
+  if (e != cudaSuccess) return -1;
+  cudaMemcpyAsync(s.h_flags, s.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(s.h_flags + 1, s.iters, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (iters_done) {
+    cudaStreamSynchronize(st);
+    *iters_done = s.h_flags[1];
+    if (s.h_flags[0]) return -3;
+  }
+  return 0;
+}
+
+}  // namespace tmamg

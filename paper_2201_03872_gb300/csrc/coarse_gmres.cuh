@@ -1,0 +1,31 @@
+// Persistent coarse-level GMRES (declarations). See coarse_gmres.cu.
+#pragma once
+#include "amg.cuh"
+
+namespace tmamg {
+
+struct CoarseGmres {
+  int m = 0, NS = 0, G = 0;
+  double2 *H = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *part = nullptr;
+  double *cs = nullptr, *tolabs = nullptr, *sc = nullptr;
+  int *kconv = nullptr, *active = nullptr, *done = nullptr, *nactive = nullptr, *err = nullptr, *iters = nullptr;
+  unsigned* bar = nullptr;
+  int* h_flags = nullptr;
+  float* hpart = nullptr;  // 9 coarse bundles: hop partials of the stencil
+  size_t hbytes = 0;       // bytes of one coarse bundle the partials are sized for
+  int alloc(int m, int nsys, int G, size_t bundle_bytes);
+  void release();
+};
+
+// grid size (CTAs) used for nt coarse tiles: a multiple of nt, at most one wave
+int coarse_gmres_grid(int nt);
+
+// xc ~ D_c(dmu mu)^{-1} rc by restarted GMRES(m) to |r| <= tol |rc| per system, at most
+// maxiter Arnoldi steps, in one cooperative launch. V: m + 1 coarse bundles (vstride floats
+// apart). If iters_done is non-null the call synchronises the stream and returns -3 when a
+// grid barrier timed out, else 0; -1 if the launch failed, -2 if the state is too small.
+int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, const float* rc, float* xc, float* V,
+                       int64_t vstride, const double* mu, double dmu, int nsys, int m, int maxiter, double tol,
+                       int* iters_done, cudaStream_t st);
+
+}  // namespace tmamg

@@ -13,6 +13,7 @@
 
 #include "amg.cuh"
 #include "blas.cuh"
+#include "coarse_gmres.cuh"
 #include "krylov.cuh"
 #include "sap.cuh"
 
@@ -32,6 +33,7 @@ struct Workspace {
   float* Vc = nullptr;  // mc + 1 coarse bundles
   float *xc = nullptr, *rc = nullptr;
   GmresState top, coarse;
+  CoarseGmres cg;
   double *rel_top = nullptr, *rel_coarse = nullptr, *rn = nullptr, *bn = nullptr, *scale = nullptr;
   double *beta0 = nullptr, *tmpd = nullptr;
   double2 *ones = nullptr, *mones = nullptr, *dot = nullptr, *partial64 = nullptr;
@@ -52,6 +54,7 @@ static void ws_free(Workspace* w) {
   if (w->h_count) cudaFreeHost(w->h_count);
   w->top.release();
   w->coarse.release();
+  w->cg.release();
   *w = Workspace();
 }
 
@@ -128,6 +131,8 @@ static int ensure_ws(tmamg_ctx* ctx, int nsys, int m, int mc) {
   if (w->top.alloc(mm, ns, partial_elems(12 * V, ns, mm + 1, 2))) return set_err(ctx, TMAMG_ERR_OOM, "gmres state");
   if (w->coarse.alloc(mcc, ns, partial_elems((int64_t)nc * Vc, ns, mcc + 1, 2)))
     return set_err(ctx, TMAMG_ERR_OOM, "gmres state");
+  // the grid for one tile is the largest any system count uses
+  if (w->cg.alloc(mcc, ns, coarse_gmres_grid(1), w->cb32)) return set_err(ctx, TMAMG_ERR_OOM, "coarse gmres state");
   fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->ones, ns, 1.0); TM_COUNT();
   fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->mones, ns, -1.0); TM_COUNT();
   return check_cuda(ctx, cudaGetLastError(), "workspace init");
@@ -307,6 +312,8 @@ struct SolveCtx {
   int nsys;
   const double* mu;  // device, per system
   int coarse_iters = 0;
+  bool timeout = false;       // a bounded device wait gave up
+  bool launch_error = false;  // a cooperative launch was refused
 };
 
 __global__ void restart_tol_kernel(const double2* dot, const double* beta0, double tol, double* rel, int n) {
@@ -328,6 +335,17 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
   cudaStream_t st = ctx->stream;
   const CoarseLevel& L1 = ctx->levels[0];
   CoarseDims cd = coarse_dims(L1);
+  if (S.sp->coarse_solver == 0) {
+    // persistent kernel: the whole restarted GMRES in one cooperative launch
+    int it = 0;
+    int rc_ = coarse_gmres_solve(w->cg, cd, L1.A, rc, xc, w->Vc, (int64_t)(w->cb32 / sizeof(float)), S.mu,
+                                 S.sp->delta_mu, S.nsys, S.sp->coarse_restart, S.sp->coarse_maxiter,
+                                 S.sp->coarse_tol, &it, st);
+    if (rc_ == -3) S.timeout = true;
+    if (rc_ == -1 || rc_ == -2) S.launch_error = true;
+    S.coarse_iters += it;
+    return;
+  }
   const int64_t M = (int64_t)cd.nc * cd.Vc;
   const int nsys = S.nsys;
   const int mc = S.sp->coarse_restart;
@@ -429,12 +447,13 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   cudaStream_t st = ctx->stream;
   const Geom& g = ctx->g;
   const int nsys = nrhs * nshift;
-  if (nsys > 1024) return set_err(ctx, TMAMG_ERR_ARG, "solve: at most 1024 systems per call");
+  if (nsys > 256) return set_err(ctx, TMAMG_ERR_ARG, "solve: at most 256 systems per call");
   if (sp->restart < 1 || sp->restart > 64 || sp->coarse_restart < 1 || sp->coarse_restart > 128 ||
       sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: bad parameters");
   if (sp->precision != 32) return set_err(ctx, TMAMG_ERR_ARG, "solve: precision 64 path not available yet");
-  if (sp->coarse_solver != 0) return set_err(ctx, TMAMG_ERR_ARG, "solve: block coarse solver not available yet");
+  if (sp->coarse_solver != 0 && sp->coarse_solver != 2)
+    return set_err(ctx, TMAMG_ERR_ARG, "solve: coarse_solver must be 0 (persistent GMRES) or 2 (per-step launches)");
   int rc = ensure_ws(ctx, nsys, sp->restart, sp->coarse_restart);
   if (rc) return rc;
   Workspace* w = ctx->ws;
@@ -512,6 +531,8 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   cudaFree(bstage);
   cudaFree(xstage);
   if (!rc) rc = check_cuda(ctx, se, "solve");
+  if (!rc && S.launch_error) rc = set_err(ctx, TMAMG_ERR_CUDA, "solve: cooperative coarse-solver launch failed");
+  if (!rc && S.timeout) rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "solve: a coarse-solver grid barrier timed out");
   if (rc) return rc;
   int all_ok = 1;
   for (int n = 0; n < nsys; ++n) {

@@ -200,6 +200,15 @@ int tmamg_prolong(tmamg_ctx* ctx, int level, const void* coarse_bundle, void* fi
  * i mu_n gamma5_c, paper Sec. 2 and Fig. 6 caption with delta mu = 1). mu: host [nsys]. */
 int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_bundle, int nsys, const double* mu);
 
+/* xc ~ D_c(delta_mu mu_k)^{-1} rc on coarse level 1 by the coarse solver selected in p
+ * (p->coarse_solver: 0 persistent GMRES, 1 block GMRES per shift, 2 GMRES with one launch
+ * per step; paper Sec. 4), to the relative residual p->coarse_tol per system, restart
+ * p->coarse_restart, at most p->coarse_maxiter steps, zero start. Systems n = r * nshift + k
+ * (r < nrhs, k < nshift); mu: host [nshift]; rc, xc: coarse bundles of nrhs * nshift
+ * systems. iterations (optional): steps taken. Synchronises the stream. */
+int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* xc_bundle, int nrhs, const double* mu,
+                       int nshift, const tmamg_solve_params* p, int* iterations);
+
 #ifdef __cplusplus
 }
 #endif

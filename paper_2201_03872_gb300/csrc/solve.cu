@@ -13,6 +13,7 @@
 
 #include "amg.cuh"
 #include "blas.cuh"
+#include "block_gmres.cuh"
 #include "coarse_gmres.cuh"
 #include "krylov.cuh"
 #include "sap.cuh"
@@ -34,6 +35,8 @@ struct Workspace {
   float *xc = nullptr, *rc = nullptr;
   GmresState top, coarse;
   CoarseGmres cg;
+  BlockGmres bg;
+  float* tc = nullptr;  // one more coarse bundle
   double *rel_top = nullptr, *rel_coarse = nullptr, *rn = nullptr, *bn = nullptr, *scale = nullptr;
   double *beta0 = nullptr, *tmpd = nullptr;
   double2 *ones = nullptr, *mones = nullptr, *dot = nullptr, *partial64 = nullptr;
@@ -55,6 +58,8 @@ static void ws_free(Workspace* w) {
   w->top.release();
   w->coarse.release();
   w->cg.release();
+  w->bg.release();
+  cudaFree(w->tc);
   *w = Workspace();
 }
 
@@ -105,6 +110,7 @@ static int ensure_ws(tmamg_ctx* ctx, int nsys, int m, int mc) {
   A((void**)&w->Vc, w->cb32 * (mcc + 1));
   A((void**)&w->xc, w->cb32);
   A((void**)&w->rc, w->cb32);
+  A((void**)&w->tc, w->cb32);
   const size_t d = sizeof(double) * ns;
   A((void**)&w->rel_top, d);
   A((void**)&w->rel_coarse, d);
@@ -314,6 +320,7 @@ struct SolveCtx {
   int coarse_iters = 0;
   bool timeout = false;       // a bounded device wait gave up
   bool launch_error = false;  // a cooperative launch was refused
+  int nshift = 1;             // systems n = r * nshift + k (block GMRES groups the rhs of shift k)
 };
 
 __global__ void restart_tol_kernel(const double2* dot, const double* beta0, double tol, double* rel, int n) {
@@ -343,6 +350,24 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
                                  S.sp->coarse_tol, &it, st);
     if (rc_ == -3) S.timeout = true;
     if (rc_ == -1 || rc_ == -2) S.launch_error = true;
+    S.coarse_iters += it;
+    return;
+  }
+  if (S.sp->coarse_solver == 1) {
+    // block GMRES: one Krylov space per shift over that shift's right-hand sides
+    const int64_t M = (int64_t)cd.nc * cd.Vc;
+    if (w->bg.alloc(S.sp->coarse_restart, S.nsys, S.nshift, M)) {
+      S.launch_error = true;
+      return;
+    }
+    const double dmu = S.sp->delta_mu;
+    const double* mu = S.mu;
+    const int nsys = S.nsys;
+    auto apply = [&, dmu, mu, nsys](const float* x, float* y) { coarse_apply(cd, L1.A, x, y, mu, dmu, nsys, st); };
+    int it = 0;
+    int rc_ = block_gmres_solve(w->bg, apply, rc, xc, w->Vc, (int64_t)(w->cb32 / sizeof(float)), w->tc, w->cb32,
+                                S.sp->coarse_restart, S.sp->coarse_maxiter, S.sp->coarse_tol, &it, st);
+    if (rc_) S.launch_error = true;
     S.coarse_iters += it;
     return;
   }
@@ -452,8 +477,10 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
       sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: bad parameters");
   if (sp->precision != 32) return set_err(ctx, TMAMG_ERR_ARG, "solve: precision 64 path not available yet");
-  if (sp->coarse_solver != 0 && sp->coarse_solver != 2)
-    return set_err(ctx, TMAMG_ERR_ARG, "solve: coarse_solver must be 0 (persistent GMRES) or 2 (per-step launches)");
+  if (sp->coarse_solver < 0 || sp->coarse_solver > 2)
+    return set_err(ctx, TMAMG_ERR_ARG, "solve: coarse_solver must be 0, 1 or 2");
+  if (sp->coarse_solver == 1 && nrhs > 16)
+    return set_err(ctx, TMAMG_ERR_ARG, "solve: block GMRES takes at most 16 right-hand sides per shift");
   int rc = ensure_ws(ctx, nsys, sp->restart, sp->coarse_restart);
   if (rc) return rc;
   Workspace* w = ctx->ws;
@@ -483,6 +510,7 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   mdot<double>(w->b64, 0, 1, w->b64, M, nsys, w->dot, nsys, w->partial64, st);
   sqrt_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->bn, nsys); TM_COUNT();
   SolveCtx S{ctx, sp, nsys, ctx->mu_dev, 0};
+  S.nshift = nshift;
   LevelOps fine;
   fine.M = M;
   fine.A = [&](const float* xx, float* yy) { launch_dirac<float>(g, ctx->U32, ctx->C32, xx, yy, ctx->mu_dev, nsys, st); };
@@ -624,6 +652,32 @@ int tmamg_prolong(tmamg_ctx* ctx, int level, const void* coarse_bundle, void* fi
   prolong_vec(agg_dims(ctx->g, l.agg), l.P, (const float*)coarse_bundle, (float*)fine_bundle, l.nv, 6, nsys, 0,
               ctx->stream);
   return check_cuda(ctx, cudaGetLastError(), "prolong launch");
+}
+
+int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* xc_bundle, int nrhs, const double* mu,
+                       int nshift, const tmamg_solve_params* p, int* iterations) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "coarse_solve: no setup");
+  if (level != 1 || !rc_bundle || !xc_bundle || !mu || nrhs < 1 || nshift < 1 || !p || rc_bundle == xc_bundle)
+    return set_err(ctx, TMAMG_ERR_ARG, "coarse_solve: bad argument");
+  const int nsys = nrhs * nshift;
+  if (nsys > 256 || p->coarse_solver < 0 || p->coarse_solver > 2 || (p->coarse_solver == 1 && nrhs > 16) ||
+      p->coarse_restart < 1 || p->coarse_restart > 64 || p->coarse_maxiter < 1)
+    return set_err(ctx, TMAMG_ERR_ARG, "coarse_solve: bad parameters");
+  int rc = ensure_ws(ctx, nsys, p->restart, p->coarse_restart);
+  if (rc) return rc;
+  std::vector<double> musys(nsys);
+  for (int n = 0; n < nsys; ++n) musys[n] = mu[n % nshift];
+  rc = upload_mu(ctx, musys.data(), nsys);
+  if (rc) return rc;
+  SolveCtx S{ctx, p, nsys, ctx->mu_dev, 0};
+  S.nshift = nshift;
+  coarse_solve(S, (const float*)rc_bundle, (float*)xc_bundle);
+  rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "coarse_solve");
+  if (!rc && S.launch_error) rc = set_err(ctx, TMAMG_ERR_CUDA, "coarse_solve: launch failed");
+  if (!rc && S.timeout) rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "coarse_solve: a grid barrier timed out");
+  if (iterations) *iterations = S.coarse_iters;
+  return rc;
 }
 
 int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_bundle, int nsys, const double* mu) {

@@ -87,6 +87,7 @@ SIGNATURES = {
     "tmamg_restrict": (I, [P, I, P, P, I]),
     "tmamg_prolong": (I, [P, I, P, P, I]),
     "tmamg_coarse_apply": (I, [P, I, P, P, I, P]),
+    "tmamg_coarse_solve": (I, [P, I, P, P, I, P, I, ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_int)]),
 }
 
 
@@ -274,3 +275,13 @@ def tmamg_coarse_apply(ctx, level, x_bundle, y_bundle, nsys, mu):
     m = _f64(mu)
     return _check("tmamg_coarse_apply", ctx, lib().tmamg_coarse_apply(ctx, int(level), _ptr(x_bundle),
                                                                       _ptr(y_bundle), int(nsys), _ptr(m)))
+
+
+def tmamg_coarse_solve(ctx, level, rc_bundle, xc_bundle, nrhs, mu, nshift, params):
+    """Returns the number of coarse iterations taken."""
+    m = _f64(mu)
+    it = ctypes.c_int(0)
+    _check("tmamg_coarse_solve", ctx, lib().tmamg_coarse_solve(ctx, int(level), _ptr(rc_bundle), _ptr(xc_bundle),
+                                                                int(nrhs), _ptr(m), int(nshift), ctypes.byref(params),
+                                                                ctypes.byref(it)))
+    return it.value

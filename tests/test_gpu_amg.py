@@ -135,7 +135,7 @@ def test_solve_tiny_configuration():
     assert np.linalg.norm(x[0, 0].ravel() - xd) <= np.linalg.cond(M) * 1e-10 * np.linalg.norm(xd)
 
 
-@pytest.mark.parametrize("coarse_solver", [0, 2])
+@pytest.mark.parametrize("coarse_solver", [0, 1, 2])
 def test_solve_multi_rhs_multi_shift(coarse_solver):
     L = (8, 4, 4, 8)
     U = synth.gauge_field(L, 0.3, seed=3)

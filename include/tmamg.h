@@ -78,7 +78,7 @@ typedef struct {
                           1: block GMRES over the rhs of each shift; 2: GMRES with one launch per step */
   double delta_mu;     /* coarse twisted-mass factor (paper Fig. 6 caption), 1 = none */
   int precision;       /* 32: mixed (FP32 inner, FP64 outer); 64: plain FP64 single-precision-free path */
-  int use_nn;          /* reserved: learned preconditioner step (0 = off) */
+  int use_nn;          /* learned step in the AMG cycle: 0 off, 1 if trained and enabled by the gate, 2 forced */
   int poll;            /* coarse iterations between host convergence polls */
 } tmamg_solve_params;
 
@@ -154,6 +154,45 @@ int tmamg_setup_from_vectors(tmamg_ctx* ctx, const tmamg_setup_params* p, const 
  * Synchronises the stream. */
 int tmamg_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int nshift, double* x, int on_device,
                 const tmamg_solve_params* p, tmamg_system_stats* stats);
+
+/* ------------------------------------------------------------------ learned preconditioner step */
+/* A gauge-covariant network of three linear parallel-transport layers (4 -> 8 -> 8 -> 4
+ * complex channels of colour 3-vectors; layer out_a(x) = sum_h sum_b W_h[a][b] (T_h in_b)(x)
+ * over the identity and the eight link hops T_{+-nu}), applied as an extra step of the AMG
+ * cycle: z += N(v - D z) after the smoother. Not part of the paper; trained on (residual,
+ * error) pairs from the plain solver. Weights on the host: complex double, the three layers'
+ * [9][cout][cin] arrays concatenated (1152 complex numbers). */
+typedef struct {
+  int pairs;         /* training pairs (a multiple of batch is used) */
+  int batch;         /* systems per training batch (<= 16) */
+  int epochs;
+  double lr;         /* Adam learning rate */
+  double pair_tol;   /* relative residual of the solves that produce the errors */
+  double mu;         /* twisted mass of the training pairs and of the gate solve */
+  uint64_t seed;
+  int gate_systems;  /* right-hand sides of the gate solve (<= 16) */
+} tmamg_nn_params;
+
+typedef struct {
+  double loss_first, loss_last;  /* mean loss per pair in the first and last epoch */
+  int iters_plain, iters_nn;     /* FGMRES iterations of the gate solve without / with the step */
+  int enabled;                   /* 1 if the step lowered the iteration count and stays on */
+} tmamg_nn_report;
+
+void tmamg_default_nn_params(tmamg_nn_params* p);
+/* Start weights: a Jacobi-like map (2 kappa on the spins) plus small seeded noise. */
+int tmamg_nn_init(tmamg_ctx* ctx, uint64_t seed);
+int tmamg_nn_set_weights(tmamg_ctx* ctx, const double* W);
+int tmamg_nn_get_weights(const tmamg_ctx* ctx, double* W);
+/* y = N(r) on FP32 fine bundles (4 channels = the 4 spins); bf16: use the BF16 inference weights. */
+int tmamg_nn_forward(tmamg_ctx* ctx, const void* r_bundle, void* y_bundle, int nsys, int bf16);
+/* loss = sum_n |N(r_n) - e_n|^2 / |e_n|^2 and its gradient (complex double, weight layout). */
+int tmamg_nn_loss_grad(tmamg_ctx* ctx, const void* r_bundle, const void* e_bundle, int nsys, double* loss,
+                       double* grad);
+/* Collect pairs (r = residual after the plain cycle of a random vector, e = D^{-1} r), train
+ * with Adam on the GPU, then run the gate: one solve with and one without the step; the step
+ * stays enabled (for use_nn = 1) only if it lowered the iteration count. Needs a setup. */
+int tmamg_nn_train(tmamg_ctx* ctx, const tmamg_nn_params* p, tmamg_nn_report* report);
 
 /* ------------------------------------------------------------------ components (bundles, device) */
 

@@ -121,6 +121,7 @@ int tmamg_destroy(tmamg_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   free_workspace(ctx);
+  free_nn(ctx);
   free_levels(ctx);
   cudaFree(ctx->U64);
   cudaFree(ctx->U32);

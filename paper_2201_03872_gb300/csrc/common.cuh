@@ -56,6 +56,7 @@ struct CoarseLevel {
 };
 
 struct Workspace;
+struct NNState;
 
 }  // namespace tmamg
 
@@ -81,12 +82,14 @@ struct tmamg_ctx {
   tmamg_setup_params sp;
   std::vector<tmamg::CoarseLevel> levels;
   tmamg::Workspace* ws = nullptr;
+  tmamg::NNState* nn = nullptr;  // learned preconditioner step (optional)
 };
 
 namespace tmamg {
 
 void free_levels(tmamg_ctx* ctx);
 void free_workspace(tmamg_ctx* ctx);
+void free_nn(tmamg_ctx* ctx);
 
 // error helpers (host)
 int set_err(tmamg_ctx* ctx, int code, const std::string& msg);

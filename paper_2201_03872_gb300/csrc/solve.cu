@@ -16,6 +16,7 @@
 #include "block_gmres.cuh"
 #include "coarse_gmres.cuh"
 #include "krylov.cuh"
+#include "nn.cuh"
 #include "sap.cuh"
 
 namespace tmamg {
@@ -321,6 +322,7 @@ struct SolveCtx {
   bool timeout = false;       // a bounded device wait gave up
   bool launch_error = false;  // a cooperative launch was refused
   int nshift = 1;             // systems n = r * nshift + k (block GMRES groups the rhs of shift k)
+  int nn = 0;                 // apply the learned step in the AMG cycle
 };
 
 __global__ void restart_tol_kernel(const double2* dot, const double* beta0, double tol, double* rel, int n) {
@@ -418,6 +420,15 @@ static void amg_cycle(SolveCtx& S, const float* v, float* z) {
   sap_apply(ctx->g, ctx->sp.sap_block, ctx->U32, ctx->C32, w->t1, w->t2, w->t3, S.mu, nsys, ctx->sp.sap_cycles,
             ctx->sp.sap_mr_steps, st);
   axpby<float>(w->ones, 2, w->t2, w->ones, 2, z, M, nsys, nullptr, st);  // z += SAP
+  if (S.nn && ctx->nn && ctx->nn->trained) {
+    // learned step on the residual left by the smoother: z += N(v - D z)
+    NNState& nns = *ctx->nn;
+    NNGeom ng{{ctx->g.L[0], ctx->g.L[1], ctx->g.L[2], ctx->g.L[3]}, ctx->g.V, ctx->g.bc_t};
+    launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, z, w->t1, S.mu, nsys, st);
+    axpby<float>(w->ones, 2, v, w->mones, 2, w->t1, M, nsys, nullptr, st);
+    nn_forward(nns, ng, ctx->U32, w->t1, w->t2, nsys, true, st);
+    axpby<float>(w->ones, 2, w->t2, w->ones, 2, z, M, nsys, nullptr, st);
+  }
 }
 
 // expand b [nrhs][V][12] (complex double) to the FP64 bundle of nsys = nrhs * nshift systems
@@ -511,6 +522,11 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   sqrt_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->bn, nsys); TM_COUNT();
   SolveCtx S{ctx, sp, nsys, ctx->mu_dev, 0};
   S.nshift = nshift;
+  S.nn = sp->use_nn == 2 || (sp->use_nn == 1 && ctx->nn && ctx->nn->enabled);
+  if (S.nn && (!ctx->nn || !ctx->nn->trained)) return set_err(ctx, TMAMG_ERR_STATE, "solve: no trained network");
+  if (S.nn) {
+    if (ctx->nn->alloc(ctx->g.V, nsys)) return set_err(ctx, TMAMG_ERR_OOM, "solve: network buffers");
+  }
   LevelOps fine;
   fine.M = M;
   fine.A = [&](const float* xx, float* yy) { launch_dirac<float>(g, ctx->U32, ctx->C32, xx, yy, ctx->mu_dev, nsys, st); };
@@ -690,6 +706,291 @@ int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_
   const CoarseLevel& l = ctx->levels[0];
   coarse_apply(coarse_dims(l), l.A, (const float*)x_bundle, (float*)y_bundle, ctx->mu_dev, 1.0, nsys, ctx->stream);
   return check_cuda(ctx, cudaGetLastError(), "coarse_apply launch");
+}
+
+}  // extern "C"
+
+// ================================================================== learned preconditioner step
+namespace tmamg {
+
+void free_nn(tmamg_ctx* ctx) {
+  if (ctx->nn) {
+    ctx->nn->release();
+    delete ctx->nn;
+    ctx->nn = nullptr;
+  }
+}
+
+static NNGeom nn_geom(const tmamg_ctx* ctx) {
+  return NNGeom{{ctx->g.L[0], ctx->g.L[1], ctx->g.L[2], ctx->g.L[3]}, ctx->g.V, ctx->g.bc_t};
+}
+
+static int nn_ready(tmamg_ctx* ctx) {
+  if (!ctx->nn) ctx->nn = new NNState();
+  return ctx->nn->alloc_weights();
+}
+
+// host weights (complex double, three layers concatenated) <-> device FP32 master weights
+static int nn_upload(tmamg_ctx* ctx, const double* W) {
+  const int n = nn_weight_offset(3);
+  std::vector<float> h(2 * n);
+  for (int i = 0; i < 2 * n; ++i) h[i] = (float)W[i];
+  int rc = check_cuda(ctx, cudaMemcpyAsync(ctx->nn->W, h.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice,
+                                           ctx->stream), "upload weights");
+  if (rc) return rc;
+  cudaMemsetAsync(ctx->nn->m1, 0, sizeof(float2) * n, ctx->stream);
+  cudaMemsetAsync(ctx->nn->m2, 0, sizeof(float2) * n, ctx->stream);
+  nn_refresh_inference(*ctx->nn, ctx->stream);
+  ctx->nn->trained = true;
+  return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "upload weights");
+}
+
+// gaussian FP32 fine bundle of nsys systems from the library's counter-based generator
+static int random_bundle(tmamg_ctx* ctx, uint64_t seed, int nsys, float* bundle) {
+  std::vector<float> host;
+  start_vectors(seed, nsys, ctx->g.V, host);
+  float* field = nullptr;
+  int rc = check_cuda(ctx, cudaMalloc(&field, host.size() * sizeof(float)), "cudaMalloc(random field)");
+  if (rc) return rc;
+  cudaMemcpyAsync(field, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+  launch_pack<float>(ctx->g, field, bundle, nsys, ctx->stream);
+  rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "random bundle");
+  cudaFree(field);
+  return rc;
+}
+
+// loss sum_n |y_n - e_n|^2 / |e_n|^2 (host value); d: scratch bundle
+static double nn_loss(tmamg_ctx* ctx, const float* y, const float* e, float* d, int nsys) {
+  Workspace* w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  const int64_t M = 12 * ctx->g.V;
+  cudaMemcpyAsync(d, e, w->fb32, cudaMemcpyDeviceToDevice, st);
+  axpby<float>(w->ones, 2, y, w->mones, 2, d, M, nsys, nullptr, st);
+  mdot<float>(d, 0, 1, d, M, nsys, w->dot, nsys, w->top.partial, st);
+  mdot<float>(e, 0, 1, e, M, nsys, w->dot + nsys, nsys, w->top.partial, st);
+  std::vector<double2> h(2 * nsys);
+  cudaMemcpyAsync(h.data(), w->dot, sizeof(double2) * 2 * nsys, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  double s = 0;
+  for (int n = 0; n < nsys; ++n) s += h[nsys + n].x > 0 ? h[n].x / h[nsys + n].x : 0.0;
+  return s;
+}
+
+// e ~ D^{-1} r in FP32 by AMG-preconditioned FGMRES (restarted from the true residual)
+static void solve32(SolveCtx& S, const float* r, float* e, double tol, int cycles) {
+  tmamg_ctx* ctx = S.ctx;
+  Workspace* w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  const int nsys = S.nsys;
+  const int64_t M = 12 * ctx->g.V;
+  LevelOps fine;
+  fine.M = M;
+  fine.A = [&](const float* xx, float* yy) { launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, xx, yy, S.mu, nsys, st); };
+  fine.precond = [&](const float* v, float* z) { amg_cycle(S, v, z); };
+  const size_t vstride = w->fb32 / sizeof(float);
+  cudaMemsetAsync(e, 0, w->fb32, st);
+  set_rel_tol(w->rel_top, nsys, tol, st);
+  for (int c = 0; c < cycles; ++c) {
+    launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, e, w->V, S.mu, nsys, st);
+    axpby<float>(w->ones, 2, r, w->mones, 2, w->V, M, nsys, nullptr, st);  // V0 = r - D e
+    gmres_cycle(w->top, fine, nsys, S.sp->restart, w->V, vstride, w->Z, e, nullptr, w->rel_top, 1, false, st);
+  }
+}
+
+}  // namespace tmamg
+
+extern "C" {
+
+void tmamg_default_nn_params(tmamg_nn_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->pairs = 48;
+  p->batch = 12;
+  p->epochs = 30;
+  p->lr = 2e-3;
+  p->pair_tol = 1e-5;
+  p->mu = 0.0;
+  p->seed = 7;
+  p->gate_systems = 4;
+}
+
+int tmamg_nn_init(tmamg_ctx* ctx, uint64_t seed) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!ctx->have_op) return set_err(ctx, TMAMG_ERR_STATE, "nn_init: operator not set");
+  int rc = nn_ready(ctx);
+  if (rc) return set_err(ctx, TMAMG_ERR_OOM, "nn_init: weights");
+  // a Jacobi-like start: layer 1 maps the spins onto channels 0..3 scaled by 2 kappa (the
+  // inverse of the operator's diagonal), layers 2 and 3 pass them on; plus small noise
+  const int n = nn_weight_offset(3);
+  std::vector<double> W(2 * n, 0.0);
+  std::vector<float> noise;
+  start_vectors(seed, 1, (n + 11) / 12, noise);
+  const int chs[4] = {4, 8, 8, 4};
+  for (int l = 0; l < 3; ++l) {
+    const int cin = chs[l], cout = chs[l + 1], off = nn_weight_offset(l);
+    for (int q = 0; q < 9 * cout * cin; ++q) {
+      W[2 * (off + q)] = 0.01 * noise[2 * (off + q)];
+      W[2 * (off + q) + 1] = 0.01 * noise[2 * (off + q) + 1];
+    }
+    const double d = l == 0 ? 2.0 * ctx->kappa : 1.0;
+    for (int a = 0; a < cout && a < cin; ++a) W[2 * (off + a * cin + a)] += d;
+  }
+  return nn_upload(ctx, W.data());
+}
+
+int tmamg_nn_set_weights(tmamg_ctx* ctx, const double* W) {
+  if (!ctx || !W) return set_err(ctx, TMAMG_ERR_ARG, "nn_set_weights: null argument");
+  if (nn_ready(ctx)) return set_err(ctx, TMAMG_ERR_OOM, "nn_set_weights: weights");
+  return nn_upload(ctx, W);
+}
+
+int tmamg_nn_get_weights(const tmamg_ctx* ctx, double* W) {
+  if (!ctx || !W || !ctx->nn || !ctx->nn->W) return TMAMG_ERR_ARG;
+  const int n = nn_weight_offset(3);
+  std::vector<float> h(2 * n);
+  cudaMemcpy(h.data(), ctx->nn->W, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost);
+  for (int i = 0; i < 2 * n; ++i) W[i] = h[i];
+  return TMAMG_OK;
+}
+
+int tmamg_nn_forward(tmamg_ctx* ctx, const void* r_bundle, void* y_bundle, int nsys, int bf16) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!r_bundle || !y_bundle || nsys < 1 || r_bundle == y_bundle) return set_err(ctx, TMAMG_ERR_ARG, "nn_forward: bad argument");
+  if (!ctx->nn || !ctx->nn->trained) return set_err(ctx, TMAMG_ERR_STATE, "nn_forward: no weights");
+  if (ctx->nn->alloc(ctx->g.V, nsys)) return set_err(ctx, TMAMG_ERR_OOM, "nn_forward: buffers");
+  nn_forward(*ctx->nn, nn_geom(ctx), ctx->U32, (const float*)r_bundle, (float*)y_bundle, nsys, bf16 != 0, ctx->stream);
+  return check_cuda(ctx, cudaGetLastError(), "nn_forward");
+}
+
+int tmamg_nn_loss_grad(tmamg_ctx* ctx, const void* r_bundle, const void* e_bundle, int nsys, double* loss,
+                       double* grad) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!r_bundle || !e_bundle || nsys < 1 || nsys > 256) return set_err(ctx, TMAMG_ERR_ARG, "nn_loss_grad: bad argument");
+  if (!ctx->nn || !ctx->nn->trained) return set_err(ctx, TMAMG_ERR_STATE, "nn_loss_grad: no weights");
+  tmamg_solve_params def;
+  tmamg_default_solve_params(&def);
+  int rc = ensure_ws(ctx, nsys, def.restart, def.coarse_restart);
+  if (rc) return rc;
+  if (ctx->nn->alloc(ctx->g.V, nsys)) return set_err(ctx, TMAMG_ERR_OOM, "nn_loss_grad: buffers");
+  Workspace* w = ctx->ws;
+  NNGeom ng = nn_geom(ctx);
+  nn_forward(*ctx->nn, ng, ctx->U32, (const float*)r_bundle, w->t1, nsys, false, ctx->stream);
+  if (loss) *loss = nn_loss(ctx, w->t1, (const float*)e_bundle, w->t2, nsys);
+  nn_backward(*ctx->nn, ng, ctx->U32, (const float*)r_bundle, w->t1, (const float*)e_bundle, nsys,
+              w->top.partial, ctx->stream);
+  rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "nn_loss_grad");
+  if (rc) return rc;
+  if (grad) {
+    const int n = nn_weight_offset(3);
+    cudaMemcpy(grad, ctx->nn->grad, sizeof(double2) * n, cudaMemcpyDeviceToHost);
+  }
+  return TMAMG_OK;
+}
+
+int tmamg_nn_train(tmamg_ctx* ctx, const tmamg_nn_params* p, tmamg_nn_report* rep) {
+  if (!ctx || !p) return set_err(ctx, TMAMG_ERR_ARG, "nn_train: null argument");
+  if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "nn_train: no multigrid setup");
+  if (p->batch < 1 || p->batch > 16 || p->pairs < p->batch || p->epochs < 1 || !(p->lr > 0) || p->gate_systems < 1 ||
+      p->gate_systems > 16)
+    return set_err(ctx, TMAMG_ERR_ARG, "nn_train: bad parameters");
+  cudaStream_t st = ctx->stream;
+  if (!ctx->nn || !ctx->nn->trained) {
+    int rc = tmamg_nn_init(ctx, p->seed);
+    if (rc) return rc;
+  }
+  NNState& nns = *ctx->nn;
+  const int nsys = p->batch;
+  tmamg_solve_params sp;
+  tmamg_default_solve_params(&sp);
+  int rc = ensure_ws(ctx, nsys, sp.restart, sp.coarse_restart);
+  if (rc) return rc;
+  if (nns.alloc(ctx->g.V, nsys)) return set_err(ctx, TMAMG_ERR_OOM, "nn_train: buffers");
+  Workspace* w = ctx->ws;
+  std::vector<double> mus(nsys, p->mu);
+  rc = upload_mu(ctx, mus.data(), nsys);
+  if (rc) return rc;
+  // ---- training pairs: r = residual the plain cycle leaves, e = D^{-1} r
+  const int nb = p->pairs / nsys;
+  float *R = nullptr, *E = nullptr;
+  rc = check_cuda(ctx, cudaMalloc(&R, w->fb32 * nb), "cudaMalloc(pairs)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&E, w->fb32 * nb), "cudaMalloc(pairs)");
+  if (rc) {
+    cudaFree(R);
+    return rc;
+  }
+  const int64_t M = 12 * ctx->g.V;
+  SolveCtx S{ctx, &sp, nsys, ctx->mu_dev, 0};
+  for (int b = 0; b < nb; ++b) {
+    float* rb = R + (w->fb32 / sizeof(float)) * b;
+    float* eb = E + (w->fb32 / sizeof(float)) * b;
+    rc = random_bundle(ctx, p->seed * 1000003ULL + b, nsys, w->t3);  // v
+    if (rc) break;
+    cudaMemcpyAsync(w->Z, w->t3, w->fb32, cudaMemcpyDeviceToDevice, st);  // keep v
+    amg_cycle(S, w->Z, w->e32);                                            // z = M v (plain)
+    launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, w->e32, rb, S.mu, nsys, st);
+    axpby<float>(w->ones, 2, w->Z, w->mones, 2, rb, M, nsys, nullptr, st);  // r = v - D z
+    solve32(S, rb, eb, p->pair_tol, 3);
+  }
+  NNGeom ng = nn_geom(ctx);
+  double first = 0, last = 0;
+  int step = 0;
+  for (int ep = 0; ep < p->epochs && !rc; ++ep) {
+    double tot = 0;
+    for (int b = 0; b < nb; ++b) {
+      const float* rb = R + (w->fb32 / sizeof(float)) * b;
+      const float* eb = E + (w->fb32 / sizeof(float)) * b;
+      nn_forward(nns, ng, ctx->U32, rb, w->t1, nsys, false, st);
+      if (ep == 0 || ep == p->epochs - 1) tot += nn_loss(ctx, w->t1, eb, w->t2, nsys);
+      nn_backward(nns, ng, ctx->U32, rb, w->t1, eb, nsys, w->top.partial, st);
+      nn_adam(nns, (float)p->lr, ++step, 1.0 / nsys, st);
+    }
+    if (ep == 0) first = tot / (nb * nsys);
+    if (ep == p->epochs - 1) last = tot / (nb * nsys);
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(R);
+  cudaFree(E);
+  if (rc) return rc;
+  nn_refresh_inference(nns, st);
+  nns.trained = true;
+  nns.loss_first = first;
+  nns.loss_last = last;
+  // ---- the gate: the same solve with and without the learned step (plain SAP is the judge)
+  const int ng_sys = p->gate_systems;
+  std::vector<float> hb;
+  start_vectors(p->seed + 99991ULL, ng_sys, ctx->g.V, hb);
+  std::vector<double> b64(hb.begin(), hb.end());
+  std::vector<double> x64(b64.size());
+  std::vector<tmamg_system_stats> stats(ng_sys);
+  double gm = p->mu;
+  int its[2] = {0, 0};
+  bool ok[2] = {false, false};
+  for (int pass = 0; pass < 2; ++pass) {
+    tmamg_solve_params gp;
+    tmamg_default_solve_params(&gp);
+    gp.use_nn = pass == 0 ? 0 : 2;
+    int r2 = do_solve(ctx, b64.data(), ng_sys, &gm, 1, x64.data(), 0, &gp, stats.data());
+    if (r2 < 0) return r2;
+    int mx = 0;
+    bool conv = true;
+    for (int n = 0; n < ng_sys; ++n) {
+      mx = stats[n].inner_iters > mx ? stats[n].inner_iters : mx;
+      conv &= stats[n].status == TMAMG_OK;
+    }
+    its[pass] = mx;
+    ok[pass] = conv;
+  }
+  nns.iters_plain = its[0];
+  nns.iters_nn = its[1];
+  nns.enabled = ok[1] && its[1] < its[0];
+  if (rep) {
+    rep->loss_first = first;
+    rep->loss_last = last;
+    rep->iters_plain = its[0];
+    rep->iters_nn = its[1];
+    rep->enabled = nns.enabled ? 1 : 0;
+  }
+  return TMAMG_OK;
 }
 
 }  // extern "C"

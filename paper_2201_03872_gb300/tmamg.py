@@ -44,6 +44,19 @@ class SystemStats(ctypes.Structure):
                 ("coarse_iters", ctypes.c_int), ("true_rel_res", ctypes.c_double)]
 
 
+class NNParams(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int), ("batch", ctypes.c_int), ("epochs", ctypes.c_int), ("lr", ctypes.c_double),
+                ("pair_tol", ctypes.c_double), ("mu", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("gate_systems", ctypes.c_int)]
+
+
+class NNReport(ctypes.Structure):
+    _fields_ = [("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double), ("iters_plain", ctypes.c_int),
+                ("iters_nn", ctypes.c_int), ("enabled", ctypes.c_int)]
+
+
+NN_WEIGHTS = 9 * (8 * 4 + 8 * 8 + 4 * 8)  # complex numbers in the three layers
+
 _lib = None
 
 
@@ -88,6 +101,13 @@ SIGNATURES = {
     "tmamg_prolong": (I, [P, I, P, P, I]),
     "tmamg_coarse_apply": (I, [P, I, P, P, I, P]),
     "tmamg_coarse_solve": (I, [P, I, P, P, I, P, I, ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_int)]),
+    "tmamg_default_nn_params": (None, [ctypes.POINTER(NNParams)]),
+    "tmamg_nn_init": (I, [P, ctypes.c_uint64]),
+    "tmamg_nn_set_weights": (I, [P, P]),
+    "tmamg_nn_get_weights": (I, [P, P]),
+    "tmamg_nn_forward": (I, [P, P, P, I, I]),
+    "tmamg_nn_loss_grad": (I, [P, P, P, I, ctypes.POINTER(ctypes.c_double), P]),
+    "tmamg_nn_train": (I, [P, ctypes.POINTER(NNParams), ctypes.POINTER(NNReport)]),
 }
 
 
@@ -285,3 +305,47 @@ def tmamg_coarse_solve(ctx, level, rc_bundle, xc_bundle, nrhs, mu, nshift, param
                                                                 int(nrhs), _ptr(m), int(nshift), ctypes.byref(params),
                                                                 ctypes.byref(it)))
     return it.value
+
+
+def tmamg_default_nn_params(**kw):
+    p = NNParams()
+    lib().tmamg_default_nn_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def tmamg_nn_init(ctx, seed=7):
+    return _check("tmamg_nn_init", ctx, lib().tmamg_nn_init(ctx, int(seed)))
+
+
+def tmamg_nn_set_weights(ctx, Ws):
+    """Ws: the three complex weight arrays [9][cout][cin] (concatenated in order)."""
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(w, dtype=np.complex128).ravel() for w in Ws]))
+    assert flat.size == NN_WEIGHTS
+    return _check("tmamg_nn_set_weights", ctx, lib().tmamg_nn_set_weights(ctx, _ptr(flat)))
+
+
+def tmamg_nn_get_weights(ctx):
+    flat = np.zeros(NN_WEIGHTS, dtype=np.complex128)
+    _check("tmamg_nn_get_weights", ctx, lib().tmamg_nn_get_weights(ctx, _ptr(flat)))
+    return flat
+
+
+def tmamg_nn_forward(ctx, r_bundle, y_bundle, nsys, bf16=False):
+    return _check("tmamg_nn_forward", ctx, lib().tmamg_nn_forward(ctx, _ptr(r_bundle), _ptr(y_bundle), int(nsys),
+                                                                  1 if bf16 else 0))
+
+
+def tmamg_nn_loss_grad(ctx, r_bundle, e_bundle, nsys):
+    loss = ctypes.c_double(0)
+    grad = np.zeros(NN_WEIGHTS, dtype=np.complex128)
+    _check("tmamg_nn_loss_grad", ctx, lib().tmamg_nn_loss_grad(ctx, _ptr(r_bundle), _ptr(e_bundle), int(nsys),
+                                                               ctypes.byref(loss), _ptr(grad)))
+    return loss.value, grad
+
+
+def tmamg_nn_train(ctx, params):
+    rep = NNReport()
+    _check("tmamg_nn_train", ctx, lib().tmamg_nn_train(ctx, ctypes.byref(params), ctypes.byref(rep)))
+    return rep

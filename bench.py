@@ -281,6 +281,34 @@ def run_solve(args, world, rank, local):
     e2e_s = max_over_ranks(time.perf_counter() - t, world)
     # the fine stencil (dominant hot kernel named by the metric), same context and systems
     kern_ms = measure_dirac(T, ctx, nsys, np.full(nsys, wl["mu"]), 20, stream)
+    variants = {}
+    if args.variants:
+        # same workload, other forms of the method (each timed over the same number of steps)
+        def timed(label, nr, **kw):
+            spv = T.solve_params(**dict(solve_kw(), **kw))
+            T.tmamg_solve(ctx, bd, nr, mus, len(mus), xd, 1, spv)
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            okv = True
+            for _ in range(args.steps):
+                rcv, stv = T.tmamg_solve(ctx, bd, nr, mus, len(mus), xd, 1, spv)
+                okv &= rcv == 0 and all(q.status == 0 for q in stv)
+            z.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(z) / args.steps
+            variants[label] = {"solves_per_s": nr * len(mus) / (ms * 1e-3), "ms_per_step": ms, "all_converged": okv,
+                               "fgmres_iterations": stv[0].inner_iters, "coarse_iterations": stv[0].coarse_iters}
+        timed("single_system", 1)
+        timed("block_gmres_coarse", nrhs, coarse_solver=1)
+        t = time.time()
+        rep = T.tmamg_nn_train(ctx, T.tmamg_default_nn_params(pairs=48, batch=12, epochs=30, lr=2e-3, mu=wl["mu"],
+                                                              gate_systems=4))
+        torch.cuda.synchronize()
+        timed("learned_step", nrhs, use_nn=2)
+        variants["learned_step"].update({"train_seconds": time.time() - t, "loss_first": rep.loss_first,
+                                         "loss_last": rep.loss_last, "gate_iterations_plain": rep.iters_plain,
+                                         "gate_iterations_with_step": rep.iters_nn, "gate_enabled": bool(rep.enabled)})
     T.tmamg_destroy(ctx)
     hbm, _, peak_src = read_peaks()
     bytes_per_apply = dirac_bytes_per_site(nsys, 32) * V
@@ -293,7 +321,7 @@ def run_solve(args, world, rank, local):
         "config": {"workload": WORKLOAD["name"], "lattice": "16^3x32", "systems_per_step": nsys, "kappa": kappa,
                    "kappa_source": ksrc, "c_sw": wl["c_sw"], "mu": wl["mu"], "tol": 1e-10,
                    "amg": "2-level, 4^4 aggregates, Nv=24, 20 setup iterations, SAP 4^4 blocks x 2 cycles x 3 MR, "
-                          "FGMRES(20) + FP64 refinement, coarse GMRES(40) to 0.1",
+                          "FGMRES(20) + FP64 refinement, persistent coarse GMRES(40) to 0.1",
                    "setup_seconds": setup_s, "all_converged": bool(ok),
                    "iterations": {"outer": s0.outer_iters, "fgmres": s0.inner_iters, "coarse": s0.coarse_iters},
                    "l2": "working set > 129 MB L2 (solver vectors 3+ GB)"},
@@ -305,6 +333,8 @@ def run_solve(args, world, rank, local):
         "gpu_launches": int(launches),
         "clocks": clk.result,
     }
+    if variants:
+        line["variants"] = variants
     return line
 
 
@@ -372,6 +402,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--what", default="solve", choices=["solve", "dirac"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the single-system, block-GMRES and learned-step forms")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_init()

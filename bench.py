@@ -256,7 +256,7 @@ def run_solve(args, world, rank, local):
     barrier(world)
     ok = True
     iters = None
-    launches0 = T.tmamg_kernel_launches()
+    launches0 = T.tmamg_kernel_launches()  # kernels launched before the timed region (ncu -s)
     with Clocks(local) as clk:
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
@@ -331,6 +331,7 @@ def run_solve(args, world, rank, local):
         "e2e": {"value": nsys * args.steps * world / e2e_s, "unit": "solves/s",
                 "h2d_bytes_per_step": int(bh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)},
         "gpu_launches": int(launches),
+        "launches_before_timed": int(launches0),
         "clocks": clk.result,
     }
     if variants:

@@ -133,93 +133,142 @@ void build_P(const AggDims& g, const float* Vb, float2* P, int nv, int d, cudaSt
 }
 
 // ------------------------------------------------------------------ restriction / prolongation
+// Per aggregate the restriction is a small matrix product xc_a = P_a^+ r_a (2 nv x K times
+// K x nsys, K = asize d) and the prolongation its transpose; one CTA per aggregate reads P_a
+// once for all systems (tile chunks of RP_TCH tiles), staged through shared memory in
+// chunks of RP_KC columns so that both P and the vectors are read with coalesced loads.
+constexpr int RP_TCH = 8;
+constexpr int RP_KC = 48;
+constexpr int RP_THREADS = 256;
+
 // xc[tile][chi nv + j][a] = sum_k conj(P[a][chi][j][k]) r[tile][chi d + c'][site(a, q)]
-constexpr int KS = 4;
-__global__ void restrict_kernel(const float2* __restrict__ P, const float* __restrict__ r, float* __restrict__ xc,
-                                AggDims g, int nv, int d) {
+__global__ void __launch_bounds__(RP_THREADS) restrict_kernel(const float2* __restrict__ P,
+                                                              const float* __restrict__ r, float* __restrict__ xc,
+                                                              AggDims g, int nv, int d, int nt) {
+  __shared__ float2 Ps[64][RP_KC + 1];        // rows chi nv + j (nc <= 64), a chunk of k
+  __shared__ float4 Rs[2][RP_KC][RP_TCH];     // both chiralities, the chunk of k, tiles
+  __shared__ int sidx[RP_KC];
   const int64_t a = blockIdx.x;
-  const int tile = blockIdx.y;
   const int nc = 2 * nv;
-  const int o = threadIdx.x / KS, sl = threadIdx.x % KS;
   const int K = g.asize * d;
-  __shared__ float4 part[256];
-  float4 acc = make_float4(0, 0, 0, 0);
-  if (o < nc) {
-    const int chi = o / nv, j = o % nv;
-    const float2* Pr = P + (((int64_t)a * 2 + chi) * nv + j) * K;
-    const float* rt = r + (int64_t)tile * (2 * d) * g.Vp * 2 * T2;
-    for (int k = sl; k < K; k += KS) {
-      int q = k / d, cp = k % d;
-      int c[4];
-      agg_site(a, q, g.Lc, g.agg, g.L, c);
-      int64_t s = site_index(c, g.L);
-      float4 v = *reinterpret_cast<const float4*>(rt + ((int64_t)(chi * d + cp) * g.Vp + s) * 2 * T2);
-      float2 p = Pr[k];
-      // conj(p) * v for the two lanes (v = re0, re1, im0, im1)
-      acc.x += p.x * v.x + p.y * v.z;
-      acc.y += p.x * v.y + p.y * v.w;
-      acc.z += p.x * v.z - p.y * v.x;
-      acc.w += p.x * v.w - p.y * v.y;
+  for (int t0 = 0; t0 < nt; t0 += RP_TCH) {
+    const int ntc = nt - t0 < RP_TCH ? nt - t0 : RP_TCH;
+    // outputs (o, u): thread handles q = tid, tid + 256, ...
+    float4 acc[3];
+    for (int i = 0; i < 3; ++i) acc[i] = make_float4(0, 0, 0, 0);
+    for (int k0 = 0; k0 < K; k0 += RP_KC) {
+      const int kc = K - k0 < RP_KC ? K - k0 : RP_KC;
+      __syncthreads();
+      for (int q = threadIdx.x; q < nc * kc; q += blockDim.x) {
+        const int o = q / kc, kk = q % kc;
+        const int chi = o / nv, j = o % nv;
+        Ps[o][kk] = P[(((int64_t)a * 2 + chi) * nv + j) * K + k0 + kk];
+      }
+      for (int kk = threadIdx.x; kk < kc; kk += blockDim.x) {
+        int c[4];
+        agg_site(a, (k0 + kk) / d, g.Lc, g.agg, g.L, c);
+        sidx[kk] = (int)site_index(c, g.L);
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < 2 * kc * ntc; q += blockDim.x) {
+        const int u = q % ntc, kk = (q / ntc) % kc, chi = q / (ntc * kc);
+        const int cp = (k0 + kk) % d;
+        Rs[chi][kk][u] =
+            *reinterpret_cast<const float4*>(r + (((int64_t)(t0 + u) * (2 * d) + chi * d + cp) * g.Vp + sidx[kk]) * 4);
+      }
+      __syncthreads();
+      int slot = 0;
+      for (int q = threadIdx.x; q < nc * ntc; q += blockDim.x, ++slot) {
+        const int o = q / ntc, u = q % ntc;
+        const int chi = o / nv;
+        float4 s = acc[slot];
+        for (int kk = 0; kk < kc; ++kk) {
+          const float2 pv = Ps[o][kk];
+          const float4 v = Rs[chi][kk][u];
+          // conj(p) v for both lanes (v = re0, re1, im0, im1)
+          s.x += pv.x * v.x + pv.y * v.z;
+          s.y += pv.x * v.y + pv.y * v.w;
+          s.z += pv.x * v.z - pv.y * v.x;
+          s.w += pv.x * v.w - pv.y * v.y;
+        }
+        acc[slot] = s;
+      }
     }
-  }
-  part[threadIdx.x] = acc;
-  __syncthreads();
-  if (o < nc && sl == 0) {
-    float4 s = part[threadIdx.x];
-    for (int u = 1; u < KS; ++u) {
-      float4 w = part[threadIdx.x + u];
-      s.x += w.x; s.y += w.y; s.z += w.z; s.w += w.w;
+    int slot = 0;
+    for (int q = threadIdx.x; q < nc * ntc; q += blockDim.x, ++slot) {
+      const int o = q / ntc, u = q % ntc;
+      *reinterpret_cast<float4*>(xc + (((int64_t)(t0 + u) * nc + o) * g.Vc + a) * 4) = acc[slot];
     }
-    *reinterpret_cast<float4*>(xc + (((int64_t)tile * nc + o) * g.Vc + a) * 2 * T2) = s;
   }
 }
 
 void restrict_vec(const AggDims& g, const float2* P, const float* r, float* xc, int nv, int d, int nsys,
                   cudaStream_t st) {
-  int nt = ntiles(nsys, T2);
-  int threads = 2 * nv * KS;
-  restrict_kernel<<<dim3((unsigned)g.Vc, nt), threads, 0, st>>>(P, r, xc, g, nv, d); TM_COUNT();
+  const int nt = ntiles(nsys, T2);
+  restrict_kernel<<<(unsigned)g.Vc, RP_THREADS, 0, st>>>(P, r, xc, g, nv, d, nt); TM_COUNT();
 }
 
-// e[tile][chi d + c'][site(a, q)] (+)= sum_j P[a][chi][j][k] xc[tile][chi nv + j][a]
-__global__ void prolong_kernel(const float2* __restrict__ P, const float* __restrict__ xc, float* __restrict__ e,
-                               AggDims g, int nv, int d, int accumulate) {
-  const int K = g.asize * d;
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int tile = blockIdx.y;
-  if (t >= g.Vc * 2 * (int64_t)K) return;
-  const int k = (int)(t % K);
-  const int chi = (int)((t / K) % 2);
-  const int64_t a = t / ((int64_t)K * 2);
+// e[tile][chi d + c'][site(a, q)] (+)= sum_j P[a][chi][j][k] xc[tile][chi nv + j][a]:
+// one CTA per aggregate, threads over k (coalesced reads of P), the aggregate's coarse
+// vector of a tile chunk in shared memory
+__global__ void __launch_bounds__(RP_THREADS) prolong_kernel(const float2* __restrict__ P,
+                                                             const float* __restrict__ xc, float* __restrict__ e,
+                                                             AggDims g, int nv, int d, int nt, int accumulate) {
+  __shared__ float4 Xs[64][RP_TCH];
+  const int64_t a = blockIdx.x;
   const int nc = 2 * nv;
-  const float2* Pc = P + ((a * 2 + chi) * nv) * (int64_t)K + k;
-  const float* xt = xc + (int64_t)tile * nc * g.Vc * 2 * T2;
-  float4 acc = make_float4(0, 0, 0, 0);
-  for (int j = 0; j < nv; ++j) {
-    float2 p = Pc[(int64_t)j * K];
-    float4 x = *reinterpret_cast<const float4*>(xt + ((int64_t)(chi * nv + j) * g.Vc + a) * 2 * T2);
-    acc.x += p.x * x.x - p.y * x.z;
-    acc.y += p.x * x.y - p.y * x.w;
-    acc.z += p.x * x.z + p.y * x.x;
-    acc.w += p.x * x.w + p.y * x.y;
+  const int K = g.asize * d;
+  for (int t0 = 0; t0 < nt; t0 += RP_TCH) {
+    const int ntc = nt - t0 < RP_TCH ? nt - t0 : RP_TCH;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc * ntc; q += blockDim.x) {
+      const int o = q / ntc, u = q % ntc;
+      Xs[o][u] = *reinterpret_cast<const float4*>(xc + (((int64_t)(t0 + u) * nc + o) * g.Vc + a) * 4);
+    }
+    __syncthreads();
+    for (int ck = threadIdx.x; ck < 2 * K; ck += blockDim.x) {
+      const int chi = ck / K, k = ck % K;
+      const float2* Pc = P + (((int64_t)a * 2 + chi) * nv) * K + k;
+      float4 acc[RP_TCH];
+#pragma unroll
+      for (int u = 0; u < RP_TCH; ++u) acc[u] = make_float4(0, 0, 0, 0);
+      for (int j = 0; j < nv; ++j) {
+        const float2 pv = Pc[(int64_t)j * K];
+#pragma unroll
+        for (int u = 0; u < RP_TCH; ++u) {
+          if (u < ntc) {
+            const float4 x = Xs[chi * nv + j][u];
+            acc[u].x += pv.x * x.x - pv.y * x.z;
+            acc[u].y += pv.x * x.y - pv.y * x.w;
+            acc[u].z += pv.x * x.z + pv.y * x.x;
+            acc[u].w += pv.x * x.w + pv.y * x.y;
+          }
+        }
+      }
+      const int q = k / d, cp = k % d;
+      int c[4];
+      agg_site(a, q, g.Lc, g.agg, g.L, c);
+      const int64_t s = site_index(c, g.L);
+#pragma unroll
+      for (int u = 0; u < RP_TCH; ++u) {
+        if (u < ntc) {
+          float* out = e + (((int64_t)(t0 + u) * (2 * d) + chi * d + cp) * g.Vp + s) * 4;
+          float4 v = acc[u];
+          if (accumulate) {
+            const float4 o = *reinterpret_cast<const float4*>(out);
+            v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+          }
+          *reinterpret_cast<float4*>(out) = v;
+        }
+      }
+    }
   }
-  int q = k / d, cp = k % d;
-  int c[4];
-  agg_site(a, q, g.Lc, g.agg, g.L, c);
-  int64_t s = site_index(c, g.L);
-  float* out = e + (((int64_t)tile * (2 * d) + chi * d + cp) * g.Vp + s) * 2 * T2;
-  if (accumulate) {
-    float4 o = *reinterpret_cast<const float4*>(out);
-    acc.x += o.x; acc.y += o.y; acc.z += o.z; acc.w += o.w;
-  }
-  *reinterpret_cast<float4*>(out) = acc;
 }
 
 void prolong_vec(const AggDims& g, const float2* P, const float* xc, float* e, int nv, int d, int nsys, int accumulate,
                  cudaStream_t st) {
-  int nt = ntiles(nsys, T2);
-  int64_t total = g.Vc * 2 * (int64_t)g.asize * d;
-  prolong_kernel<<<dim3((unsigned)((total + 255) / 256), nt), 256, 0, st>>>(P, xc, e, g, nv, d, accumulate); TM_COUNT();
+  const int nt = ntiles(nsys, T2);
+  prolong_kernel<<<(unsigned)g.Vc, RP_THREADS, 0, st>>>(P, xc, e, g, nv, d, nt, accumulate); TM_COUNT();
 }
 
 // ------------------------------------------------------------------ coarse stencil application

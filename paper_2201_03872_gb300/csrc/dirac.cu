@@ -231,8 +231,9 @@ void launch_build_clover(const Geom& g, const double2* U64, double kappa, double
                                                                        c_sw, C64, C32); TM_COUNT();
 }
 
+// FP32: 192-thread CTAs, two per SM, up to 170 registers (no spills); FP64: 256 threads, one per SM
 template <typename real, int T, int BX>
-__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 2 : 1) dirac_kernel(const typename LinkT<real>::t* __restrict__ U,
+__global__ void __launch_bounds__(sizeof(real) == 4 ? 192 : 256, sizeof(real) == 4 ? 2 : 1) dirac_kernel(const typename LinkT<real>::t* __restrict__ U,
                                                     const real* __restrict__ C, const real* __restrict__ x,
                                                     real* __restrict__ y, const double* __restrict__ mu, int nsys,
                                                     int ntile, int Lx, int Ly, int Lz, int Lt, real bc_t) {
@@ -278,10 +279,10 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 2 : 1) dirac_kernel(c
   for (int k = 0; k < 12; ++k) stcv(yo + (int64_t)k * V * 2 * T, acc.c[k]);
 }
 
-// largest divisor of nt that keeps the CTA at <= 256 threads
-static inline int pick_ty(int nt, int bx) {
+// largest divisor of nt that keeps the CTA at <= maxthreads threads
+static inline int pick_ty(int nt, int bx, int maxthreads) {
   int best = 1;
-  for (int d = 1; d * bx <= 256 && d <= nt; ++d)
+  for (int d = 1; d * bx <= maxthreads && d <= nt; ++d)
     if (nt % d == 0) best = d;
   return best;
 }
@@ -290,9 +291,11 @@ template <typename real>
 void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu, int nsys,
                   cudaStream_t st) {
   constexpr int T = Tile<real>::T;
-  constexpr int BX = 64;
+  // FP32: 32 sites x up to 6 tiles per CTA, so a site's links and clover are read once per CTA
+  constexpr int BX = sizeof(real) == 4 ? 32 : 64;
+  constexpr int MAXT = sizeof(real) == 4 ? 192 : 256;
   int nt = ntiles(nsys, T);
-  int ty = pick_ty(nt, BX);
+  int ty = pick_ty(nt, BX, MAXT);
   dim3 block(BX, ty);
   dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nt / ty));
   dirac_kernel<real, T, BX><<<grid, block, 0, st>>>(reinterpret_cast<const typename LinkT<real>::t*>(U), C, x, y, mu,

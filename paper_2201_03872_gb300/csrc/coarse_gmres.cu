@@ -34,6 +34,9 @@ constexpr int CG_MAXM = 64;  // largest restart length
 constexpr int CG_EPT = 4;    // entries per thread held in registers in the vector phases
 constexpr int CG_ABATCH = 8; // stencil loads in flight per thread
 constexpr int CG_MAXNC = 64; // largest coarse site dimension 2 Nv
+constexpr int CG_AJC = 16;   // stencil columns per asynchronous chunk
+// per-warp shared memory of the stencil phase, in float4 units (vector staging + 2 chunks)
+constexpr int CG_WARP_F4 = CG_MAXNC * CG_TCH + CG_AJC * CG_MAXNC;
 
 struct CGArgs {
   const float2* A;
@@ -107,17 +110,29 @@ __device__ __forceinline__ T ldx(const T* p) {
 }
 
 __device__ __forceinline__ void cfma(float4& acc, float ar, float ai, const float4& v) {
-  // acc (2 lanes, re0 re1 im0 im1) += (ar + i ai) * v
-  acc.x += ar * v.x - ai * v.z;
-  acc.y += ar * v.y - ai * v.w;
-  acc.z += ar * v.z + ai * v.x;
-  acc.w += ar * v.w + ai * v.y;
+  // acc (2 lanes, re0 re1 im0 im1) += (ar + i ai) * v, as packed FP32x2 FMAs over the lanes
+  float2 re = make_float2(acc.x, acc.y), im = make_float2(acc.z, acc.w);
+  const float2 vre = make_float2(v.x, v.y), vim = make_float2(v.z, v.w);
+  re = __ffma2_rn(make_float2(ar, ar), vre, re);
+  re = __ffma2_rn(make_float2(-ai, -ai), vim, re);
+  im = __ffma2_rn(make_float2(ar, ar), vim, im);
+  im = __ffma2_rn(make_float2(ai, ai), vre, im);
+  acc = make_float4(re.x, re.y, im.x, im.y);
 }
 
 // Stencil phase A: hop partials hpart[h][t][i][a] = sum_j A_h(a)[i][j] in[t][j][a + h].
 // One warp per task (site a, hop h, chunk of CG_TCH tiles); lane l owns rows l and l + 32.
 // Stencil loads are coalesced over rows; the vector loads are warp-wide broadcasts from L2;
 // eight columns are in flight at a time. No CTA-wide synchronisation.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
 __device__ void cg_apply_partials(const CGArgs& p, const float* in, float4* wsm) {
   const int nc = p.nc;
   const int lane = threadIdx.x & 31;
@@ -125,8 +140,14 @@ __device__ void cg_apply_partials(const CGArgs& p, const float* in, float4* wsm)
   const int64_t ntask = (int64_t)9 * p.Vc * nchunk;
   const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t nw = (int64_t)p.G * (blockDim.x >> 5);
-  float4* xw = wsm + (threadIdx.x >> 5) * (CG_MAXNC * CG_TCH);  // this warp's staging slice
+  // this warp's shared memory: vector staging [CG_MAXNC][CG_TCH] float4, then two buffers of
+  // CG_AJC stencil columns [CG_AJC][nc] float2, filled by asynchronous 16-byte copies so that
+  // the next chunk is in flight while the current one is used
+  float4* xw = wsm + (threadIdx.x >> 5) * CG_WARP_F4;
+  float2* abuf[2] = {reinterpret_cast<float2*>(xw + CG_MAXNC * CG_TCH),
+                     reinterpret_cast<float2*>(xw + CG_MAXNC * CG_TCH) + CG_AJC * CG_MAXNC};
   const bool r1 = lane + 32 < nc;
+  const int nj = (nc + CG_AJC - 1) / CG_AJC;
   for (int64_t task = wid; task < ntask; task += nw) {
     const int ch = (int)(task % nchunk);
     const int64_t ha = task / nchunk;
@@ -142,44 +163,58 @@ __device__ void cg_apply_partials(const CGArgs& p, const float* in, float4* wsm)
       c[nu] = (c[nu] + dir + p.L[nu]) % p.L[nu];
       nb = site_index(c, p.L);
     }
-    // stage the neighbour's vector entries of this tile chunk (independent loads)
-    __syncwarp();
+    const float2* Ab = p.A + ((int64_t)h * p.Vc + a) * nc * nc;  // column-major block
+    __syncwarp();  // the previous task's buffers are free
+    // group 0: vector entries and stencil chunk 0; group 1: stencil chunk 1
     for (int q = lane; q < nc * ntc; q += 32) {
       const int j = q / ntc, u = q - j * ntc;
-      xw[j * CG_TCH + u] = ld4(in + ((((int64_t)(t0 + u) * nc + j) * p.Vc) + nb) * 4);
+      cp_async16(xw + j * CG_TCH + u, in + ((((int64_t)(t0 + u) * nc + j) * p.Vc) + nb) * 4);
     }
-    __syncwarp();
-    const float2* Ab = p.A + ((int64_t)h * p.Vc + a) * nc * nc;  // column-major block
+    {
+      const int jn0 = nc < CG_AJC ? nc : CG_AJC;
+      for (int q = lane; q < jn0 * nc / 2; q += 32) cp_async16(abuf[0] + 2 * q, Ab + 2 * q);
+      asm volatile("cp.async.commit_group;\n" ::);
+    }
+    if (nj > 1) {
+      const int jn1 = nc - CG_AJC < CG_AJC ? nc - CG_AJC : CG_AJC;
+      for (int q = lane; q < jn1 * nc / 2; q += 32) cp_async16(abuf[1] + 2 * q, Ab + (int64_t)CG_AJC * nc + 2 * q);
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
     float4 acc0[CG_TCH], acc1[CG_TCH];
 #pragma unroll
     for (int u = 0; u < CG_TCH; ++u) {
       acc0[u] = make_float4(0, 0, 0, 0);
       acc1[u] = make_float4(0, 0, 0, 0);
     }
-    for (int j0 = 0; j0 < nc; j0 += CG_ABATCH) {
-      float2 m0[CG_ABATCH], m1[CG_ABATCH];
+    for (int c = 0; c < nj; ++c) {
+      const int j0 = c * CG_AJC;
+      const int jn = nc - j0 < CG_AJC ? nc - j0 : CG_AJC;
+      asm volatile("cp.async.wait_group 1;\n" ::);  // chunk c has landed (one group may still fly)
+      __syncwarp();
+      const float2* aw = abuf[c & 1];
+      for (int jj = 0; jj < jn; ++jj) {
+        const float2 m0 = lane < nc ? aw[jj * nc + lane] : make_float2(0, 0);
+        const float2 m1 = r1 ? aw[jj * nc + lane + 32] : make_float2(0, 0);
+        const int j = j0 + jj;
 #pragma unroll
-      for (int k = 0; k < CG_ABATCH; ++k) {
-        const int j = j0 + k;
-        const bool ok = j < nc;
-        m0[k] = ok && lane < nc ? __ldg(Ab + (int64_t)j * nc + lane) : make_float2(0, 0);
-        m1[k] = ok && r1 ? __ldg(Ab + (int64_t)j * nc + lane + 32) : make_float2(0, 0);
-      }
-#pragma unroll
-      for (int k = 0; k < CG_ABATCH; ++k) {
-        const int j = j0 + k;
-        if (j < nc) {
-#pragma unroll
-          for (int u = 0; u < CG_TCH; ++u) {
-            if (u < ntc) {
-              const float4 v = xw[j * CG_TCH + u];
-              cfma(acc0[u], m0[k].x, m0[k].y, v);
-              cfma(acc1[u], m1[k].x, m1[k].y, v);
-            }
+        for (int u = 0; u < CG_TCH; ++u) {
+          if (u < ntc) {
+            const float4 v = xw[j * CG_TCH + u];
+            cfma(acc0[u], m0.x, m0.y, v);
+            cfma(acc1[u], m1.x, m1.y, v);
           }
         }
       }
+      __syncwarp();  // buffer c & 1 is consumed: refill it with chunk c + 2
+      if (c + 2 < nj) {
+        const int j2 = (c + 2) * CG_AJC;
+        const int jn2 = nc - j2 < CG_AJC ? nc - j2 : CG_AJC;
+        for (int q = lane; q < jn2 * nc / 2; q += 32)
+          cp_async16(abuf[c & 1] + 2 * q, Ab + (int64_t)j2 * nc + 2 * q);
+      }
+      asm volatile("cp.async.commit_group;\n" ::);
     }
+    asm volatile("cp.async.wait_group 0;\n" ::);
 #pragma unroll
     for (int u = 0; u < CG_TCH; ++u) {
       if (u < ntc) {
@@ -284,10 +319,29 @@ __device__ void givens_step(const CGArgs& p, int n, int j, double hn, int total)
   double2 cv[CG_MAXM + 1];
   double c_[CG_MAXM];
   double2 s_[CG_MAXM];
-  for (int i = 0; i <= j; ++i) cv[i] = ldx(col + i * NS + n);  // independent loads
-  for (int i = 0; i < j; ++i) {
-    c_[i] = p.cs[i * NS + n];
-    s_[i] = p.sn[i * NS + n];
+  // operands fetched eight at a time into registers before they are parked in local memory
+  for (int i0 = 0; i0 <= j; i0 += 8) {
+    double2 t[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t[k] = i0 + k <= j ? ldx(col + (i0 + k) * NS + n) : make_double2(0, 0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (i0 + k <= j) cv[i0 + k] = t[k];
+  }
+  for (int i0 = 0; i0 < j; i0 += 8) {
+    double tc[8];
+    double2 ts[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      tc[k] = i0 + k < j ? ldx(p.cs + (i0 + k) * NS + n) : 0.0;
+      ts[k] = i0 + k < j ? ldx(p.sn + (i0 + k) * NS + n) : make_double2(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (i0 + k < j) {
+        c_[i0 + k] = tc[k];
+        s_[i0 + k] = ts[k];
+      }
   }
   cv[j + 1] = make_double2(hn, 0);
   for (int i = 0; i < j; ++i) {
@@ -684,7 +738,7 @@ void CoarseGmres::release() {
 }
 
 static size_t dyn_smem_bytes(int m) {
-  const size_t stage = sizeof(float4) * (size_t)(CG_THREADS / 32) * CG_MAXNC * CG_TCH;  // per-warp vector staging
+  const size_t stage = sizeof(float4) * (size_t)(CG_THREADS / 32) * CG_WARP_F4;  // per-warp staging
   const size_t rs = sizeof(double2) * (size_t)m * m;                                  // back substitution
   return stage > rs ? stage : rs;
 }

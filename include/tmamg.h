@@ -80,6 +80,9 @@ typedef struct {
   int precision;       /* 32: mixed (FP32 inner, FP64 outer); 64: plain FP64 single-precision-free path */
   int use_nn;          /* learned step in the AMG cycle: 0 off, 1 if trained and enabled by the gate, 2 forced */
   int poll;            /* coarse iterations between host convergence polls */
+  int coarse_precision; /* coarse stencil: 16 (default; 0 means 16) FP16 operator and FP16-staged vectors on
+                           the tensor cores (tcgen05) with FP32 accumulation, per-system scaling that keeps
+                           the FP16 range; 32: FP32 operator on the CUDA cores (reference path) */
 } tmamg_solve_params;
 
 typedef struct {
@@ -236,8 +239,16 @@ int tmamg_restrict(tmamg_ctx* ctx, int level, const void* fine_bundle, void* coa
 int tmamg_prolong(tmamg_ctx* ctx, int level, const void* coarse_bundle, void* fine_bundle, int nsys);
 
 /* y = D_c(mu_n) x on coarse level 1 (9-point stencil of dense 2nv x 2nv blocks plus
- * i mu_n gamma5_c, paper Sec. 2 and Fig. 6 caption with delta mu = 1). mu: host [nsys]. */
-int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_bundle, int nsys, const double* mu);
+ * i mu_n gamma5_c, paper Sec. 2 and Fig. 6 caption with delta mu = 1). mu: host [nsys].
+ * precision 16: FP16 stencil blocks and FP16-staged x on the tensor cores, FP32 accumulation;
+ * each system's x is scaled by a power of two near 1/max|x_n| before the conversion and y is
+ * scaled back, so the elementwise error is about (2^-10 + 18 ncp 2^-22) sum |A_ij| |x_j| over the
+ * nine blocks (FP16 rounding of both operands, FP32 sums of 18 ncp terms, ncp = 2nv rounded up
+ * to a multiple of 8; 2nv <= 64, at most 1024 systems); precision 32: FP32 blocks on the CUDA
+ * cores. Asynchronous on the context stream except for the read of the bounded-wait flag
+ * (TMAMG_ERR_TIMEOUT). */
+int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_bundle, int nsys, const double* mu,
+                       int precision);
 
 /* xc ~ D_c(delta_mu mu_k)^{-1} rc on coarse level 1 by the coarse solver selected in p
  * (p->coarse_solver: 0 persistent GMRES, 1 block GMRES per shift, 2 GMRES with one launch

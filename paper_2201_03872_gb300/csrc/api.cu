@@ -90,6 +90,7 @@ void tmamg_default_solve_params(tmamg_solve_params* p) {
   p->precision = 32;
   p->use_nn = 0;
   p->poll = 4;
+  p->coarse_precision = 16;
 }
 
 int tmamg_create(const int L[4], int bc_t, void* cuda_stream, tmamg_ctx** out) {
@@ -248,6 +249,9 @@ void free_levels(tmamg_ctx* ctx) {
   for (auto& l : ctx->levels) {
     cudaFree(l.P);
     cudaFree(l.A);
+    cudaFree(l.A16);
+    cudaFree(l.cmax);
+    cudaFree(l.cerr);
   }
   ctx->levels.clear();
 }

@@ -24,6 +24,7 @@
 
 #include "amg.cuh"
 #include "coarse_gmres.cuh"
+#include "coarse_mma.cuh"
 
 namespace tmamg {
 
@@ -40,6 +41,9 @@ constexpr int CG_WARP_F4 = CG_MAXNC * CG_TCH + CG_AJC * CG_MAXNC;
 
 struct CGArgs {
   const float2* A;
+  const __half* A16;  // FP16 operator for the tensor-core stencil, or null (FP32 stencil)
+  int cm_nbuf;        // operator buffers of the tensor-core stencil
+  double* b0;         // [NS] initial residual norm per system (scale of the restart product)
   int L[4];
   int64_t Vc;
   int nc;
@@ -92,6 +96,7 @@ __device__ __forceinline__ bool grid_barrier(const CGArgs& p) {
           atomicExch(p.err, 1);
           break;
         }
+        if (*(volatile int*)p.err) break;  // another CTA gave up
         __nanosleep(32);
       }
     }
@@ -157,11 +162,19 @@ __device__ void cg_apply_partials(const CGArgs& p, const float* in, float4* wsm)
     const int ntc = p.nt - t0 < CG_TCH ? p.nt - t0 : CG_TCH;
     int64_t nb = a;
     if (h > 0) {
-      int c[4];
-      site_coords(a, p.L, c);
+      const int L0 = p.L[0], L1 = p.L[1], L2 = p.L[2], L3 = p.L[3];
+      int c0 = (int)(a % L0);
+      int64_t rr = a / L0;
+      int c1 = (int)(rr % L1);
+      rr /= L1;
+      int c2 = (int)(rr % L2);
+      int c3 = (int)(rr / L2);
       const int nu = (h - 1) / 2, dir = ((h - 1) & 1) ? -1 : 1;
-      c[nu] = (c[nu] + dir + p.L[nu]) % p.L[nu];
-      nb = site_index(c, p.L);
+      if (nu == 0) c0 = (c0 + dir + L0) % L0;
+      else if (nu == 1) c1 = (c1 + dir + L1) % L1;
+      else if (nu == 2) c2 = (c2 + dir + L2) % L2;
+      else c3 = (c3 + dir + L3) % L3;
+      nb = ((int64_t)(c3 * L2 + c2) * L1 + c1) * L0 + c0;
     }
     const float2* Ab = p.A + ((int64_t)h * p.Vc + a) * nc * nc;  // column-major block
     __syncwarp();  // the previous task's buffers are free
@@ -425,10 +438,31 @@ __device__ void backsub(const CGArgs& p, int n, double2* Rs) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs p) {
+// tensor-core stencil phase: y = s_out D_c (s_in x) over all sites
+__device__ __forceinline__ bool cg_apply_tc(const CGArgs& p, CmShared& cs, unsigned char* dsm, unsigned& ph,
+                                            const float* x, float* y, const double* scale, int mode) {
+  CmArgs q;
+  q.A16 = p.A16;
+  q.L[0] = p.L[0]; q.L[1] = p.L[1]; q.L[2] = p.L[2]; q.L[3] = p.L[3];
+  q.Vc = p.Vc;
+  q.nc = p.nc;
+  q.x = x;
+  q.y = y;
+  q.mu = p.mu;
+  q.dmu = p.dmu;
+  q.scale = scale;
+  q.mode = mode;
+  q.nsys = p.nsys;
+  q.nbuf = p.cm_nbuf;
+  q.err = p.err;
+  return cm_apply(q, cs, dsm, ph, blockIdx.x, p.G);
+}
+
+__device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* dyn) {
   __shared__ double sm[(CG_THREADS / 32) * CG_IVEC * 4];
   __shared__ float4 hsm[CG_MAXM + 1];  // H column (or y) of this CTA's two systems
-  extern __shared__ float4 dyn[];
+  unsigned ph = 0;  // barrier parities of the tensor-core stencil
+  unsigned char* dsm = reinterpret_cast<unsigned char*>(dyn);
   const int b = blockIdx.x;
   const int tile = b % p.nt;
   const int slice = b / p.nt;
@@ -460,6 +494,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs p) {
     const double beta = sqrt(fmax(s.x, 0.0));
     p.tolabs[n] = p.tol * beta;
     const bool on = beta > 0.0 && isfinite(beta);
+    p.b0[n] = on ? beta : 0.0;
     p.active[n] = on;
     p.done[n] = !on;
     p.sc[n] = on ? 1.0 / beta : 0.0;
@@ -474,9 +509,16 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs p) {
     int j = 0;
     for (; j < m && total < p.maxiter; ++j) {
       // P1: V_{j+1} = sc * A V_j   (V_j not yet scaled in place)
-      cg_apply_partials(p, p.V + (int64_t)j * p.vstride, dyn);
+      if (p.A16) {
+        if (!cg_apply_tc(p, cs, dsm, ph, p.V + (int64_t)j * p.vstride, p.V + (int64_t)(j + 1) * p.vstride, p.sc,
+                         CM_SCALE_IN))
+          return;
+      } else {
+        cg_apply_partials(p, p.V + (int64_t)j * p.vstride, dyn);
+      }
       if (!grid_barrier(p)) return;
-      cg_apply_sum(p, p.V + (int64_t)j * p.vstride, p.V + (int64_t)(j + 1) * p.vstride, tile, e0, estep);
+      if (!p.A16)
+        cg_apply_sum(p, p.V + (int64_t)j * p.vstride, p.V + (int64_t)(j + 1) * p.vstride, tile, e0, estep);
       // (P2 below touches only this thread's entries of V_j and V_{j+1}: no barrier needed)
       // P2: scale V_j in place (owner entries), then dots <V_i, w> for i <= j
       {
@@ -663,9 +705,13 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs p) {
     // restart: V0 = rc - A x, with sc = 1 for the apply
     if (gtid < p.nsys) p.sc[gtid] = 1.0;
     if (!grid_barrier(p)) return;
-    cg_apply_partials(p, p.xc, dyn);
+    if (p.A16) {
+      if (!cg_apply_tc(p, cs, dsm, ph, p.xc, p.V, p.b0, CM_SCALE_OUT)) return;
+    } else {
+      cg_apply_partials(p, p.xc, dyn);
+    }
     if (!grid_barrier(p)) return;
-    cg_apply_sum(p, p.xc, p.V, tile, e0, estep);
+    if (!p.A16) cg_apply_sum(p, p.xc, p.V, tile, e0, estep);
     {
       float4 nrm = make_float4(0, 0, 0, 0);
       for (int64_t e = e0; e < p.M; e += estep) {
@@ -696,6 +742,14 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs p) {
   if (gtid == 0) *p.iters = total;
 }
 
+__global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs p) {
+  __shared__ CmShared cs;
+  extern __shared__ __align__(128) float4 dyn[];
+  if (p.A16) cm_begin(cs);
+  cg_body(p, cs, dyn);
+  if (p.A16) cm_end(cs);
+}
+
 int CoarseGmres::alloc(int m_, int nsys_, int G_, size_t bundle_bytes) {
   if (m_ <= m && nsys_ <= NS && G_ <= G && bundle_bytes <= hbytes) return 0;
   release();
@@ -713,6 +767,7 @@ int CoarseGmres::alloc(int m_, int nsys_, int G_, size_t bundle_bytes) {
   A((void**)&g, sizeof(double2) * (size_t)(m + 1) * NS);
   A((void**)&y, sizeof(double2) * (size_t)m * NS);
   A((void**)&tolabs, sizeof(double) * NS);
+  A((void**)&b0, sizeof(double) * NS);
   A((void**)&sc, sizeof(double) * NS);
   A((void**)&kconv, sizeof(int) * NS);
   A((void**)&active, sizeof(int) * NS);
@@ -728,23 +783,32 @@ int CoarseGmres::alloc(int m_, int nsys_, int G_, size_t bundle_bytes) {
 }
 
 void CoarseGmres::release() {
-  void* ptrs[] = {H, cs, sn, g, y, tolabs, sc, kconv, active, done, nactive, part, bar, err, iters, hpart};
+  void* ptrs[] = {H, cs, sn, g, y, tolabs, b0, sc, kconv, active, done, nactive, part, bar, err, iters, hpart};
   for (void* q : ptrs) cudaFree(q);
   if (h_flags) cudaFreeHost(h_flags);
-  H = nullptr; cs = nullptr; sn = nullptr; g = nullptr; y = nullptr; tolabs = nullptr; sc = nullptr;
+  H = nullptr; cs = nullptr; sn = nullptr; g = nullptr; y = nullptr; tolabs = nullptr; b0 = nullptr; sc = nullptr;
   kconv = nullptr; active = nullptr; done = nullptr; nactive = nullptr; part = nullptr; bar = nullptr;
   err = nullptr; iters = nullptr; h_flags = nullptr; hpart = nullptr;
   m = 0; NS = 0; G = 0; hbytes = 0;
 }
 
-static size_t dyn_smem_bytes(int m) {
-  const size_t stage = sizeof(float4) * (size_t)(CG_THREADS / 32) * CG_WARP_F4;  // per-warp staging
-  const size_t rs = sizeof(double2) * (size_t)m * m;                                  // back substitution
+// dynamic shared memory: back substitution, and the stencil phase (FP32 per-warp staging, or
+// the tensor-core operand buffers with nbuf operator copies)
+static size_t dyn_smem_bytes(int m, int nc, int nsys, bool tc, int nbuf) {
+  const size_t rs = sizeof(double2) * (size_t)m * m;
+  const size_t stage = tc ? cm_smem_bytes(nc, cm_chunk(nsys), nbuf)
+                          : sizeof(float4) * (size_t)(CG_THREADS / 32) * CG_WARP_F4;
   return stage > rs ? stage : rs;
 }
 
-// the largest dynamic shared memory any supported restart length needs
-static size_t dyn_smem_cap() { return dyn_smem_bytes(CG_MAXM); }
+static size_t dyn_smem_cap() {
+  static size_t cap = 0;
+  if (!cap) {
+    cap = cm_dyn_cap((const void*)coarse_gmres_kernel);
+    cudaFuncSetAttribute(coarse_gmres_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+  }
+  return cap;
+}
 
 int coarse_gmres_grid(int nt) {
   static int per_sm = -1, sms = 0;
@@ -752,7 +816,6 @@ int coarse_gmres_grid(int nt) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(coarse_gmres_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem_cap());
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel, CG_THREADS, dyn_smem_cap());
     if (per_sm < 1) per_sm = 1;
   }
@@ -763,15 +826,23 @@ int coarse_gmres_grid(int nt) {
   return Gt * nt;
 }
 
-int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, const float* rc, float* xc, float* V,
-                       int64_t vstride, const double* mu, double dmu, int nsys, int m, int maxiter, double tol,
-                       int* iters_done, cudaStream_t st) {
+int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, const __half* A16, const float* rc,
+                       float* xc, float* V, int64_t vstride, const double* mu, double dmu, int nsys, int m,
+                       int maxiter, double tol, int* iters_done, cudaStream_t st) {
   const int nt = ntiles(nsys, 2);
   const int G = coarse_gmres_grid(nt);
   const size_t need = (size_t)nt * cd.nc * cd.Vc * 4 * sizeof(float);
   if (G > s.G || m > s.m || nsys > s.NS || m > CG_MAXM || cd.nc > 64 || (cd.nc % 2) || need > s.hbytes) return -2;
+  const size_t cap = dyn_smem_cap();
+  int nbuf = 2;
+  if (A16 && dyn_smem_bytes(m, cd.nc, nsys, true, 2) > cap) nbuf = 1;
+  const size_t dyn = dyn_smem_bytes(m, cd.nc, nsys, A16 != nullptr, nbuf);
+  if (dyn > cap) return -2;
   CGArgs p;
   p.A = A;
+  p.A16 = A16;
+  p.cm_nbuf = nbuf;
+  p.b0 = s.b0;
   for (int k = 0; k < 4; ++k) p.L[k] = cd.L[k];
   p.Vc = cd.Vc;
   p.nc = cd.nc;
@@ -797,7 +868,7 @@ int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, co
   cudaMemsetAsync(s.err, 0, sizeof(int), st);
   void* args[] = {&p};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)coarse_gmres_kernel, dim3(G), dim3(CG_THREADS), args,
-                                              dyn_smem_bytes(m), st);
+                                              dyn, st);
   TM_COUNT();
   if (e != cudaSuccess) return -1;
   cudaMemcpyAsync(s.h_flags, s.err, sizeof(int), cudaMemcpyDeviceToHost, st);

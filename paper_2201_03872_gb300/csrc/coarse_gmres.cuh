@@ -1,5 +1,7 @@
 // Persistent coarse-level GMRES (declarations). See coarse_gmres.cu.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "amg.cuh"
 
 namespace tmamg {
@@ -7,7 +9,7 @@ namespace tmamg {
 struct CoarseGmres {
   int m = 0, NS = 0, G = 0;
   double2 *H = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *part = nullptr;
-  double *cs = nullptr, *tolabs = nullptr, *sc = nullptr;
+  double *cs = nullptr, *tolabs = nullptr, *b0 = nullptr, *sc = nullptr;
   int *kconv = nullptr, *active = nullptr, *done = nullptr, *nactive = nullptr, *err = nullptr, *iters = nullptr;
   unsigned* bar = nullptr;
   int* h_flags = nullptr;
@@ -22,10 +24,11 @@ int coarse_gmres_grid(int nt);
 
 // xc ~ D_c(dmu mu)^{-1} rc by restarted GMRES(m) to |r| <= tol |rc| per system, at most
 // maxiter Arnoldi steps, in one cooperative launch. V: m + 1 coarse bundles (vstride floats
-// apart). If iters_done is non-null the call synchronises the stream and returns -3 when a
-// grid barrier timed out, else 0; -1 if the launch failed, -2 if the state is too small.
-int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, const float* rc, float* xc, float* V,
-                       int64_t vstride, const double* mu, double dmu, int nsys, int m, int maxiter, double tol,
-                       int* iters_done, cudaStream_t st);
+// apart). A16: the FP16 operator of the tensor-core stencil (coarse_mma.cuh), or null for the
+// FP32 stencil A. If iters_done is non-null the call synchronises the stream and returns -3
+// when a bounded wait timed out, else 0; -1 if the launch failed, -2 if the state is too small.
+int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, const __half* A16, const float* rc,
+                       float* xc, float* V, int64_t vstride, const double* mu, double dmu, int nsys, int m,
+                       int maxiter, double tol, int* iters_done, cudaStream_t st);
 
 }  // namespace tmamg

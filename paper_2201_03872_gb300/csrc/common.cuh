@@ -6,6 +6,7 @@
 // brings the same complex entry (re[T], im[T]) of T systems.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -53,7 +54,12 @@ struct CoarseLevel {
   int asize = 0;        // fine sites per aggregate
   float2* P = nullptr;  // [Vc][2 chi][nv][asize*6] for a fine parent (6 = 2 spins x 3 colours per chirality)
   float2* A = nullptr;  // [9][Vc][nc (col j)][nc (row i)]  coarse stencil blocks, column-major per block
+  __half* A16 = nullptr;  // the same blocks in FP16, in the operand layout of the tensor-core stencil
+  float* cmax = nullptr;  // [CM_MAXSYS] per-system range scratch of the stand-alone tensor-core stencil
+  int* cerr = nullptr;    // bounded-wait flag of the stand-alone tensor-core stencil
 };
+
+constexpr int CM_MAXSYS = 1024;  // systems per stand-alone tensor-core stencil call
 
 struct Workspace;
 struct NNState;

@@ -15,6 +15,7 @@
 #include "blas.cuh"
 #include "block_gmres.cuh"
 #include "coarse_gmres.cuh"
+#include "coarse_mma.cuh"
 #include "krylov.cuh"
 #include "nn.cuh"
 #include "sap.cuh"
@@ -231,9 +232,17 @@ int do_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec_field
   const int nc = 2 * nv;
   int rc = check_cuda(ctx, cudaMalloc(&lv.P, sizeof(float2) * (size_t)ad.Vc * 2 * nv * ad.asize * 6), "cudaMalloc(P)");
   if (!rc) rc = check_cuda(ctx, cudaMalloc(&lv.A, sizeof(float2) * 9 * (size_t)ad.Vc * nc * nc), "cudaMalloc(A)");
+  if (!rc && nc <= CM_MAXNC)
+    rc = check_cuda(ctx, cudaMalloc(&lv.A16, (size_t)cm_site_bytes(nc) * ad.Vc), "cudaMalloc(A16)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&lv.cmax, sizeof(float) * CM_MAXSYS), "cudaMalloc(cmax)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&lv.cerr, sizeof(int)), "cudaMalloc(cerr)");
+  if (!rc) rc = check_cuda(ctx, cudaMemsetAsync(lv.cerr, 0, sizeof(int), st), "cudaMemset(cerr)");
   if (rc) {
     cudaFree(lv.P);
     cudaFree(lv.A);
+    cudaFree(lv.A16);
+    cudaFree(lv.cmax);
+    cudaFree(lv.cerr);
     return rc;
   }
   ctx->levels.push_back(lv);
@@ -301,6 +310,7 @@ int do_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec_field
   CoarseLevel& L1 = ctx->levels[0];
   build_P(ad, Vt, L1.P, nv, 6, st);
   build_coarse_operator_fine(ad, ctx->U32, ctx->C32, L1.P, L1.A, nv, g.bc_t, W, Y, Rc, st);
+  if (L1.A16) pack_coarse_f16(coarse_dims(L1), L1.A, L1.A16, st);
   rc = check_cuda(ctx, cudaGetLastError(), "setup kernels");
   cudaError_t se = cudaStreamSynchronize(st);
   cudaFree(field);
@@ -337,6 +347,28 @@ __global__ void copy_beta_kernel(const double* b, double* dst, int n) {
   if (i < n) dst[i] = b[i];
 }
 
+// y = D_c x on level l: FP16 operator on the tensor cores (precision 16, or 0 = default) or
+// the FP32 stencil (precision 32); false if the sizes are outside the tensor-core path
+static bool coarse_apply_level(const CoarseLevel& l, int precision, const float* x, float* y, const double* mu,
+                               double dmu, int nsys, cudaStream_t st) {
+  const CoarseDims cd = coarse_dims(l);
+  if (precision != 32) {
+    if (!l.A16 || nsys > CM_MAXSYS) return false;
+    return coarse_apply_f16(cd, l.A16, x, y, mu, dmu, nsys, l.cmax, l.cerr, st) == 0;
+  }
+  coarse_apply(cd, l.A, x, y, mu, dmu, nsys, st);
+  return true;
+}
+
+// the stand-alone tensor-core stencil records a bounded wait that gave up in l.cerr: read and clear
+static bool coarse_apply_timed_out(const CoarseLevel& l, cudaStream_t st) {
+  int h = 0;
+  cudaMemcpyAsync(&h, l.cerr, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  if (h) cudaMemsetAsync(l.cerr, 0, sizeof(int), st);
+  return h != 0;
+}
+
 // xc ~ D_c^{-1} rc by restarted GMRES to the relative residual coarse_tol
 static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
   tmamg_ctx* ctx = S.ctx;
@@ -347,7 +379,8 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
   if (S.sp->coarse_solver == 0) {
     // persistent kernel: the whole restarted GMRES in one cooperative launch
     int it = 0;
-    int rc_ = coarse_gmres_solve(w->cg, cd, L1.A, rc, xc, w->Vc, (int64_t)(w->cb32 / sizeof(float)), S.mu,
+    const __half* A16 = S.sp->coarse_precision != 32 ? L1.A16 : nullptr;
+    int rc_ = coarse_gmres_solve(w->cg, cd, L1.A, A16, rc, xc, w->Vc, (int64_t)(w->cb32 / sizeof(float)), S.mu,
                                  S.sp->delta_mu, S.nsys, S.sp->coarse_restart, S.sp->coarse_maxiter,
                                  S.sp->coarse_tol, &it, st);
     if (rc_ == -3) S.timeout = true;
@@ -365,7 +398,10 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
     const double dmu = S.sp->delta_mu;
     const double* mu = S.mu;
     const int nsys = S.nsys;
-    auto apply = [&, dmu, mu, nsys](const float* x, float* y) { coarse_apply(cd, L1.A, x, y, mu, dmu, nsys, st); };
+    const int prec = S.sp->coarse_precision;
+    auto apply = [&, dmu, mu, nsys, prec](const float* x, float* y) {
+      if (!coarse_apply_level(L1, prec, x, y, mu, dmu, nsys, st)) S.launch_error = true;
+    };
     int it = 0;
     int rc_ = block_gmres_solve(w->bg, apply, rc, xc, w->Vc, (int64_t)(w->cb32 / sizeof(float)), w->tc, w->cb32,
                                 S.sp->coarse_restart, S.sp->coarse_maxiter, S.sp->coarse_tol, &it, st);
@@ -381,7 +417,10 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
   ops.M = M;
   const double dmu = S.sp->delta_mu;
   const double* mu = S.mu;
-  ops.A = [&, dmu, mu, nsys](const float* x, float* y) { coarse_apply(cd, L1.A, x, y, mu, dmu, nsys, st); };
+  const int prec = S.sp->coarse_precision;
+  ops.A = [&, dmu, mu, nsys, prec](const float* x, float* y) {
+    if (!coarse_apply_level(L1, prec, x, y, mu, dmu, nsys, st)) S.launch_error = true;
+  };
   cudaMemsetAsync(xc, 0, w->cb32, st);
   cudaMemcpyAsync(w->Vc, rc, w->cb32, cudaMemcpyDeviceToDevice, st);
   set_rel_tol(w->rel_coarse, nsys, S.sp->coarse_tol, st);
@@ -394,7 +433,7 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
     if (cyc == 0) copy_beta_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->coarse.beta, w->beta0, nsys); TM_COUNT();
     if (r.iters < m || done >= S.sp->coarse_maxiter) break;  // every system converged inside the cycle
     // restart from the true coarse residual
-    coarse_apply(cd, L1.A, xc, w->Vc, mu, dmu, nsys, st);
+    ops.A(xc, w->Vc);
     axpby<float>(w->ones, 2, rc, w->mones, 2, w->Vc, M, nsys, nullptr, st);
     mdot<float>(w->Vc, 0, 1, w->Vc, M, nsys, w->dot, nsys, w->coarse.partial, st);
     restart_tol_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->beta0, S.sp->coarse_tol, w->rel_coarse, nsys); TM_COUNT();
@@ -488,6 +527,8 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
       sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: bad parameters");
   if (sp->precision != 32) return set_err(ctx, TMAMG_ERR_ARG, "solve: precision 64 path not available yet");
+  if (sp->coarse_precision != 0 && sp->coarse_precision != 16 && sp->coarse_precision != 32)
+    return set_err(ctx, TMAMG_ERR_ARG, "solve: coarse_precision must be 16 or 32");
   if (sp->coarse_solver < 0 || sp->coarse_solver > 2)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: coarse_solver must be 0, 1 or 2");
   if (sp->coarse_solver == 1 && nrhs > 16)
@@ -576,7 +617,8 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   cudaFree(xstage);
   if (!rc) rc = check_cuda(ctx, se, "solve");
   if (!rc && S.launch_error) rc = set_err(ctx, TMAMG_ERR_CUDA, "solve: cooperative coarse-solver launch failed");
-  if (!rc && S.timeout) rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "solve: a coarse-solver grid barrier timed out");
+  if (!rc && coarse_apply_timed_out(ctx->levels[0], st)) S.timeout = true;
+  if (!rc && S.timeout) rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "solve: a coarse-solver bounded wait timed out");
   if (rc) return rc;
   int all_ok = 1;
   for (int n = 0; n < nsys; ++n) {
@@ -678,7 +720,8 @@ int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* x
     return set_err(ctx, TMAMG_ERR_ARG, "coarse_solve: bad argument");
   const int nsys = nrhs * nshift;
   if (nsys > 256 || p->coarse_solver < 0 || p->coarse_solver > 2 || (p->coarse_solver == 1 && nrhs > 16) ||
-      p->coarse_restart < 1 || p->coarse_restart > 64 || p->coarse_maxiter < 1)
+      p->coarse_restart < 1 || p->coarse_restart > 64 || p->coarse_maxiter < 1 ||
+      (p->coarse_precision != 0 && p->coarse_precision != 16 && p->coarse_precision != 32))
     return set_err(ctx, TMAMG_ERR_ARG, "coarse_solve: bad parameters");
   int rc = ensure_ws(ctx, nsys, p->restart, p->coarse_restart);
   if (rc) return rc;
@@ -691,21 +734,29 @@ int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* x
   coarse_solve(S, (const float*)rc_bundle, (float*)xc_bundle);
   rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "coarse_solve");
   if (!rc && S.launch_error) rc = set_err(ctx, TMAMG_ERR_CUDA, "coarse_solve: launch failed");
-  if (!rc && S.timeout) rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "coarse_solve: a grid barrier timed out");
+  if (!rc && coarse_apply_timed_out(ctx->levels[0], ctx->stream)) S.timeout = true;
+  if (!rc && S.timeout) rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "coarse_solve: a bounded wait timed out");
   if (iterations) *iterations = S.coarse_iters;
   return rc;
 }
 
-int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_bundle, int nsys, const double* mu) {
+int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_bundle, int nsys, const double* mu,
+                       int precision) {
   if (!ctx) return TMAMG_ERR_ARG;
   if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "coarse_apply: no setup");
-  if (level != 1 || !x_bundle || !y_bundle || !mu || nsys < 1 || x_bundle == y_bundle)
+  if (level != 1 || !x_bundle || !y_bundle || !mu || nsys < 1 || x_bundle == y_bundle ||
+      (precision != 16 && precision != 32))
     return set_err(ctx, TMAMG_ERR_ARG, "coarse_apply: bad argument");
   int rc = upload_mu(ctx, mu, nsys);
   if (rc) return rc;
   const CoarseLevel& l = ctx->levels[0];
-  coarse_apply(coarse_dims(l), l.A, (const float*)x_bundle, (float*)y_bundle, ctx->mu_dev, 1.0, nsys, ctx->stream);
-  return check_cuda(ctx, cudaGetLastError(), "coarse_apply launch");
+  if (!coarse_apply_level(l, precision, (const float*)x_bundle, (float*)y_bundle, ctx->mu_dev, 1.0, nsys,
+                          ctx->stream))
+    return set_err(ctx, TMAMG_ERR_ARG, "coarse_apply: sizes outside the tensor-core stencil");
+  rc = check_cuda(ctx, cudaGetLastError(), "coarse_apply launch");
+  if (!rc && coarse_apply_timed_out(l, ctx->stream))
+    rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "coarse_apply: a bounded wait timed out");
+  return rc;
 }
 
 }  // extern "C"

@@ -36,7 +36,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_outer", ctypes.c_int),
                 ("coarse_tol", ctypes.c_double), ("coarse_restart", ctypes.c_int), ("coarse_maxiter", ctypes.c_int),
                 ("coarse_solver", ctypes.c_int), ("delta_mu", ctypes.c_double), ("precision", ctypes.c_int),
-                ("use_nn", ctypes.c_int), ("poll", ctypes.c_int)]
+                ("use_nn", ctypes.c_int), ("poll", ctypes.c_int), ("coarse_precision", ctypes.c_int)]
 
 
 class SystemStats(ctypes.Structure):
@@ -99,7 +99,7 @@ SIGNATURES = {
     "tmamg_sap_noalloc": (I, [P, P, P, I, P, ctypes.POINTER(ctypes.c_int), I, I]),
     "tmamg_restrict": (I, [P, I, P, P, I]),
     "tmamg_prolong": (I, [P, I, P, P, I]),
-    "tmamg_coarse_apply": (I, [P, I, P, P, I, P]),
+    "tmamg_coarse_apply": (I, [P, I, P, P, I, P, I]),
     "tmamg_coarse_solve": (I, [P, I, P, P, I, P, I, ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_int)]),
     "tmamg_default_nn_params": (None, [ctypes.POINTER(NNParams)]),
     "tmamg_nn_init": (I, [P, ctypes.c_uint64]),
@@ -291,10 +291,11 @@ def tmamg_prolong(ctx, level, coarse_bundle, fine_bundle, nsys):
                                                             _ptr(fine_bundle), int(nsys)))
 
 
-def tmamg_coarse_apply(ctx, level, x_bundle, y_bundle, nsys, mu):
+def tmamg_coarse_apply(ctx, level, x_bundle, y_bundle, nsys, mu, precision=16):
     m = _f64(mu)
     return _check("tmamg_coarse_apply", ctx, lib().tmamg_coarse_apply(ctx, int(level), _ptr(x_bundle),
-                                                                      _ptr(y_bundle), int(nsys), _ptr(m)))
+                                                                      _ptr(y_bundle), int(nsys), _ptr(m),
+                                                                      int(precision)))
 
 
 def tmamg_coarse_solve(ctx, level, rc_bundle, xc_bundle, nrhs, mu, nshift, params):

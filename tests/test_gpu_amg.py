@@ -92,13 +92,61 @@ def test_coarse_operator_matches_oracle(L, agg, nv):
         mu = np.linspace(-0.1, 0.3, nsys)
         xb = lat.torch.from_numpy(coarse_to_bundle(x, nc, Vc)).cuda()
         yb = lat.coarse_buffer(nsys)
-        lat.T.tmamg_coarse_apply(lat.ctx, 1, xb, yb, nsys, mu)
+        lat.T.tmamg_coarse_apply(lat.ctx, 1, xb, yb, nsys, mu, 32)
         lat.torch.cuda.synchronize()
         y = coarse_from_bundle(yb.cpu().numpy(), nsys, nc, Vc)
         Lxc, Lyc, Lzc, Ltc = P.Lc
         ref = cl.apply(x.reshape(nsys, Ltc, Lzc, Lyc, Lxc, 2, nv), mu).reshape(nsys, Vc, nc)
         for n in range(nsys):
             assert relerr(y[n], ref[n]) < TOL32, relerr(y[n], ref[n])
+    finally:
+        lat.close()
+
+
+# FP16 tensor-core stencil: both operands are rounded to FP16 (unit roundoff 2^-11 each) and the
+# 18 ncp products of one output entry are summed in FP32 (allowing a truncating accumulator,
+# 2^-23 per addition); the elementwise bound is therefore (2^-10 + 18 ncp 2^-22) (|A| |x|)_i,
+# with (|A| |x|)_i from the oracle's blocks. The power-of-two scaling keeps max |x_n| in
+# [1/2, 1), so entries below 2^-14 max|x_n| meet the subnormal grid (absolute 2^-25 max|x_n|).
+def _f16_bound(absb, rowsum, ncp, xmax):
+    return (2.0 ** -10 + 18 * ncp * 2.0 ** -22) * absb + 2.0 ** -24 * xmax * rowsum
+
+
+@pytest.mark.parametrize("L,agg,nv,nsys", [((4, 4, 4, 4), (2, 2, 2, 2), 8, 5),
+                                           ((8, 4, 4, 8), (4, 2, 2, 4), 12, 21),
+                                           ((8, 4, 4, 8), (4, 2, 2, 4), 12, 2)])
+def test_coarse_apply_tensor_cores_within_fp16_bound(L, agg, nv, nsys):
+    lat, op, P, cl = _setup_pair(L, agg, nv)
+    try:
+        Vc = int(np.prod(P.Lc))
+        nc = 2 * nv
+        ncp = (nc + 7) // 8 * 8
+        x = synth.complex_normal(82, 1, (nsys, Vc, nc))
+        # one zero system and systems far from unit range exercise the per-system scaling
+        x[0] = 0
+        if nsys > 2:
+            x[1] *= 1e-6
+            x[2] *= 3e4
+        mu = np.linspace(-0.1, 0.3, nsys)
+        xb = lat.torch.from_numpy(coarse_to_bundle(x, nc, Vc)).cuda()
+        yb = lat.coarse_buffer(nsys)
+        lat.T.tmamg_coarse_apply(lat.ctx, 1, xb, yb, nsys, mu, 16)
+        lat.torch.cuda.synchronize()
+        y = coarse_from_bundle(yb.cpu().numpy(), nsys, nc, Vc)
+        Lxc, Lyc, Lzc, Ltc = P.Lc
+        shp = (Ltc, Lzc, Lyc, Lxc, 2, nv)
+        cl_abs = amg.CoarseLevel(np.abs(cl.A), P.Lc, nv)
+        rowsum = cl_abs.apply(np.ones(shp), 0.0).real.reshape(Vc, nc)
+        assert np.all(y[0] == 0)
+        for n in range(nsys):
+            ref = cl.apply(x[n].reshape(shp), mu[n]).reshape(Vc, nc)
+            # the twist term stays in FP32 (relative 2^-23 of |mu| |x|)
+            absb = cl_abs.apply(np.abs(x[n]).reshape(shp), 0.0).real.reshape(Vc, nc) + abs(mu[n]) * np.abs(x[n])
+            bound = _f16_bound(absb, rowsum, ncp, np.abs(x[n]).max())
+            err = np.abs(y[n] - ref)
+            assert np.all(err <= bound + 1e-300), (n, float((err / np.maximum(bound, 1e-300)).max()))
+            if n > 0:
+                assert relerr(y[n], ref) < 2e-3
     finally:
         lat.close()
 
@@ -135,8 +183,8 @@ def test_solve_tiny_configuration():
     assert np.linalg.norm(x[0, 0].ravel() - xd) <= np.linalg.cond(M) * 1e-10 * np.linalg.norm(xd)
 
 
-@pytest.mark.parametrize("coarse_solver", [0, 1, 2])
-def test_solve_multi_rhs_multi_shift(coarse_solver):
+@pytest.mark.parametrize("coarse_solver,coarse_precision", [(0, 16), (1, 16), (2, 16), (0, 32), (2, 32)])
+def test_solve_multi_rhs_multi_shift(coarse_solver, coarse_precision):
     L = (8, 4, 4, 8)
     U = synth.gauge_field(L, 0.3, seed=3)
     kappa = 0.126
@@ -144,7 +192,8 @@ def test_solve_multi_rhs_multi_shift(coarse_solver):
     mus = [0.001, 0.02, 0.3]
     rc, stats, x = _solve(L, U, kappa, 1.0, b, mus,
                           dict(agg=(4, 2, 2, 4), nv=12, sap_block=(2, 2, 2, 2), setup_iters=4),
-                          dict(restart=10, tol=1e-10, coarse_solver=coarse_solver))
+                          dict(restart=10, tol=1e-10, coarse_solver=coarse_solver,
+                               coarse_precision=coarse_precision))
     op = dirac.Operator(U, kappa, 1.0)
     assert rc == 0
     for r in range(3):

@@ -78,29 +78,28 @@ struct CGArgs {
   int NS;  // stride of the per-system arrays
 };
 
+// Grid barrier on a monotonic arrival counter (zeroed before the launch): barrier number k
+// is complete once the counter reaches k G. The CTA's writes are published by bar.sync plus
+// the release of thread 0's increment; the acquire load that sees the count makes every
+// other CTA's writes visible to this CTA (cross-CTA data is then read through L2).
 __device__ __forceinline__ bool grid_barrier(const CGArgs& p) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = p.bar + 1;
-    unsigned g0 = *vgen;
-    __threadfence();
-    unsigned prev = atomicAdd(p.bar, 1u);
-    if (prev == (unsigned)p.G - 1) {
-      atomicExch(p.bar, 0u);
-      __threadfence();
-      atomicAdd(p.bar + 1, 1u);
-    } else {
-      long long t0 = clock64();
-      while (*vgen == g0) {
-        if (clock64() - t0 > 2000000000LL) {  // about one second at 2 GHz
-          atomicExch(p.err, 1);
-          break;
-        }
-        if (*(volatile int*)p.err) break;  // another CTA gave up
-        __nanosleep(32);
+    unsigned prev;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;\n" : "=r"(prev) : "l"(p.bar) : "memory");
+    const unsigned G = (unsigned)p.G;
+    const unsigned target = (prev / G + 1) * G;
+    const long long t0 = clock64();
+    while (true) {
+      unsigned cur;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(cur) : "l"(p.bar) : "memory");
+      if ((int)(cur - target) >= 0) break;
+      if (clock64() - t0 > 2000000000LL) {  // about one second at 2 GHz
+        atomicExch(p.err, 1);
+        break;
       }
+      if (*(volatile int*)p.err) break;  // another CTA gave up
     }
-    __threadfence();
   }
   __syncthreads();
   return *(volatile int*)p.err == 0;
@@ -304,15 +303,15 @@ __device__ void cta_reduce_store(const CGArgs& p, float4* vals, int nv, int slot
 __device__ double2 part_sum(const CGArgs& p, int i, int n) {
   const int t = n / 2, ln = n % 2;
   double2 s = make_double2(0, 0);
-  for (int sl0 = 0; sl0 < p.Gt; sl0 += 8) {
-    double2 v[8];
+  for (int sl0 = 0; sl0 < p.Gt; sl0 += 32) {
+    double2 v[32];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 32; ++k) {
       const int sl = sl0 + k;
       v[k] = sl < p.Gt ? ldx(p.part + ((int64_t)(sl * p.nt + t) * (p.m + 2) + i) * 2 + ln) : make_double2(0, 0);
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 32; ++k) {
       s.x += v[k].x;
       s.y += v[k].y;
     }
@@ -325,36 +324,21 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
 
-// Givens step for system n at Arnoldi step j, with H[j+1][j] = hn
-__device__ void givens_step(const CGArgs& p, int n, int j, double hn, int total) {
+// Givens step for system n at Arnoldi step j, with H[j+1][j] = hn. The rotations of the
+// cycle stay in the calling thread's own arrays c_, s_ (the same thread handles system n at
+// every step), so only the new column is fetched.
+__device__ void givens_step(const CGArgs& p, int n, int j, double hn, int total, double* c_, double2* s_) {
   const int NS = p.NS, m = p.m;
   double2* col = p.H + (int64_t)j * (m + 1) * NS;
   double2 cv[CG_MAXM + 1];
-  double c_[CG_MAXM];
-  double2 s_[CG_MAXM];
-  // operands fetched eight at a time into registers before they are parked in local memory
-  for (int i0 = 0; i0 <= j; i0 += 8) {
-    double2 t[8];
+  // the column fetched sixteen entries at a time into registers before it is parked in local memory
+  for (int i0 = 0; i0 <= j; i0 += 16) {
+    double2 t[16];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) t[k] = i0 + k <= j ? ldx(col + (i0 + k) * NS + n) : make_double2(0, 0);
+    for (int k = 0; k < 16; ++k) t[k] = i0 + k <= j ? ldx(col + (i0 + k) * NS + n) : make_double2(0, 0);
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 16; ++k)
       if (i0 + k <= j) cv[i0 + k] = t[k];
-  }
-  for (int i0 = 0; i0 < j; i0 += 8) {
-    double tc[8];
-    double2 ts[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      tc[k] = i0 + k < j ? ldx(p.cs + (i0 + k) * NS + n) : 0.0;
-      ts[k] = i0 + k < j ? ldx(p.sn + (i0 + k) * NS + n) : make_double2(0, 0);
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (i0 + k < j) {
-        c_[i0 + k] = tc[k];
-        s_[i0 + k] = ts[k];
-      }
   }
   cv[j + 1] = make_double2(hn, 0);
   for (int i = 0; i < j; ++i) {
@@ -382,8 +366,8 @@ __device__ void givens_step(const CGArgs& p, int n, int j, double hn, int total)
   cv[j] = na == 0.0 ? make_double2(r, 0) : make_double2(a.x / na * r, a.y / na * r);
   cv[j + 1] = make_double2(0, 0);
   for (int i = 0; i <= j + 1; ++i) col[i * NS + n] = cv[i];
-  p.cs[j * NS + n] = c;
-  p.sn[j * NS + n] = sn;
+  c_[j] = c;
+  s_[j] = sn;
   const double2 gj = p.g[j * NS + n];
   const double2 t = cmul(conjd(sn), gj);
   p.g[(j + 1) * NS + n] = make_double2(-t.x, -t.y);
@@ -462,6 +446,8 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
   __shared__ double sm[(CG_THREADS / 32) * CG_IVEC * 4];
   __shared__ float4 hsm[CG_MAXM + 1];  // H column (or y) of this CTA's two systems
   unsigned ph = 0;  // barrier parities of the tensor-core stencil
+  double gc[CG_MAXM];   // Givens rotations of the current cycle (used by the threads gtid < nsys)
+  double2 gs[CG_MAXM];
   unsigned char* dsm = reinterpret_cast<unsigned char*>(dyn);
   const int b = blockIdx.x;
   const int tile = b % p.nt;
@@ -567,19 +553,23 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
         }
       }
       if (!grid_barrier(p)) return;
-      // P3: H[i][j] = sum of partials (one thread per (i, n))
-      if (gtid < (j + 1) * p.nsys) {
-        const int i = gtid / p.nsys, n = gtid % p.nsys;
-        p.H[((int64_t)j * (m + 1) + i) * NS + n] = part_sum(p, i, n);
-      }
-      if (!grid_barrier(p)) return;
-      // P4: w -= sum_i H[i][j] V_i (owner entries) and |w|^2 partials
+      // P3 + P4: every CTA sums the H column of its tile's two systems from the partials
+      // (the same fixed order everywhere; slice 0 stores it for P5), then
+      // w -= sum_i H[i][j] V_i (owner entries) and |w|^2 partials
       {
+        double* hd = reinterpret_cast<double*>(sm);  // [j + 1][2 lanes] (re, im)
+        if (threadIdx.x < 2 * (j + 1)) {
+          const int i = threadIdx.x >> 1, ln = threadIdx.x & 1;
+          const int n = 2 * tile + ln;
+          const double2 h = n < p.nsys ? part_sum(p, i, n) : make_double2(0, 0);
+          if (slice == 0 && n < p.nsys) p.H[((int64_t)j * (m + 1) + i) * NS + n] = h;
+          hd[(i * 2 + ln) * 2] = h.x;
+          hd[(i * 2 + ln) * 2 + 1] = h.y;
+        }
+        __syncthreads();
         if (threadIdx.x <= j) {
           const int i = threadIdx.x;
-          const double2 h0 = n0 < p.nsys ? ldx(p.H + ((int64_t)j * (m + 1) + i) * NS + n0) : make_double2(0, 0);
-          const double2 h1 = n1 < p.nsys ? ldx(p.H + ((int64_t)j * (m + 1) + i) * NS + n1) : make_double2(0, 0);
-          hsm[i] = make_float4((float)h0.x, (float)h0.y, (float)h1.x, (float)h1.y);
+          hsm[i] = make_float4((float)hd[i * 4], (float)hd[i * 4 + 1], (float)hd[i * 4 + 2], (float)hd[i * 4 + 3]);
         }
         __syncthreads();
         float* w = p.V + (int64_t)(j + 1) * p.vstride + toff;
@@ -630,7 +620,7 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
         const double2 s = part_sum(p, m + 1, n);
         const double hn = sqrt(fmax(s.x, 0.0));
         p.sc[n] = hn > 0 ? 1.0 / hn : 0.0;
-        if (p.active[n]) givens_step(p, n, j, hn, total);
+        if (p.active[n]) givens_step(p, n, j, hn, total, gc, gs);
       }
       if (b == 0) {
         __syncthreads();

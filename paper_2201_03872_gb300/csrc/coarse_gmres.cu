@@ -324,9 +324,9 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
 
-// Givens step for system n at Arnoldi step j, with H[j+1][j] = hn. The rotations of the
+// Givens step for system n on Arnoldi column j, with H[j+1][j] = hn. The rotations of the
 // cycle stay in the calling thread's own arrays c_, s_ (the same thread handles system n at
-// every step), so only the new column is fetched.
+// every step), so only the new column is fetched. total: Arnoldi steps done before step j.
 __device__ void givens_step(const CGArgs& p, int n, int j, double hn, int total, double* c_, double2* s_) {
   const int NS = p.NS, m = p.m;
   double2* col = p.H + (int64_t)j * (m + 1) * NS;
@@ -383,6 +383,16 @@ __device__ void givens_step(const CGArgs& p, int n, int j, double hn, int total,
   }
 }
 
+// The rotations of column j for every active system, by threads n < nsys of CTA 0 (the same
+// thread per system at every step; H[j+1][j] was stored by the norm phase of step j).
+__device__ __forceinline__ void givens_column(const CGArgs& p, int j, int total, double* gc, double2* gs) {
+  const int n = threadIdx.x;
+  if (n < p.nsys && ldx(p.active + n)) {
+    const double hn = ldx(p.H + ((int64_t)j * (p.m + 1) + j + 1) * p.NS + n).x;
+    givens_step(p, n, j, hn, total, gc, gs);
+  }
+}
+
 // y = R^{-1} g for system n: the CTA stages R in shared memory, warp 0 substitutes
 __device__ void backsub(const CGArgs& p, int n, double2* Rs) {
   const int NS = p.NS, m = p.m;
@@ -424,7 +434,8 @@ __device__ void backsub(const CGArgs& p, int n, double2* Rs) {
 
 // tensor-core stencil phase: y = s_out D_c (s_in x) over all sites
 __device__ __forceinline__ bool cg_apply_tc(const CGArgs& p, CmShared& cs, unsigned char* dsm, unsigned& ph,
-                                            const float* x, float* y, const double* scale, int mode) {
+                                            const float* x, float* y, const double* scale, int mode, int cta,
+                                            int ncta) {
   CmArgs q;
   q.A16 = p.A16;
   q.L[0] = p.L[0]; q.L[1] = p.L[1]; q.L[2] = p.L[2]; q.L[3] = p.L[3];
@@ -439,7 +450,7 @@ __device__ __forceinline__ bool cg_apply_tc(const CGArgs& p, CmShared& cs, unsig
   q.nsys = p.nsys;
   q.nbuf = p.cm_nbuf;
   q.err = p.err;
-  return cm_apply(q, cs, dsm, ph, blockIdx.x, p.G);
+  return cm_apply(q, cs, dsm, ph, cta, ncta);
 }
 
 __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* dyn) {
@@ -459,6 +470,7 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
   const int gtid = b * CG_THREADS + threadIdx.x;
   const int m = p.m;
   const int n0 = 2 * tile, n1 = 2 * tile + 1;
+  const int GG = p.G > 1 ? 1 : 0;  // CTAs kept free of stencil sites for the Givens rotations
 
   // ---- start: x = 0, V0 = rc, |rc| per system
   {
@@ -494,14 +506,18 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
   while (true) {
     int j = 0;
     for (; j < m && total < p.maxiter; ++j) {
-      // P1: V_{j+1} = sc * A V_j   (V_j not yet scaled in place)
+      // P1: V_{j+1} = sc * A V_j   (V_j not yet scaled in place). The Givens rotations of the
+      // previous column run at the same time on CTA 0, which (on the tensor-core path) takes no
+      // stencil sites: the stop test lags the Arnoldi process by one step, and the solution
+      // uses the converged column count, so the extra step changes nothing in it.
       if (p.A16) {
-        if (!cg_apply_tc(p, cs, dsm, ph, p.V + (int64_t)j * p.vstride, p.V + (int64_t)(j + 1) * p.vstride, p.sc,
-                         CM_SCALE_IN))
+        if (b >= GG && !cg_apply_tc(p, cs, dsm, ph, p.V + (int64_t)j * p.vstride, p.V + (int64_t)(j + 1) * p.vstride,
+                                    p.sc, CM_SCALE_IN, b - GG, p.G - GG))
           return;
       } else {
         cg_apply_partials(p, p.V + (int64_t)j * p.vstride, dyn);
       }
+      if (j > 0 && b == 0) givens_column(p, j - 1, total - 1, gc, gs);
       if (!grid_barrier(p)) return;
       if (!p.A16)
         cg_apply_sum(p, p.V + (int64_t)j * p.vstride, p.V + (int64_t)(j + 1) * p.vstride, tile, e0, estep);
@@ -614,29 +630,38 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
         cta_reduce_store(p, &nrm, 1, m + 1, sm);
       }
       if (!grid_barrier(p)) return;
-      // P5: H[j+1][j] = |w|, Givens rotation, convergence masks (one thread per system)
-      if (gtid < p.nsys) {
-        const int n = gtid;
+      // P5: H[j+1][j] = |w| and sc = 1 / |w| (one thread per system)
+      if (b == 0 && threadIdx.x < p.nsys) {
+        const int n = threadIdx.x;
         const double2 s = part_sum(p, m + 1, n);
         const double hn = sqrt(fmax(s.x, 0.0));
         p.sc[n] = hn > 0 ? 1.0 / hn : 0.0;
-        if (p.active[n]) givens_step(p, n, j, hn, total, gc, gs);
-      }
-      if (b == 0) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          int c = 0;
-          for (int n = 0; n < p.nsys; ++n) c += p.active[n];
-          *p.nactive = c;
-        }
+        p.H[((int64_t)j * (m + 1) + j + 1) * NS + n] = make_double2(hn, 0);
       }
       ++total;
       if (!grid_barrier(p)) return;
-      if (*(volatile int*)p.nactive == 0) {
-        ++j;
-        break;
+      {
+        // active systems left (warp 0 of every CTA counts; the flags were last written
+        // before the barrier)
+        __shared__ int nact;
+        if (threadIdx.x < 32) {
+          int c = 0;
+          for (int n = threadIdx.x; n < p.nsys; n += 32) c += ldx(p.active + n);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+          if (threadIdx.x == 0) nact = c;
+        }
+        __syncthreads();
+        if (nact == 0) {
+          ++j;
+          break;
+        }
       }
     }
+    // rotations of the cycle's last column (the loop ended on the cycle length or the step
+    // budget; systems that converged earlier are inactive already)
+    if (j > 0 && b == 0) givens_column(p, j - 1, total - 1, gc, gs);
+    if (!grid_barrier(p)) return;
     // y = R^{-1} g per system (a CTA per system), then x += sum_i y_i V_i
     for (int n = b; n < p.nsys; n += p.G) backsub(p, n, reinterpret_cast<double2*>(dyn));
     if (!grid_barrier(p)) return;
@@ -696,7 +721,7 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
     if (gtid < p.nsys) p.sc[gtid] = 1.0;
     if (!grid_barrier(p)) return;
     if (p.A16) {
-      if (!cg_apply_tc(p, cs, dsm, ph, p.xc, p.V, p.b0, CM_SCALE_OUT)) return;
+      if (!cg_apply_tc(p, cs, dsm, ph, p.xc, p.V, p.b0, CM_SCALE_OUT, b, p.G)) return;
     } else {
       cg_apply_partials(p, p.xc, dyn);
     }

@@ -184,6 +184,54 @@ __device__ __forceinline__ uint32_t cm_pack2(float a, float b) {
   return d;
 }
 
+// one staging item of the B operands: the eight components 8g .. 8g+7 of tile c TP + tp at
+// the neighbour of hop h (item = (h TP + tp) MG + g), scaled per system
+__device__ __forceinline__ void cm_item_load(const CmArgs& q, const CmShared& cs, int item, int c, int MG, int TP,
+                                             int nt, float4* v) {
+  const int g = item % MG;
+  const int r = item / MG;
+  const int tp = r % TP, h = r / TP;
+  const int t = c * TP + tp;
+  const int64_t nbh = cs.nb[h];
+  const int nc = q.nc;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int j = 8 * g + u;
+    v[u] = (t < nt && j < nc) ? __ldcg(reinterpret_cast<const float4*>(q.x + ((((int64_t)t * nc + j) * q.Vc) + nbh) * 4))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// rows n = 4 tp + q' of B^T at k-groups g (Re half of K) and MG + g (Im half):
+// q' = 0: (Re x_{2t}, -Im x_{2t}); 1: (Re x_{2t+1}, -Im x_{2t+1}); 2: (Im x_{2t}, Re x_{2t});
+// 3: (Im x_{2t+1}, Re x_{2t+1})
+__device__ __forceinline__ void cm_item_store(const CmShared& cs, unsigned char* sB, int item, int MG, int TP, int NG,
+                                              uint32_t BH, const float4* vin) {
+  const int g = item % MG;
+  const int r = item / MG;
+  const int tp = r % TP, h = r / TP;
+  const float s0 = cs.sin_[2 * tp], s1 = cs.sin_[2 * tp + 1];
+  float4 v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) v[u] = make_float4(vin[u].x * s0, vin[u].y * s1, vin[u].z * s0, vin[u].w * s1);
+  unsigned char* hb = sB + (size_t)h * BH;
+  const int n0 = 4 * tp;
+  const uint32_t rowoff = (uint32_t)((n0 >> 3) * 128 + (n0 & 7) * 16);
+  unsigned char* lo = hb + (size_t)g * NG * 128 + rowoff;         // k in [8g, 8g + 8)
+  unsigned char* hi = hb + (size_t)(MG + g) * NG * 128 + rowoff;  // k in ncp + [8g, 8g + 8)
+#define CM_ROW(F, SG) make_uint4(cm_pack2(SG v[0].F, SG v[1].F), cm_pack2(SG v[2].F, SG v[3].F), \
+                                 cm_pack2(SG v[4].F, SG v[5].F), cm_pack2(SG v[6].F, SG v[7].F))
+  *reinterpret_cast<uint4*>(lo) = CM_ROW(x, +);
+  *reinterpret_cast<uint4*>(hi) = CM_ROW(z, -);
+  *reinterpret_cast<uint4*>(lo + 16) = CM_ROW(y, +);
+  *reinterpret_cast<uint4*>(hi + 16) = CM_ROW(w, -);
+  *reinterpret_cast<uint4*>(lo + 32) = CM_ROW(z, +);
+  *reinterpret_cast<uint4*>(hi + 32) = CM_ROW(x, +);
+  *reinterpret_cast<uint4*>(lo + 48) = CM_ROW(w, +);
+  *reinterpret_cast<uint4*>(hi + 48) = CM_ROW(y, +);
+#undef CM_ROW
+}
+
 // The stencil over the sites a = cta, cta + ncta, ... (every thread of the CTA calls it).
 // ph carries the barrier parities between calls (bit 0, 1: operator buffers, bit 2: accumulator).
 // Returns false when a bounded wait gave up (q.err is then set to 2).
@@ -249,53 +297,16 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
     for (int c = 0; c < nchunk; ++c) {
       cm_chunk_scales(q, cs, c, S);
       __syncthreads();
-      // ---- B operands of the nine hops: item = (hop, tile pair, group of 8 components)
+      // ---- B operands of the nine hops: item = (hop, tile pair, group of 8 components); two
+      // items per thread have their 16 loads in flight together
       const int nitem = 9 * TP * MG;
-      for (int item = tid; item < nitem; item += blockDim.x) {
-        const int g = item % MG;
-        const int r = item / MG;
-        const int tp = r % TP, h = r / TP;
-        const int t = c * TP + tp;
-        const int64_t nbh = cs.nb[h];
-        float4 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int j = 8 * g + u;
-          v[u] = (t < nt && j < nc)
-                     ? __ldcg(reinterpret_cast<const float4*>(q.x + ((((int64_t)t * nc + j) * q.Vc) + nbh) * 4))
-                     : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        const float s0 = cs.sin_[2 * tp], s1 = cs.sin_[2 * tp + 1];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          v[u].x *= s0; v[u].z *= s0;
-          v[u].y *= s1; v[u].w *= s1;
-        }
-        // rows n = 4 tp + q of B^T, k-groups g (Re half of K) and MG + g (Im half)
-        unsigned char* hb = sB + (size_t)h * BH;
-        const int n0 = 4 * tp;
-        const uint32_t rowoff = (uint32_t)((n0 >> 3) * 128 + (n0 & 7) * 16);
-        unsigned char* lo = hb + (size_t)g * NG * 128 + rowoff;          // k in [8g, 8g + 8)
-        unsigned char* hi = hb + (size_t)(MG + g) * NG * 128 + rowoff;   // k in ncp + [8g, 8g + 8)
-        // q = 0: (Re x_{2t}, -Im x_{2t}); 1: (Re x_{2t+1}, -Im x_{2t+1}); 2: (Im x_{2t}, Re x_{2t});
-        // 3: (Im x_{2t+1}, Re x_{2t+1})
-        uint4 w;
-        w = make_uint4(cm_pack2(v[0].x, v[1].x), cm_pack2(v[2].x, v[3].x), cm_pack2(v[4].x, v[5].x), cm_pack2(v[6].x, v[7].x));
-        *reinterpret_cast<uint4*>(lo) = w;
-        w = make_uint4(cm_pack2(-v[0].z, -v[1].z), cm_pack2(-v[2].z, -v[3].z), cm_pack2(-v[4].z, -v[5].z), cm_pack2(-v[6].z, -v[7].z));
-        *reinterpret_cast<uint4*>(hi) = w;
-        w = make_uint4(cm_pack2(v[0].y, v[1].y), cm_pack2(v[2].y, v[3].y), cm_pack2(v[4].y, v[5].y), cm_pack2(v[6].y, v[7].y));
-        *reinterpret_cast<uint4*>(lo + 16) = w;
-        w = make_uint4(cm_pack2(-v[0].w, -v[1].w), cm_pack2(-v[2].w, -v[3].w), cm_pack2(-v[4].w, -v[5].w), cm_pack2(-v[6].w, -v[7].w));
-        *reinterpret_cast<uint4*>(hi + 16) = w;
-        w = make_uint4(cm_pack2(v[0].z, v[1].z), cm_pack2(v[2].z, v[3].z), cm_pack2(v[4].z, v[5].z), cm_pack2(v[6].z, v[7].z));
-        *reinterpret_cast<uint4*>(lo + 32) = w;
-        w = make_uint4(cm_pack2(v[0].x, v[1].x), cm_pack2(v[2].x, v[3].x), cm_pack2(v[4].x, v[5].x), cm_pack2(v[6].x, v[7].x));
-        *reinterpret_cast<uint4*>(hi + 32) = w;
-        w = make_uint4(cm_pack2(v[0].w, v[1].w), cm_pack2(v[2].w, v[3].w), cm_pack2(v[4].w, v[5].w), cm_pack2(v[6].w, v[7].w));
-        *reinterpret_cast<uint4*>(lo + 48) = w;
-        w = make_uint4(cm_pack2(v[0].y, v[1].y), cm_pack2(v[2].y, v[3].y), cm_pack2(v[4].y, v[5].y), cm_pack2(v[6].y, v[7].y));
-        *reinterpret_cast<uint4*>(hi + 48) = w;
+      for (int i0 = tid; i0 < nitem; i0 += 2 * (int)blockDim.x) {
+        const int i1 = i0 + blockDim.x;
+        float4 va[8], vb[8];
+        cm_item_load(q, cs, i0, c, MG, TP, nt, va);
+        if (i1 < nitem) cm_item_load(q, cs, i1, c, MG, TP, nt, vb);
+        cm_item_store(cs, sB, i0, MG, TP, NG, BH, va);
+        if (i1 < nitem) cm_item_store(cs, sB, i1, MG, TP, NG, BH, vb);
       }
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       cm_fence_before();
@@ -327,6 +338,16 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
       if (c == 0) ph ^= 1u << buf;
       // ---- warps 0 and 1 read rows 0..63 of the accumulator and write y
       if (warp < 2) {
+        // the site's own entries for the twist term, fetched while the MMAs run
+        const int i = warp * 32 + lane;
+        float4 xv[CM_MAXS / 2];
+#pragma unroll
+        for (int tp = 0; tp < CM_MAXS / 2; ++tp) {
+          const int t = c * TP + tp;
+          xv[tp] = (i < nc && tp < TP && t < nt)
+                       ? __ldcg(reinterpret_cast<const float4*>(q.x + ((((int64_t)t * nc + i) * q.Vc) + a) * 4))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         if (cm_wait(mbD, (ph >> 2) & 1u, fail)) {
           cm_fence_after();
           if (q.nbuf == 1 && tid == 0 && c == nchunk - 1 && a + ncta < q.Vc) load_site(a + ncta, 0);
@@ -341,7 +362,6 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
                            : "r"(ta + 8 * k));
           }
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-          const int i = warp * 32 + lane;
           if (i < nc) {
             const float g5 = i < nc / 2 ? 1.f : -1.f;
 #pragma unroll
@@ -349,15 +369,14 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
               const int t = c * TP + tp;
               if (tp < TP && t < nt) {
                 const int64_t off = ((((int64_t)t * nc + i) * q.Vc) + a) * 4;
-                const float4 xv = __ldcg(reinterpret_cast<const float4*>(q.x + off));
                 const float si0 = cs.sin_[2 * tp], si1 = cs.sin_[2 * tp + 1];
                 const float tw0 = g5 * cs.tw[2 * tp] * si0, tw1 = g5 * cs.tw[2 * tp + 1] * si1;
                 const float so0 = cs.sout[2 * tp], so1 = cs.sout[2 * tp + 1];
                 float4 o;
-                o.x = so0 * (__uint_as_float(r[4 * tp]) - tw0 * xv.z);
-                o.y = so1 * (__uint_as_float(r[4 * tp + 1]) - tw1 * xv.w);
-                o.z = so0 * (__uint_as_float(r[4 * tp + 2]) + tw0 * xv.x);
-                o.w = so1 * (__uint_as_float(r[4 * tp + 3]) + tw1 * xv.y);
+                o.x = so0 * (__uint_as_float(r[4 * tp]) - tw0 * xv[tp].z);
+                o.y = so1 * (__uint_as_float(r[4 * tp + 1]) - tw1 * xv[tp].w);
+                o.z = so0 * (__uint_as_float(r[4 * tp + 2]) + tw0 * xv[tp].x);
+                o.w = so1 * (__uint_as_float(r[4 * tp + 3]) + tw1 * xv[tp].y);
                 *reinterpret_cast<float4*>(q.y + off) = o;
               }
             }

@@ -55,20 +55,27 @@ def read_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region.
+
+    The sampler starts before the warm-up (its start-up queries stay out of the timed region)
+    and only the samples stamped inside mark()'s window are kept."""
 
     def __init__(self, idx):
         self.idx = idx
         self.proc = None
         self.path = None
+        self.window = None
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -81,11 +88,22 @@ class Clocks:
         time.sleep(0.25)
         self.proc.terminate()
         out, _ = self.proc.communicate()
+        import datetime
         sm, smax, reasons = [], [], set()
+        rows = []
         for line in out.strip().splitlines():
             f = [v.strip() for v in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            rows.append((ts, f[1:]))
+        if self.window is not None:
+            inside = [r for r in rows if r[0] is not None and self.window[0] - 0.2 <= r[0] <= self.window[1] + 0.2]
+            rows = inside or rows[-3:]
+        for _, f in rows:
             try:
                 sm.append(float(f[1]))
                 smax.append(float(f[2]))
@@ -144,13 +162,14 @@ def run_dirac(args, world, rank, local):
     xb = torch.empty(nb // 4, dtype=torch.float32, device="cuda")
     yb = torch.empty_like(xb)
     T.tmamg_pack(ctx, xf, xb, nsys, 32)
-    for _ in range(args.warmup):
-        T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32)
-    torch.cuda.synchronize()
-    barrier(world)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with Clocks(local) as clk:
+        for _ in range(args.warmup):
+            T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32)
         torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        h0 = time.time()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
@@ -160,6 +179,7 @@ def run_dirac(args, world, rank, local):
             ev[k][1].record(stream)
         t1.record(stream)
         torch.cuda.synchronize()
+        clk.mark(h0, time.time())
     total_ms = t0.elapsed_time(t1)
     kern_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     total_ms = max_over_ranks(total_ms, world)
@@ -250,15 +270,16 @@ def run_solve(args, world, rank, local):
     bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
     xd = torch.zeros(nsys * V * 24, dtype=torch.float64, device="cuda")
     sp = T.solve_params(**solve_kw())
-    for _ in range(args.warmup):
-        T.tmamg_solve(ctx, bd, nrhs, mus, len(mus), xd, 1, sp)
-    torch.cuda.synchronize()
-    barrier(world)
     ok = True
     iters = None
-    launches0 = T.tmamg_kernel_launches()  # kernels launched before the timed region (ncu -s)
     with Clocks(local) as clk:
+        for _ in range(args.warmup):
+            T.tmamg_solve(ctx, bd, nrhs, mus, len(mus), xd, 1, sp)
         torch.cuda.synchronize()
+        barrier(world)
+        launches0 = T.tmamg_kernel_launches()  # kernels launched before the timed region (ncu -s)
+        torch.cuda.synchronize()
+        h0 = time.time()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
@@ -268,6 +289,7 @@ def run_solve(args, world, rank, local):
             iters = stats
         t1.record(stream)
         torch.cuda.synchronize()
+        clk.mark(h0, time.time())
     launches = T.tmamg_kernel_launches() - launches0
     total_ms = max_over_ranks(t0.elapsed_time(t1), world)
     solves_per_s = nsys * args.steps * world / (total_ms * 1e-3)

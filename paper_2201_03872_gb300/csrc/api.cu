@@ -252,6 +252,7 @@ void free_levels(tmamg_ctx* ctx) {
     cudaFree(l.A16);
     cudaFree(l.cmax);
     cudaFree(l.cerr);
+    cudaFree(l.x16);
   }
   ctx->levels.clear();
 }

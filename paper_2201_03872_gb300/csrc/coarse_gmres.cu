@@ -42,7 +42,8 @@ constexpr int CG_WARP_F4 = CG_MAXNC * CG_TCH + CG_AJC * CG_MAXNC;
 struct CGArgs {
   const float2* A;
   const __half* A16;  // FP16 operator for the tensor-core stencil, or null (FP32 stencil)
-  int cm_nbuf;        // operator buffers of the tensor-core stencil
+  __half* X16;        // B images of the vector the tensor-core stencil multiplies
+  int cm_nstage;      // shared-memory stages of the tensor-core stencil
   double* b0;         // [NS] initial residual norm per system (scale of the restart product)
   int L[4];
   int64_t Vc;
@@ -433,11 +434,12 @@ __device__ void backsub(const CGArgs& p, int n, double2* Rs) {
 }
 
 // tensor-core stencil phase: y = s_out D_c (s_in x) over all sites
-__device__ __forceinline__ bool cg_apply_tc(const CGArgs& p, CmShared& cs, unsigned char* dsm, unsigned& ph,
+__device__ __forceinline__ bool cg_apply_tc(const CGArgs& p, CmShared& cs, unsigned char* dsm, CmPipe& pipe,
                                             const float* x, float* y, const double* scale, int mode, int cta,
                                             int ncta) {
   CmArgs q;
   q.A16 = p.A16;
+  q.X16 = p.X16;
   q.L[0] = p.L[0]; q.L[1] = p.L[1]; q.L[2] = p.L[2]; q.L[3] = p.L[3];
   q.Vc = p.Vc;
   q.nc = p.nc;
@@ -448,15 +450,24 @@ __device__ __forceinline__ bool cg_apply_tc(const CGArgs& p, CmShared& cs, unsig
   q.scale = scale;
   q.mode = mode;
   q.nsys = p.nsys;
-  q.nbuf = p.cm_nbuf;
+  q.nstage = p.cm_nstage;
   q.err = p.err;
-  return cm_apply(q, cs, dsm, ph, cta, ncta);
+  return cm_apply(q, cs, dsm, pipe, cta, ncta);
+}
+
+// B images of x for the tensor-core stencil, input factor cvs[n] per system (shared memory);
+// all CTAs take part, the caller's next grid barrier publishes them
+__device__ __forceinline__ void cg_convert(const CGArgs& p, const float* x, const float* cvs) {
+  cm_convert(x, p.X16, p.Vc, p.nc, p.nsys, cvs, (int64_t)blockIdx.x * CG_THREADS + threadIdx.x,
+             (int64_t)p.G * CG_THREADS);
+  cm_fence_global_async();
 }
 
 __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* dyn) {
   __shared__ double sm[(CG_THREADS / 32) * CG_IVEC * 4];
   __shared__ float4 hsm[CG_MAXM + 1];  // H column (or y) of this CTA's two systems
-  unsigned ph = 0;  // barrier parities of the tensor-core stencil
+  CmPipe pipe;  // this thread's place in the tensor-core stencil pipeline
+  __shared__ float cvs[256];  // input factors of the B-image conversion, per system
   double gc[CG_MAXM];   // Givens rotations of the current cycle (used by the threads gtid < nsys)
   double2 gs[CG_MAXM];
   unsigned char* dsm = reinterpret_cast<unsigned char*>(dyn);
@@ -501,6 +512,12 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
     p.kconv[n] = 0;
   }
   if (!grid_barrier(p)) return;
+  if (p.A16) {
+    for (int n = threadIdx.x; n < p.nsys; n += CG_THREADS) cvs[n] = (float)ldx(p.sc + n);
+    __syncthreads();
+    cg_convert(p, p.V, cvs);
+    if (!grid_barrier(p)) return;
+  }
 
   int total = 0;
   while (true) {
@@ -511,8 +528,8 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
       // stencil sites: the stop test lags the Arnoldi process by one step, and the solution
       // uses the converged column count, so the extra step changes nothing in it.
       if (p.A16) {
-        if (b >= GG && !cg_apply_tc(p, cs, dsm, ph, p.V + (int64_t)j * p.vstride, p.V + (int64_t)(j + 1) * p.vstride,
-                                    p.sc, CM_SCALE_IN, b - GG, p.G - GG))
+        if (b >= GG && !cg_apply_tc(p, cs, dsm, pipe, p.V + (int64_t)j * p.vstride,
+                                    p.V + (int64_t)(j + 1) * p.vstride, p.sc, CM_SCALE_IN, b - GG, p.G - GG))
           return;
       } else {
         cg_apply_partials(p, p.V + (int64_t)j * p.vstride, dyn);
@@ -630,13 +647,21 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
         cta_reduce_store(p, &nrm, 1, m + 1, sm);
       }
       if (!grid_barrier(p)) return;
-      // P5: H[j+1][j] = |w| and sc = 1 / |w| (one thread per system)
-      if (b == 0 && threadIdx.x < p.nsys) {
-        const int n = threadIdx.x;
+      // P5: H[j+1][j] = |w| and sc = 1 / |w| (every CTA sums the norms in the same order; CTA 0
+      // stores them), then the B images of sc w for the next stencil
+      for (int n = threadIdx.x; n < p.nsys; n += CG_THREADS) {
         const double2 s = part_sum(p, m + 1, n);
         const double hn = sqrt(fmax(s.x, 0.0));
-        p.sc[n] = hn > 0 ? 1.0 / hn : 0.0;
-        p.H[((int64_t)j * (m + 1) + j + 1) * NS + n] = make_double2(hn, 0);
+        const double scn = hn > 0 ? 1.0 / hn : 0.0;
+        cvs[n] = (float)scn;
+        if (b == 0) {
+          p.sc[n] = scn;
+          p.H[((int64_t)j * (m + 1) + j + 1) * NS + n] = make_double2(hn, 0);
+        }
+      }
+      if (p.A16) {
+        __syncthreads();
+        cg_convert(p, p.V + (int64_t)(j + 1) * p.vstride, cvs);
       }
       ++total;
       if (!grid_barrier(p)) return;
@@ -721,7 +746,14 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
     if (gtid < p.nsys) p.sc[gtid] = 1.0;
     if (!grid_barrier(p)) return;
     if (p.A16) {
-      if (!cg_apply_tc(p, cs, dsm, ph, p.xc, p.V, p.b0, CM_SCALE_OUT, b, p.G)) return;
+      for (int n = threadIdx.x; n < p.nsys; n += CG_THREADS) {
+        const double v = ldx(p.b0 + n);
+        cvs[n] = v > 0.0 ? (float)(1.0 / v) : 1.f;
+      }
+      __syncthreads();
+      cg_convert(p, p.xc, cvs);
+      if (!grid_barrier(p)) return;
+      if (!cg_apply_tc(p, cs, dsm, pipe, p.xc, p.V, p.b0, CM_SCALE_OUT, b, p.G)) return;
     } else {
       cg_apply_partials(p, p.xc, dyn);
     }
@@ -765,13 +797,14 @@ __global__ void __launch_bounds__(CG_THREADS, 1) coarse_gmres_kernel(CGArgs p) {
   if (p.A16) cm_end(cs);
 }
 
-int CoarseGmres::alloc(int m_, int nsys_, int G_, size_t bundle_bytes) {
-  if (m_ <= m && nsys_ <= NS && G_ <= G && bundle_bytes <= hbytes) return 0;
+int CoarseGmres::alloc(int m_, int nsys_, int G_, size_t bundle_bytes, size_t x16b) {
+  if (m_ <= m && nsys_ <= NS && G_ <= G && bundle_bytes <= hbytes && x16b <= x16_bytes) return 0;
   release();
   m = m_;
   NS = nsys_;
   G = G_;
   hbytes = bundle_bytes;
+  x16_bytes = x16b;
   cudaError_t e = cudaSuccess;
   auto A = [&](void** q, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(q, bytes);
@@ -793,26 +826,26 @@ int CoarseGmres::alloc(int m_, int nsys_, int G_, size_t bundle_bytes) {
   A((void**)&err, sizeof(int));
   A((void**)&iters, sizeof(int));
   A((void**)&hpart, 9 * bundle_bytes);
+  if (x16_bytes) A((void**)&X16, x16_bytes);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h_flags, sizeof(int) * 2);
   return e == cudaSuccess ? 0 : -1;
 }
 
 void CoarseGmres::release() {
-  void* ptrs[] = {H, cs, sn, g, y, tolabs, b0, sc, kconv, active, done, nactive, part, bar, err, iters, hpart};
+  void* ptrs[] = {H, cs, sn, g, y, tolabs, b0, sc, kconv, active, done, nactive, part, bar, err, iters, hpart, X16};
   for (void* q : ptrs) cudaFree(q);
   if (h_flags) cudaFreeHost(h_flags);
   H = nullptr; cs = nullptr; sn = nullptr; g = nullptr; y = nullptr; tolabs = nullptr; b0 = nullptr; sc = nullptr;
   kconv = nullptr; active = nullptr; done = nullptr; nactive = nullptr; part = nullptr; bar = nullptr;
-  err = nullptr; iters = nullptr; h_flags = nullptr; hpart = nullptr;
-  m = 0; NS = 0; G = 0; hbytes = 0;
+  err = nullptr; iters = nullptr; h_flags = nullptr; hpart = nullptr; X16 = nullptr;
+  m = 0; NS = 0; G = 0; hbytes = 0; x16_bytes = 0;
 }
 
 // dynamic shared memory: back substitution, and the stencil phase (FP32 per-warp staging, or
 // the tensor-core operand buffers with nbuf operator copies)
-static size_t dyn_smem_bytes(int m, int nc, int nsys, bool tc, int nbuf) {
+static size_t dyn_smem_bytes(int m, int nc, int nsys, bool tc, int nstage) {
   const size_t rs = sizeof(double2) * (size_t)m * m;
-  const size_t stage = tc ? cm_smem_bytes(nc, cm_chunk(nsys), nbuf)
-                          : sizeof(float4) * (size_t)(CG_THREADS / 32) * CG_WARP_F4;
+  const size_t stage = tc ? cm_smem_bytes(nc, nsys, nstage) : sizeof(float4) * (size_t)(CG_THREADS / 32) * CG_WARP_F4;
   return stage > rs ? stage : rs;
 }
 
@@ -849,14 +882,15 @@ int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, co
   const size_t need = (size_t)nt * cd.nc * cd.Vc * 4 * sizeof(float);
   if (G > s.G || m > s.m || nsys > s.NS || m > CG_MAXM || cd.nc > 64 || (cd.nc % 2) || need > s.hbytes) return -2;
   const size_t cap = dyn_smem_cap();
-  int nbuf = 2;
-  if (A16 && dyn_smem_bytes(m, cd.nc, nsys, true, 2) > cap) nbuf = 1;
-  const size_t dyn = dyn_smem_bytes(m, cd.nc, nsys, A16 != nullptr, nbuf);
+  const int nstage = A16 ? cm_nstage(cd.nc, nsys, cap) : 0;
+  if (A16 && (nstage < 2 || cm_x16_bytes(cd.Vc, cd.nc, nsys) > s.x16_bytes)) return -2;
+  const size_t dyn = dyn_smem_bytes(m, cd.nc, nsys, A16 != nullptr, nstage);
   if (dyn > cap) return -2;
   CGArgs p;
   p.A = A;
   p.A16 = A16;
-  p.cm_nbuf = nbuf;
+  p.X16 = s.X16;
+  p.cm_nstage = nstage;
   p.b0 = s.b0;
   for (int k = 0; k < 4; ++k) p.L[k] = cd.L[k];
   p.Vc = cd.Vc;

@@ -15,7 +15,9 @@ struct CoarseGmres {
   int* h_flags = nullptr;
   float* hpart = nullptr;  // 9 coarse bundles: hop partials of the stencil
   size_t hbytes = 0;       // bytes of one coarse bundle the partials are sized for
-  int alloc(int m, int nsys, int G, size_t bundle_bytes);
+  __half* X16 = nullptr;   // B images of the tensor-core stencil
+  size_t x16_bytes = 0;
+  int alloc(int m, int nsys, int G, size_t bundle_bytes, size_t x16_bytes);
   void release();
 };
 

@@ -64,12 +64,26 @@ __global__ void maxabs_kernel(const float* __restrict__ x, float* mx, int64_t M,
   }
 }
 
+// B images of x with the power-of-two scaling of CM_SCALE_MAX
+__global__ void __launch_bounds__(256) convert_x16_kernel(const float* __restrict__ x, __half* X16, int64_t Vc, int nc,
+                                                          int nsys, const float* mx) {
+  __shared__ float sin[CM_MAXSYS];
+  for (int n = threadIdx.x; n < nsys; n += blockDim.x) {
+    float si, so;
+    cm_sys_scale(mx, CM_SCALE_MAX, n, si, so);
+    sin[n] = si;
+  }
+  __syncthreads();
+  cm_convert(x, X16, Vc, nc, nsys, sin, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+             (int64_t)gridDim.x * blockDim.x);
+}
+
 __global__ void __launch_bounds__(CM_THREADS, 1) coarse_mma_kernel(CmArgs q) {
   __shared__ CmShared cs;
   extern __shared__ __align__(128) unsigned char cm_dyn[];
   cm_begin(cs);
-  unsigned ph = 0;
-  cm_apply(q, cs, cm_dyn, ph, blockIdx.x, gridDim.x);
+  CmPipe pipe;
+  cm_apply(q, cs, cm_dyn, pipe, blockIdx.x, gridDim.x);
   cm_end(cs);
 }
 
@@ -84,7 +98,7 @@ size_t cm_dyn_cap(const void* kernel) {
 }
 
 int coarse_apply_f16(const CoarseDims& cd, const __half* A16, const float* x, float* y, const double* mu, double dmu,
-                     int nsys, float* mx, int* err, cudaStream_t st) {
+                     int nsys, float* mx, __half* X16, int* err, cudaStream_t st) {
   static int sms = 0;
   static size_t cap = 0;
   if (!sms) {
@@ -95,10 +109,9 @@ int coarse_apply_f16(const CoarseDims& cd, const __half* A16, const float* x, fl
     cudaFuncSetAttribute(coarse_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
   }
   if (nsys <= 0) return 0;
-  if (cd.nc > CM_MAXNC || cd.nc < 1) return -2;
-  const int S = cm_chunk(nsys);
-  int nbuf = cm_smem_bytes(cd.nc, S, 2) <= cap ? 2 : 1;
-  if (cm_smem_bytes(cd.nc, S, 1) > cap) return -2;
+  if (cd.nc > CM_MAXNC || cd.nc < 1 || nsys > CM_MAXSYS) return -2;
+  const int nstage = cm_nstage(cd.nc, nsys, cap);
+  if (nstage < 2) return -2;
   const int nt = ntiles(nsys, 2);
   const int64_t M = (int64_t)cd.nc * cd.Vc;
   cudaMemsetAsync(mx, 0, sizeof(float) * nsys, st);
@@ -106,8 +119,13 @@ int coarse_apply_f16(const CoarseDims& cd, const __half* A16, const float* x, fl
   if (bx > 64) bx = 64;
   maxabs_kernel<<<dim3(bx, nt), 256, 0, st>>>(x, mx, M, nsys);
   TM_COUNT();
+  const int ncp = cm_ncp(cd.nc), S = cm_chunk(nsys);
+  const int64_t items = cd.Vc * cm_nchunk(nsys) * (S / 2) * (ncp / 8);
+  convert_x16_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(x, X16, cd.Vc, cd.nc, nsys, mx);
+  TM_COUNT();
   CmArgs q;
   q.A16 = A16;
+  q.X16 = X16;
   for (int k = 0; k < 4; ++k) q.L[k] = cd.L[k];
   q.Vc = cd.Vc;
   q.nc = cd.nc;
@@ -118,10 +136,10 @@ int coarse_apply_f16(const CoarseDims& cd, const __half* A16, const float* x, fl
   q.scale = mx;
   q.mode = CM_SCALE_MAX;
   q.nsys = nsys;
-  q.nbuf = nbuf;
+  q.nstage = nstage;
   q.err = err;
   const int64_t G = cd.Vc < sms ? cd.Vc : sms;
-  coarse_mma_kernel<<<(unsigned)G, CM_THREADS, cm_smem_bytes(cd.nc, S, nbuf), st>>>(q);
+  coarse_mma_kernel<<<(unsigned)G, CM_THREADS, cm_smem_bytes(cd.nc, nsys, nstage), st>>>(q);
   TM_COUNT();
   return 0;
 }

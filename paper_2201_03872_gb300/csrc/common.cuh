@@ -57,6 +57,8 @@ struct CoarseLevel {
   __half* A16 = nullptr;  // the same blocks in FP16, in the operand layout of the tensor-core stencil
   float* cmax = nullptr;  // [CM_MAXSYS] per-system range scratch of the stand-alone tensor-core stencil
   int* cerr = nullptr;    // bounded-wait flag of the stand-alone tensor-core stencil
+  __half* x16 = nullptr;  // B images of the stand-alone tensor-core stencil (grown on demand)
+  size_t x16_bytes = 0;
 };
 
 constexpr int CM_MAXSYS = 1024;  // systems per stand-alone tensor-core stencil call

@@ -140,7 +140,8 @@ static int ensure_ws(tmamg_ctx* ctx, int nsys, int m, int mc) {
   if (w->coarse.alloc(mcc, ns, partial_elems((int64_t)nc * Vc, ns, mcc + 1, 2)))
     return set_err(ctx, TMAMG_ERR_OOM, "gmres state");
   // the grid for one tile is the largest any system count uses
-  if (w->cg.alloc(mcc, ns, coarse_gmres_grid(1), w->cb32)) return set_err(ctx, TMAMG_ERR_OOM, "coarse gmres state");
+  if (w->cg.alloc(mcc, ns, coarse_gmres_grid(1), w->cb32, cm_x16_bytes(Vc, nc, ns)))
+    return set_err(ctx, TMAMG_ERR_OOM, "coarse gmres state");
   fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->ones, ns, 1.0); TM_COUNT();
   fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->mones, ns, -1.0); TM_COUNT();
   return check_cuda(ctx, cudaGetLastError(), "workspace init");
@@ -349,12 +350,21 @@ __global__ void copy_beta_kernel(const double* b, double* dst, int n) {
 
 // y = D_c x on level l: FP16 operator on the tensor cores (precision 16, or 0 = default) or
 // the FP32 stencil (precision 32); false if the sizes are outside the tensor-core path
-static bool coarse_apply_level(const CoarseLevel& l, int precision, const float* x, float* y, const double* mu,
-                               double dmu, int nsys, cudaStream_t st) {
+static bool coarse_apply_level(CoarseLevel& l, int precision, const float* x, float* y, const double* mu, double dmu,
+                               int nsys, cudaStream_t st) {
   const CoarseDims cd = coarse_dims(l);
   if (precision != 32) {
     if (!l.A16 || nsys > CM_MAXSYS) return false;
-    return coarse_apply_f16(cd, l.A16, x, y, mu, dmu, nsys, l.cmax, l.cerr, st) == 0;
+    const size_t need = cm_x16_bytes(cd.Vc, cd.nc, nsys);
+    if (need > l.x16_bytes) {  // grown once per system count; later calls reuse it
+      cudaStreamSynchronize(st);
+      cudaFree(l.x16);
+      l.x16 = nullptr;
+      l.x16_bytes = 0;
+      if (cudaMalloc(&l.x16, need) != cudaSuccess) return false;
+      l.x16_bytes = need;
+    }
+    return coarse_apply_f16(cd, l.A16, x, y, mu, dmu, nsys, l.cmax, l.x16, l.cerr, st) == 0;
   }
   coarse_apply(cd, l.A, x, y, mu, dmu, nsys, st);
   return true;
@@ -374,7 +384,7 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
   tmamg_ctx* ctx = S.ctx;
   Workspace* w = ctx->ws;
   cudaStream_t st = ctx->stream;
-  const CoarseLevel& L1 = ctx->levels[0];
+  CoarseLevel& L1 = ctx->levels[0];
   CoarseDims cd = coarse_dims(L1);
   if (S.sp->coarse_solver == 0) {
     // persistent kernel: the whole restarted GMRES in one cooperative launch
@@ -749,7 +759,7 @@ int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_
     return set_err(ctx, TMAMG_ERR_ARG, "coarse_apply: bad argument");
   int rc = upload_mu(ctx, mu, nsys);
   if (rc) return rc;
-  const CoarseLevel& l = ctx->levels[0];
+  CoarseLevel& l = ctx->levels[0];
   if (!coarse_apply_level(l, precision, (const float*)x_bundle, (float*)y_bundle, ctx->mu_dev, 1.0, nsys,
                           ctx->stream))
     return set_err(ctx, TMAMG_ERR_ARG, "coarse_apply: sizes outside the tensor-core stencil");

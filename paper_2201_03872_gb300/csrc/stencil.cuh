@@ -35,8 +35,12 @@ struct CV {
 
 template <typename real, int T>
 __device__ __forceinline__ void ldcv(CV<real, T>& v, const real* __restrict__ p) {
-  static_assert(sizeof(real) * 2 * T == 16, "one bundle entry is 16 bytes");
-  if constexpr (sizeof(real) == 4) {
+  static_assert(sizeof(real) * 2 * T == 16 || (sizeof(real) == 4 && T == 1), "one entry is 16 (or 8) bytes");
+  if constexpr (sizeof(real) == 4 && T == 1) {  // one system of a shared-memory block layout
+    const float2 a = *reinterpret_cast<const float2*>(p);
+    v.re[0] = a.x;
+    v.im[0] = a.y;
+  } else if constexpr (sizeof(real) == 4) {
     float4 a = *reinterpret_cast<const float4*>(p);
     v.re[0] = a.x; v.re[1] = a.y;
     v.im[0] = a.z; v.im[1] = a.w;

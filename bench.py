@@ -211,7 +211,7 @@ def run_dirac(args, world, rank, local):
                    "l2": "working set 378 MB > 129 MB L2; back-to-back applications"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "peak_source": peak_src,
-                     "kernel": "dirac_kernel<float,4>", "algorithmic_bytes_per_launch": bytes_per_apply},
+                     "kernel": "dirac_kernel<float,2>", "algorithmic_bytes_per_launch": bytes_per_apply},
         "e2e": {"value": bytes_per_apply * args.steps * world / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
                 "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(x.nbytes)},
         "gpu_launches": args.steps,

@@ -246,13 +246,43 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 192 : 256, sizeof(real) ==
   site_coords(s, L, c);
   const int64_t tstride = (int64_t)12 * V * 2 * T;
   const real* xt = x + tile * tstride;
+  const int64_t strides[4] = {1, (int64_t)Lx, (int64_t)Lx * Ly, (int64_t)Lx * Ly * Lz};
+  if constexpr (sizeof(real) == 4) {
+    // packed FP32x2 arithmetic over the tile's two systems
+    Spinor2 acc;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      acc.c[k].re = make_float2(0.f, 0.f);
+      acc.c[k].im = make_float2(0.f, 0.f);
+    }
+#define TM_HOP2(NU)                                                                                  \
+    {                                                                                                \
+      int64_t sf = c[NU] + 1 < L[NU] ? s + strides[NU] : s - (int64_t)(L[NU] - 1) * strides[NU];    \
+      int64_t sb = c[NU] > 0 ? s - strides[NU] : s + (int64_t)(L[NU] - 1) * strides[NU];             \
+      float pf = (NU == 3 && c[3] == Lt - 1) ? (float)bc_t : 1.f;                                  \
+      float pb = (NU == 3 && c[3] == 0) ? (float)bc_t : 1.f;                                       \
+      hop2<NU, true>(acc, xt + sf * 4, V, U + (int64_t)NU * 9 * V, V, s, pf);                        \
+      hop2<NU, false>(acc, xt + sb * 4, V, U + (int64_t)NU * 9 * V, V, sb, pb);                      \
+    }
+    TM_HOP2(0)
+    TM_HOP2(1)
+    TM_HOP2(2)
+    TM_HOP2(3)
+#undef TM_HOP2
+    const int n0 = tile * 2;
+    const float2 m2 = make_float2(n0 < nsys ? (float)mu[n0] : 0.f, n0 + 1 < nsys ? (float)mu[n0 + 1] : 0.f);
+    local2(acc, xt + s * 4, V, C, V, s, m2);
+    real* yo = y + tile * tstride + s * 4;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) st2(yo + (int64_t)k * V * 4, acc.c[k]);
+    return;
+  }
   Spinor<real, T> acc;
 #pragma unroll
   for (int k = 0; k < 12; ++k)
 #pragma unroll
     for (int l = 0; l < T; ++l) { acc.c[k].re[l] = 0; acc.c[k].im[l] = 0; }
 
-  const int64_t strides[4] = {1, (int64_t)Lx, (int64_t)Lx * Ly, (int64_t)Lx * Ly * Lz};
 #define TM_HOP(NU)                                                                                   \
   {                                                                                                  \
     int64_t sf = c[NU] + 1 < L[NU] ? s + strides[NU] : s - (int64_t)(L[NU] - 1) * strides[NU];      \

@@ -73,13 +73,14 @@ __device__ __forceinline__ void block_reduce(float* v, int n, float* red) {
 // Persistent block solver: CTA b takes a contiguous range of the work items (block of this
 // colour, tile), item = k * ntile + tile, so consecutive items mostly share a block. The
 // block's links and clover are staged in shared memory once per block and serve every tile
-// and every MR step. Two threads per block site, one per system of the tile (adjacent lanes,
-// so their link and clover reads are shared-memory broadcasts); the block residual rho lives
-// in shared memory as [12][bv][2 systems] (re, im) pairs, the block correction in registers.
+// and every MR step; the block residual rho lives in shared memory (neighbours read it), the
+// block correction in registers. One thread per block site handles the tile's two systems in
+// packed FP32x2 arithmetic; CTA of ceil(bv / 32) * 32 threads (the threads past bv only take
+// part in the reductions and barriers).
 //
-// shared memory: links [4 nu][9][bv] float2, clover [72][bv] float, rho [12][bv][2] float2,
-// reduction scratch [nwarps][2 systems][3] float
-constexpr int SAP_THREADS = 512;
+// shared memory: links [4 nu][9][bv] float2, clover [72][bv] float, rho [12][bv] float4,
+// reduction scratch [nwarps][8] float
+constexpr int SAP_THREADS = 256;
 
 __device__ __forceinline__ int colour_block(const SapDims& d, int colour, int k) {
   if (d.pdim < 0) return k;  // one block covers the lattice (colour 0 only)
@@ -99,44 +100,20 @@ __device__ __forceinline__ int colour_block(const SapDims& d, int colour, int k)
   return ((c[3] * d.nb[2] + c[2]) * d.nb[1] + c[1]) * d.nb[0] + c[0];
 }
 
-// sums of v[0..2] over the CTA's threads of system l = lane & 1; every thread gets its
-// system's totals
-__device__ __forceinline__ void pair_reduce(float* v, float* red) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    float x = v[i];
-#pragma unroll
-    for (int o = 16; o > 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    v[i] = x;
-  }
-  if (lane < 2)
-    for (int i = 0; i < 3; ++i) red[(warp * 2 + lane) * 3 + i] = v[i];
-  __syncthreads();
-  const int l = lane & 1;
-  for (int i = 0; i < 3; ++i) {
-    float s = 0;
-    for (int w = 0; w < nw; ++w) s += red[(w * 2 + l) * 3 + i];
-    v[i] = s;
-  }
-  __syncthreads();
-}
-
 __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __restrict__ U,
                                                                 const float* __restrict__ C, float* __restrict__ r,
                                                                 float* __restrict__ delta, float* __restrict__ e,
                                                                 const double* __restrict__ mu, int nsys, SapDims d,
                                                                 int colour, int steps, int nitems, int ntile) {
-  constexpr int T = 2;  // systems per tile of the global bundles
+  constexpr int T = 2;  // systems per tile
   extern __shared__ float4 sm[];
   const int bv = d.bv;
   float2* Ls = reinterpret_cast<float2*>(sm);              // [4][9][bv]
   float* Cs = reinterpret_cast<float*>(Ls + 36 * bv);      // [72][bv]
-  float2* rho = reinterpret_cast<float2*>(Cs + 72 * bv);   // [12][bv][2]
-  float* red = reinterpret_cast<float*>(rho + 24 * bv);    // [nwarps][2][3]
-  const int site = threadIdx.x >> 1, l = threadIdx.x & 1;
-  const bool act = site < bv;
+  float4* rho = reinterpret_cast<float4*>(Cs + 72 * bv);   // [12][bv]
+  float* red = reinterpret_cast<float*>(rho + 12 * bv);    // [nwarps][8]
+  const int tid = threadIdx.x;
+  const bool act = tid < bv;
   const int64_t V = (int64_t)d.L[0] * d.L[1] * d.L[2] * d.L[3];
   const int64_t tstride = (int64_t)12 * V * 2 * T;
   const int per = (nitems + gridDim.x - 1) / gridDim.x;
@@ -153,14 +130,15 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
     __syncthreads();  // the previous item's reads of rho (and of the staged block) are done
     if (b != cur) {
       cur = b;
-      block_site(d, b, act ? site : 0, bc, lc, c);
+      block_site(d, b, act ? tid : 0, bc, lc, c);
       s = site_index(c, d.L);
       if (act) {
         // links of the block: U_nu(x) for x in the block (forward hops, and backward hops
-        // through the in-block neighbour x - nu, whose own forward link it is); the two
-        // threads of a site split the loads
-        for (int q = l; q < 36; q += 2) Ls[q * bv + site] = U[(int64_t)q * V + s];
-        for (int q = l; q < 72; q += 2) Cs[q * bv + site] = C[(int64_t)q * V + s];
+        // through the in-block neighbour x - nu, whose own forward link it is)
+#pragma unroll 12
+        for (int q = 0; q < 36; ++q) Ls[q * bv + tid] = U[(int64_t)q * V + s];
+#pragma unroll 12
+        for (int q = 0; q < 72; ++q) Cs[q * bv + tid] = C[(int64_t)q * V + s];
       }
 #pragma unroll
       for (int nu = 0; nu < 4; ++nu) {
@@ -191,83 +169,90 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
       }
     }
     float* rt = r + tile * tstride;
-    CV<float, 1> eb[12];
+    CV2 eb[12];
 #pragma unroll
     for (int k2 = 0; k2 < 12; ++k2) {
-      eb[k2].re[0] = 0.f;
-      eb[k2].im[0] = 0.f;
-      if (act) {
-        const float4 g = *reinterpret_cast<const float4*>(rt + ((int64_t)k2 * V + s) * 2 * T);
-        rho[(k2 * bv + site) * 2 + l] = l == 0 ? make_float2(g.x, g.z) : make_float2(g.y, g.w);
-      }
+      eb[k2].re = make_float2(0.f, 0.f);
+      eb[k2].im = make_float2(0.f, 0.f);
+      if (act) rho[k2 * bv + tid] = *reinterpret_cast<const float4*>(rt + ((int64_t)k2 * V + s) * 2 * T);
     }
-    const int n = tile * T + l;
-    float m[1] = {n < nsys ? (float)mu[n] : 0.f};
-    const float* rb = reinterpret_cast<const float*>(rho) + 2 * l;  // this thread's system
+    const int n0 = tile * T;
+    const float2 m2 = make_float2(n0 < nsys ? (float)mu[n0] : 0.f, n0 + 1 < nsys ? (float)mu[n0 + 1] : 0.f);
+    const float* rb = reinterpret_cast<const float*>(rho);
     for (int it = 0; it < steps; ++it) {
       __syncthreads();  // rho (and the staged links) complete
-      Spinor<float, 1> q;
+      Spinor2 q;
 #pragma unroll
-      for (int k2 = 0; k2 < 12; ++k2) { q.c[k2].re[0] = 0; q.c[k2].im[0] = 0; }
-      float v[3] = {0.f, 0.f, 0.f};
+      for (int k2 = 0; k2 < 12; ++k2) {
+        q.c[k2].re = make_float2(0.f, 0.f);
+        q.c[k2].im = make_float2(0.f, 0.f);
+      }
+      float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (act) {
-#define TM_BHOP(NU)                                                                                              \
-        {                                                                                                        \
-          if (nf[NU] >= 0)                                                                                       \
-            hop<NU, true, float, 1>(q, rb + (int64_t)nf[NU] * 4, 2 * bv, Ls + NU * 9 * bv, bv, site, pf[NU]);     \
-          if (nbk[NU] >= 0)                                                                                      \
-            hop<NU, false, float, 1>(q, rb + (int64_t)nbk[NU] * 4, 2 * bv, Ls + NU * 9 * bv, bv, nbk[NU], pb[NU]); \
+#define TM_BHOP(NU)                                                                              \
+        {                                                                                        \
+          if (nf[NU] >= 0) hop2<NU, true>(q, rb + nf[NU] * 4, bv, Ls + NU * 9 * bv, bv, tid, pf[NU]); \
+          if (nbk[NU] >= 0)                                                                      \
+            hop2<NU, false>(q, rb + nbk[NU] * 4, bv, Ls + NU * 9 * bv, bv, nbk[NU], pb[NU]);     \
         }
         TM_BHOP(0)
         TM_BHOP(1)
         TM_BHOP(2)
         TM_BHOP(3)
 #undef TM_BHOP
-        local_term<float, 1>(q, rb + (int64_t)site * 4, 2 * bv, Cs, bv, site, m);
-        // partial <q, q> and <q, rho>
+        local2(q, rb + tid * 4, bv, Cs, bv, tid, m2);
+        // partial <q, q> and <q, rho> per system (packed over the two systems)
+        float2 qq = make_float2(0.f, 0.f), qr = qq, qi = qq;
 #pragma unroll
         for (int k2 = 0; k2 < 12; ++k2) {
-          const float2 rr = rho[(k2 * bv + site) * 2 + l];
-          const float qr = q.c[k2].re[0], qi = q.c[k2].im[0];
-          v[0] += qr * qr + qi * qi;
-          v[1] += qr * rr.x + qi * rr.y;
-          v[2] += qr * rr.y - qi * rr.x;
+          const float4 rr = rho[k2 * bv + tid];
+          const float2 rre = make_float2(rr.x, rr.y), rim = make_float2(rr.z, rr.w);
+          const CV2& qv = q.c[k2];
+          qq = fma2(qv.re, qv.re, qq);
+          qq = fma2(qv.im, qv.im, qq);
+          qr = fma2(qv.re, rre, qr);
+          qr = fma2(qv.im, rim, qr);
+          qi = fma2(qv.re, rim, qi);
+          qi = fma2(f2(-1.f), mul2(qv.im, rre), qi);
         }
+        v[0] = qq.x; v[1] = qr.x; v[2] = qi.x;
+        v[3] = qq.y; v[4] = qr.y; v[5] = qi.y;
       }
-      pair_reduce(v, red);  // contains the barrier: every q is computed, rho may change
-      const float ar = v[0] > 0.f ? v[1] / v[0] : 0.f;
-      const float ai = v[0] > 0.f ? v[2] / v[0] : 0.f;
+      block_reduce<T>(v, 6, red);  // contains the barrier: every q is computed, rho may change
+      const float2 ar = make_float2(v[0] > 0.f ? v[1] / v[0] : 0.f, v[3] > 0.f ? v[4] / v[3] : 0.f);
+      const float2 ai = make_float2(v[0] > 0.f ? v[2] / v[0] : 0.f, v[3] > 0.f ? v[5] / v[3] : 0.f);
+      const float2 nai = make_float2(-ai.x, -ai.y);
       if (act) {
 #pragma unroll
         for (int k2 = 0; k2 < 12; ++k2) {
-          float2 rr = rho[(k2 * bv + site) * 2 + l];
-          eb[k2].re[0] += ar * rr.x - ai * rr.y;
-          eb[k2].im[0] += ar * rr.y + ai * rr.x;
-          const float qr = q.c[k2].re[0], qi = q.c[k2].im[0];
-          rr.x -= ar * qr - ai * qi;
-          rr.y -= ar * qi + ai * qr;
-          rho[(k2 * bv + site) * 2 + l] = rr;
+          const float4 rr = rho[k2 * bv + tid];
+          float2 rre = make_float2(rr.x, rr.y), rim = make_float2(rr.z, rr.w);
+          // e += alpha rho; rho -= alpha q (alpha = ar + i ai per system)
+          eb[k2].re = fma2(ar, rre, eb[k2].re);
+          eb[k2].re = fma2(nai, rim, eb[k2].re);
+          eb[k2].im = fma2(ar, rim, eb[k2].im);
+          eb[k2].im = fma2(ai, rre, eb[k2].im);
+          const CV2& qv = q.c[k2];
+          rre = fma2(f2(-1.f), mul2(ar, qv.re), rre);
+          rre = fma2(ai, qv.im, rre);
+          rim = fma2(f2(-1.f), mul2(ar, qv.im), rim);
+          rim = fma2(nai, qv.re, rim);
+          rho[k2 * bv + tid] = make_float4(rre.x, rre.y, rim.x, rim.y);
         }
       }
     }
-    // write back: the even lane of a site assembles the tile's 16-byte entries
-    __syncwarp();  // the partner lane's last rho update is visible
-    {
+    if (act) {
       float* dt = delta + tile * tstride;
       float* et = e + tile * tstride;
 #pragma unroll
       for (int k2 = 0; k2 < 12; ++k2) {
-        const float er = __shfl_xor_sync(0xffffffffu, eb[k2].re[0], 1);
-        const float ei = __shfl_xor_sync(0xffffffffu, eb[k2].im[0], 1);
-        if (act && l == 0) {
-          const int64_t o = ((int64_t)k2 * V + s) * 2 * T;
-          const float4 dv = make_float4(eb[k2].re[0], er, eb[k2].im[0], ei);
-          *reinterpret_cast<float4*>(dt + o) = dv;
-          const float4 e0 = *reinterpret_cast<const float4*>(et + o);
-          *reinterpret_cast<float4*>(et + o) = make_float4(e0.x + dv.x, e0.y + dv.y, e0.z + dv.z, e0.w + dv.w);
-          const float2 r0 = rho[(k2 * bv + site) * 2], r1 = rho[(k2 * bv + site) * 2 + 1];
-          *reinterpret_cast<float4*>(rt + o) = make_float4(r0.x, r1.x, r0.y, r1.y);
-        }
+        const int64_t o = ((int64_t)k2 * V + s) * 2 * T;
+        st2(dt + o, eb[k2]);
+        CV2 e0 = ld2(et + o);
+        e0.re = add2(e0.re, eb[k2].re);
+        e0.im = add2(e0.im, eb[k2].im);
+        st2(et + o, e0);
+        *reinterpret_cast<float4*>(rt + o) = rho[k2 * bv + tid];
       }
     }
   }
@@ -374,11 +359,11 @@ void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C
   int nt = ntiles(nsys, T);
   size_t M = (size_t)12 * g.V * 2 * T * nt;
   cudaMemsetAsync(e, 0, M * sizeof(float), st);
-  const int nthreads = (2 * d.bv + 31) / 32 * 32;  // two threads per block site
+  const int nthreads = (d.bv + 31) / 32 * 32;  // one thread per block site
   const int nwarps = nthreads / 32;
-  // links [4][9][bv] float2 + clover [72][bv] + rho [12][bv][2] float2 + reduction scratch
-  size_t smem = sizeof(float2) * 36 * d.bv + sizeof(float) * 72 * d.bv + sizeof(float2) * 24 * d.bv +
-                sizeof(float) * 6 * nwarps;
+  // links [4][9][bv] float2 + clover [72][bv] + rho [12][bv] float4 + reduction scratch
+  size_t smem = sizeof(float2) * 36 * d.bv + sizeof(float) * 72 * d.bv + sizeof(float4) * 12 * d.bv +
+                sizeof(float) * 8 * nwarps;
   static int sms = 0;
   if (!sms) {
     int dev = 0;

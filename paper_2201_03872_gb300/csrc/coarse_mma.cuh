@@ -208,22 +208,34 @@ __device__ __forceinline__ uint32_t cm_pack2(float a, float b) {
   return d;
 }
 
-// neighbour a + h of coarse site a (h = 1 + 2 nu forward, 2 + 2 nu backward), periodic lattice
-__device__ __forceinline__ int64_t cm_neighbour(int64_t a, int h, int L0, int L1, int L2, int L3) {
-  int c0 = (int)(a % L0);
-  int64_t rr = a / L0;
-  int c1 = (int)(rr % L1);
+// coordinates of coarse site a (32-bit arithmetic: the producer thread computes these on the
+// critical path of the copy pipeline, where 64-bit divisions cost about a microsecond per stage)
+struct CmCoord {
+  int c[4];
+};
+__device__ __forceinline__ CmCoord cm_coords(int a, int L0, int L1, int L2) {
+  CmCoord k;
+  k.c[0] = a % L0;
+  int rr = a / L0;
+  k.c[1] = rr % L1;
   rr /= L1;
-  int c2 = (int)(rr % L2);
-  int c3 = (int)(rr / L2);
+  k.c[2] = rr % L2;
+  k.c[3] = rr / L2;
+  return k;
+}
+// neighbour a + h (h = 1 + 2 nu forward, 2 + 2 nu backward) of the site at k, periodic lattice;
+// no division
+__device__ __forceinline__ int cm_neighbour(const CmCoord& k, int h, int L0, int L1, int L2, int L3) {
+  int c0 = k.c[0], c1 = k.c[1], c2 = k.c[2], c3 = k.c[3];
   if (h > 0) {
-    const int nu = (h - 1) / 2, dir = ((h - 1) & 1) ? -1 : 1;
-    if (nu == 0) c0 = (c0 + dir + L0) % L0;
-    else if (nu == 1) c1 = (c1 + dir + L1) % L1;
-    else if (nu == 2) c2 = (c2 + dir + L2) % L2;
-    else c3 = (c3 + dir + L3) % L3;
+    const int nu = (h - 1) >> 1;
+    const bool back = ((h - 1) & 1) != 0;
+    if (nu == 0) c0 = back ? (c0 == 0 ? L0 - 1 : c0 - 1) : (c0 + 1 == L0 ? 0 : c0 + 1);
+    else if (nu == 1) c1 = back ? (c1 == 0 ? L1 - 1 : c1 - 1) : (c1 + 1 == L1 ? 0 : c1 + 1);
+    else if (nu == 2) c2 = back ? (c2 == 0 ? L2 - 1 : c2 - 1) : (c2 + 1 == L2 ? 0 : c2 + 1);
+    else c3 = back ? (c3 == 0 ? L3 - 1 : c3 - 1) : (c3 + 1 == L3 ? 0 : c3 + 1);
   }
-  return ((int64_t)(c3 * L2 + c2) * L1 + c1) * L0 + c0;
+  return ((c3 * L2 + c2) * L1 + c1) * L0 + c0;
 }
 
 // The B images of x for all sites: item = ((a chunks + c) TP + tp) MG + g covers the eight
@@ -238,11 +250,12 @@ __device__ __forceinline__ void cm_convert(const float* __restrict__ x, __half* 
   const int64_t IB = cm_img_bytes(nc, S);
   const int64_t total = Vc * nchunk * TP * MG;
   for (int64_t item = first; item < total; item += stride) {
-    const int g = (int)(item % MG);
-    int64_t r = item / MG;
-    const int tp = (int)(r % TP);
+    const int it32 = (int)item;  // Vc * chunks * TP * MG < 2^31 for every supported size
+    const int g = it32 % MG;
+    int r = it32 / MG;
+    const int tp = r % TP;
     r /= TP;
-    const int c = (int)(r % nchunk);
+    const int c = r % nchunk;
     const int64_t a = r / nchunk;
     const int t = c * TP + tp;
     float4 v[8];
@@ -305,14 +318,22 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
     const unsigned char* Ag = reinterpret_cast<const unsigned char*>(q.A16);
     const unsigned char* Xg = reinterpret_cast<const unsigned char*>(q.X16);
     const int L0 = q.L[0], L1 = q.L[1], L2 = q.L[2], L3 = q.L[3];
-    for (int64_t a = cta; a < q.Vc && !*fail; a += ncta)
+    for (int64_t a = cta; a < q.Vc && !*fail; a += ncta) {
+      const CmCoord kc = cm_coords((int)a, L0, L1, L2);
+      int nbs[9];
+#pragma unroll
+      for (int h = 0; h < 9; ++h) nbs[h] = cm_neighbour(kc, h, L0, L1, L2, L3);
       for (int c = 0; c < nchunk && !*fail; ++c)
+#pragma unroll 1
         for (int h = 0; h < 9; ++h) {
           const int st = pipe.stage;
           if (!cm_wait(cm_smem(&cs.empty[st]), pipe.phase ^ 1u, fail)) break;
           const uint32_t fb = cm_smem(&cs.full[st]);
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(ST) : "memory");
-          const int64_t nb = cm_neighbour(a, h, L0, L1, L2, L3);
+          int nb = nbs[0];
+#pragma unroll
+          for (int q2 = 1; q2 < 9; ++q2)
+            if (h == q2) nb = nbs[q2];
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
                   s0 + st * ST),
@@ -321,13 +342,14 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
                   s0 + st * ST + HA),
-              "l"(Xg + (nb * nchunk + c) * (int64_t)IB), "r"(IB), "r"(fb)
+              "l"(Xg + ((int64_t)nb * nchunk + c) * (int64_t)IB), "r"(IB), "r"(fb)
               : "memory");
           if (++pipe.stage == NS) {
             pipe.stage = 0;
             pipe.phase ^= 1u;
           }
         }
+    }
   } else if (tid == 32) {
     // ---- MMA issuer: nine hops x KS steps per unit into accumulator pipe.acc
     const uint32_t idesc = (1u << 4)                        // FP32 accumulator

@@ -4,9 +4,10 @@
 // aggregates, and the construction recurses).
 //
 // P layout (per coarsening): float2 P[Vc][2 chi][nv][K] with K = asize * d: for aggregate a,
-// chirality chi and test vector j, the K = (site in aggregate) x (d unknowns of that
-// chirality) entries; d = 6 (2 spins x 3 colours) when the parent is the fine lattice, and
-// the parent's nv when the parent is a coarse lattice. A parent component is chi * d + c'.
+// chirality chi and test vector j, the K = (d unknowns of that chirality) x (site in aggregate)
+// entries, k = c' asize + q (sites fastest, so that consecutive k touch consecutive lattice
+// sites); d = 6 (2 spins x 3 colours) when the parent is the fine lattice, and the parent's
+// nv when the parent is a coarse lattice. A parent component is chi * d + c'.
 // Coarse vectors are bundles with ncomp = nc = 2 nv and nsite = Vc; component chi * nv + j.
 // Coarse stencil: float2 A[9][Vc][nc (column j)][nc (row i)], hop index 0 = self,
 // 1 + 2 nu = +nu, 2 + 2 nu = -nu.
@@ -36,7 +37,7 @@ __global__ void gather_P_kernel(const float* __restrict__ Vb, float2* __restrict
   int j = (int)((t / K) % nv);
   int chi = (int)((t / ((int64_t)K * nv)) % 2);
   int64_t a = t / ((int64_t)K * nv * 2);
-  int q = k / d, cp = k % d;
+  int cp = k / g.asize, q = k % g.asize;
   int c[4];
   agg_site(a, q, g.Lc, g.agg, g.L, c);
   int64_t s = site_index(c, g.L);
@@ -134,70 +135,94 @@ void build_P(const AggDims& g, const float* Vb, float2* P, int nv, int d, cudaSt
 
 // ------------------------------------------------------------------ restriction / prolongation
 // Per aggregate the restriction is a small matrix product xc_a = P_a^+ r_a (2 nv x K times
-// K x nsys, K = asize d) and the prolongation its transpose; one CTA per aggregate reads P_a
-// once for all systems (tile chunks of RP_TCH tiles), staged through shared memory in
-// chunks of RP_KC columns so that both P and the vectors are read with coalesced loads.
-constexpr int RP_TCH = 8;
-constexpr int RP_KC = 48;
-constexpr int RP_THREADS = 256;
+// K x nsys, K = asize d) and the prolongation its transpose; P_a is read once for all systems.
 
-// xc[tile][chi nv + j][a] = sum_k conj(P[a][chi][j][k]) r[tile][chi d + c'][site(a, q)]
-__global__ void __launch_bounds__(RP_THREADS) restrict_kernel(const float2* __restrict__ P,
+// xc[tile][chi nv + j][a] = sum_k conj(P[a][chi][j][k]) r[tile][chi d + c'][site(a, q)], k = c' asize + q.
+// One CTA per (aggregate, chirality). A thread owns a 3 x 3 block of outputs (three rows j, three
+// system tiles) and one of 16 interleaved slices of k; per k it loads three entries of P and
+// three 16-byte vector entries and does nine packed complex multiply-adds (both systems of a
+// tile at once). The 16 slice sums of an output are added by shuffles in a fixed order.
+constexpr int RS_KS = 16;       // k slices (lanes of a half warp)
+constexpr int RS_SLOTS = 16;    // output blocks processed at once per CTA
+constexpr int RS_THREADS = RS_KS * RS_SLOTS;
+
+__global__ void __launch_bounds__(RS_THREADS) restrict_kernel(const float2* __restrict__ P,
                                                               const float* __restrict__ r, float* __restrict__ xc,
                                                               AggDims g, int nv, int d, int nt) {
-  __shared__ float2 Ps[64][RP_KC + 1];        // rows chi nv + j (nc <= 64), a chunk of k
-  __shared__ float4 Rs[2][RP_KC][RP_TCH];     // both chiralities, the chunk of k, tiles
-  __shared__ int sidx[RP_KC];
-  const int64_t a = blockIdx.x;
-  const int nc = 2 * nv;
+  extern __shared__ int sidx[];  // [asize] lattice site of each aggregate member
+  const int64_t a = blockIdx.x >> 1;
+  const int chi = blockIdx.x & 1;
   const int K = g.asize * d;
-  for (int t0 = 0; t0 < nt; t0 += RP_TCH) {
-    const int ntc = nt - t0 < RP_TCH ? nt - t0 : RP_TCH;
-    // outputs (o, u): thread handles q = tid, tid + 256, ...
-    float4 acc[3];
-    for (int i = 0; i < 3; ++i) acc[i] = make_float4(0, 0, 0, 0);
-    for (int k0 = 0; k0 < K; k0 += RP_KC) {
-      const int kc = K - k0 < RP_KC ? K - k0 : RP_KC;
-      __syncthreads();
-      for (int q = threadIdx.x; q < nc * kc; q += blockDim.x) {
-        const int o = q / kc, kk = q % kc;
-        const int chi = o / nv, j = o % nv;
-        Ps[o][kk] = P[(((int64_t)a * 2 + chi) * nv + j) * K + k0 + kk];
-      }
-      for (int kk = threadIdx.x; kk < kc; kk += blockDim.x) {
-        int c[4];
-        agg_site(a, (k0 + kk) / d, g.Lc, g.agg, g.L, c);
-        sidx[kk] = (int)site_index(c, g.L);
-      }
-      __syncthreads();
-      for (int q = threadIdx.x; q < 2 * kc * ntc; q += blockDim.x) {
-        const int u = q % ntc, kk = (q / ntc) % kc, chi = q / (ntc * kc);
-        const int cp = (k0 + kk) % d;
-        Rs[chi][kk][u] =
-            *reinterpret_cast<const float4*>(r + (((int64_t)(t0 + u) * (2 * d) + chi * d + cp) * g.Vp + sidx[kk]) * 4);
-      }
-      __syncthreads();
-      int slot = 0;
-      for (int q = threadIdx.x; q < nc * ntc; q += blockDim.x, ++slot) {
-        const int o = q / ntc, u = q % ntc;
-        const int chi = o / nv;
-        float4 s = acc[slot];
-        for (int kk = 0; kk < kc; ++kk) {
-          const float2 pv = Ps[o][kk];
-          const float4 v = Rs[chi][kk][u];
-          // conj(p) v for both lanes (v = re0, re1, im0, im1)
-          s.x += pv.x * v.x + pv.y * v.z;
-          s.y += pv.x * v.y + pv.y * v.w;
-          s.z += pv.x * v.z - pv.y * v.x;
-          s.w += pv.x * v.w - pv.y * v.y;
+  for (int q = threadIdx.x; q < g.asize; q += blockDim.x) {
+    int c[4];
+    agg_site(a, q, g.Lc, g.agg, g.L, c);
+    sidx[q] = (int)site_index(c, g.L);
+  }
+  __syncthreads();
+  const int ks = threadIdx.x % RS_KS, slot = threadIdx.x / RS_KS;
+  const int JG = (nv + 2) / 3, TG = (nt + 2) / 3;
+  const float2* Pa = P + ((a * 2 + chi) * nv) * (int64_t)K;
+  for (int og0 = 0; og0 < JG * TG; og0 += RS_SLOTS) {
+    const int og = og0 + slot;
+    const bool live = og < JG * TG;
+    const int jg = live ? og / TG : 0, tg = live ? og % TG : 0;
+    float2 are[9], aim[9];
+#pragma unroll
+    for (int u = 0; u < 9; ++u) {
+      are[u] = make_float2(0.f, 0.f);
+      aim[u] = make_float2(0.f, 0.f);
+    }
+    if (live) {
+      const int j0 = 3 * jg, t0 = 3 * tg;
+      for (int k = ks; k < K; k += RS_KS) {
+        const int cp = k / g.asize, q = k - cp * g.asize;
+        const int64_t site = sidx[q];
+        float2 p[3];
+        float4 v[3];
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj)
+          p[jj] = j0 + jj < nv ? __ldg(Pa + (int64_t)(j0 + jj) * K + k) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int tt = 0; tt < 3; ++tt)
+          v[tt] = t0 + tt < nt
+                      ? __ldg(reinterpret_cast<const float4*>(r + (((int64_t)(t0 + tt) * (2 * d) + chi * d + cp) * g.Vp + site) * 4))
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const float2 pr = make_float2(p[jj].x, p[jj].x), pi = make_float2(p[jj].y, p[jj].y);
+          const float2 npi = make_float2(-p[jj].y, -p[jj].y);
+#pragma unroll
+          for (int tt = 0; tt < 3; ++tt) {
+            const float2 vr = make_float2(v[tt].x, v[tt].y), vi = make_float2(v[tt].z, v[tt].w);
+            // conj(p) v = (pr vr + pi vi) + i (pr vi - pi vr), both systems at once
+            are[jj * 3 + tt] = __ffma2_rn(pr, vr, are[jj * 3 + tt]);
+            are[jj * 3 + tt] = __ffma2_rn(pi, vi, are[jj * 3 + tt]);
+            aim[jj * 3 + tt] = __ffma2_rn(pr, vi, aim[jj * 3 + tt]);
+            aim[jj * 3 + tt] = __ffma2_rn(npi, vr, aim[jj * 3 + tt]);
+          }
         }
-        acc[slot] = s;
       }
     }
-    int slot = 0;
-    for (int q = threadIdx.x; q < nc * ntc; q += blockDim.x, ++slot) {
-      const int o = q / ntc, u = q % ntc;
-      *reinterpret_cast<float4*>(xc + (((int64_t)(t0 + u) * nc + o) * g.Vc + a) * 4) = acc[slot];
+    // sum of the 16 slices (lanes ks of the half warp), fixed order
+#pragma unroll
+    for (int u = 0; u < 9; ++u) {
+#pragma unroll
+      for (int o = RS_KS / 2; o > 0; o >>= 1) {
+        are[u].x += __shfl_xor_sync(0xffffffffu, are[u].x, o);
+        are[u].y += __shfl_xor_sync(0xffffffffu, are[u].y, o);
+        aim[u].x += __shfl_xor_sync(0xffffffffu, aim[u].x, o);
+        aim[u].y += __shfl_xor_sync(0xffffffffu, aim[u].y, o);
+      }
+    }
+    if (live && ks == 0) {
+      const int j0 = 3 * jg, t0 = 3 * tg;
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
+        for (int tt = 0; tt < 3; ++tt)
+          if (j0 + jj < nv && t0 + tt < nt)
+            *reinterpret_cast<float4*>(xc + (((int64_t)(t0 + tt) * (2 * nv) + chi * nv + j0 + jj) * g.Vc + a) * 4) =
+                make_float4(are[jj * 3 + tt].x, are[jj * 3 + tt].y, aim[jj * 3 + tt].x, aim[jj * 3 + tt].y);
     }
   }
 }
@@ -205,55 +230,71 @@ __global__ void __launch_bounds__(RP_THREADS) restrict_kernel(const float2* __re
 void restrict_vec(const AggDims& g, const float2* P, const float* r, float* xc, int nv, int d, int nsys,
                   cudaStream_t st) {
   const int nt = ntiles(nsys, T2);
-  restrict_kernel<<<(unsigned)g.Vc, RP_THREADS, 0, st>>>(P, r, xc, g, nv, d, nt); TM_COUNT();
+  restrict_kernel<<<(unsigned)(g.Vc * 2), RS_THREADS, sizeof(int) * g.asize, st>>>(P, r, xc, g, nv, d, nt);
+  TM_COUNT();
 }
 
+// prolongation: tile chunk and CTA size
+constexpr int RP_TCH = 8;
+constexpr int RP_THREADS = 256;
+
 // e[tile][chi d + c'][site(a, q)] (+)= sum_j P[a][chi][j][k] xc[tile][chi nv + j][a]:
-// one CTA per aggregate, threads over k (coalesced reads of P), the aggregate's coarse
-// vector of a tile chunk in shared memory
+// one CTA per (aggregate, chirality), threads over k (sites fastest: coalesced reads of P and
+// writes of e), the aggregate's coarse vector of a tile chunk in shared memory, packed complex
+// multiply-adds over the two systems of a tile
 __global__ void __launch_bounds__(RP_THREADS) prolong_kernel(const float2* __restrict__ P,
                                                              const float* __restrict__ xc, float* __restrict__ e,
                                                              AggDims g, int nv, int d, int nt, int accumulate) {
-  __shared__ float4 Xs[64][RP_TCH];
-  const int64_t a = blockIdx.x;
+  __shared__ float4 Xs[32][RP_TCH];  // [j][tile of the chunk] for this chirality (nv <= 32)
+  extern __shared__ int sidx[];      // [asize]
+  const int64_t a = blockIdx.x >> 1;
+  const int chi = blockIdx.x & 1;
   const int nc = 2 * nv;
   const int K = g.asize * d;
+  for (int q = threadIdx.x; q < g.asize; q += blockDim.x) {
+    int c[4];
+    agg_site(a, q, g.Lc, g.agg, g.L, c);
+    sidx[q] = (int)site_index(c, g.L);
+  }
+  const float2* Pa = P + ((a * 2 + chi) * nv) * (int64_t)K;
   for (int t0 = 0; t0 < nt; t0 += RP_TCH) {
     const int ntc = nt - t0 < RP_TCH ? nt - t0 : RP_TCH;
     __syncthreads();
-    for (int q = threadIdx.x; q < nc * ntc; q += blockDim.x) {
-      const int o = q / ntc, u = q % ntc;
-      Xs[o][u] = *reinterpret_cast<const float4*>(xc + (((int64_t)(t0 + u) * nc + o) * g.Vc + a) * 4);
+    for (int q = threadIdx.x; q < nv * ntc; q += blockDim.x) {
+      const int j = q / ntc, u = q % ntc;
+      Xs[j][u] = *reinterpret_cast<const float4*>(xc + (((int64_t)(t0 + u) * nc + chi * nv + j) * g.Vc + a) * 4);
     }
     __syncthreads();
-    for (int ck = threadIdx.x; ck < 2 * K; ck += blockDim.x) {
-      const int chi = ck / K, k = ck % K;
-      const float2* Pc = P + (((int64_t)a * 2 + chi) * nv) * K + k;
-      float4 acc[RP_TCH];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      float2 are[RP_TCH], aim[RP_TCH];
 #pragma unroll
-      for (int u = 0; u < RP_TCH; ++u) acc[u] = make_float4(0, 0, 0, 0);
+      for (int u = 0; u < RP_TCH; ++u) {
+        are[u] = make_float2(0.f, 0.f);
+        aim[u] = make_float2(0.f, 0.f);
+      }
       for (int j = 0; j < nv; ++j) {
-        const float2 pv = Pc[(int64_t)j * K];
+        const float2 pv = __ldg(Pa + (int64_t)j * K + k);
+        const float2 pr = make_float2(pv.x, pv.x), pi = make_float2(pv.y, pv.y), npi = make_float2(-pv.y, -pv.y);
 #pragma unroll
         for (int u = 0; u < RP_TCH; ++u) {
           if (u < ntc) {
-            const float4 x = Xs[chi * nv + j][u];
-            acc[u].x += pv.x * x.x - pv.y * x.z;
-            acc[u].y += pv.x * x.y - pv.y * x.w;
-            acc[u].z += pv.x * x.z + pv.y * x.x;
-            acc[u].w += pv.x * x.w + pv.y * x.y;
+            const float4 x = Xs[j][u];
+            const float2 xr = make_float2(x.x, x.y), xi = make_float2(x.z, x.w);
+            // p x = (pr xr - pi xi) + i (pr xi + pi xr), both systems at once
+            are[u] = __ffma2_rn(pr, xr, are[u]);
+            are[u] = __ffma2_rn(npi, xi, are[u]);
+            aim[u] = __ffma2_rn(pr, xi, aim[u]);
+            aim[u] = __ffma2_rn(pi, xr, aim[u]);
           }
         }
       }
-      const int q = k / d, cp = k % d;
-      int c[4];
-      agg_site(a, q, g.Lc, g.agg, g.L, c);
-      const int64_t s = site_index(c, g.L);
+      const int cp = k / g.asize, q = k - cp * g.asize;
+      const int64_t s = sidx[q];
 #pragma unroll
       for (int u = 0; u < RP_TCH; ++u) {
         if (u < ntc) {
           float* out = e + (((int64_t)(t0 + u) * (2 * d) + chi * d + cp) * g.Vp + s) * 4;
-          float4 v = acc[u];
+          float4 v = make_float4(are[u].x, are[u].y, aim[u].x, aim[u].y);
           if (accumulate) {
             const float4 o = *reinterpret_cast<const float4*>(out);
             v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
@@ -268,7 +309,8 @@ __global__ void __launch_bounds__(RP_THREADS) prolong_kernel(const float2* __res
 void prolong_vec(const AggDims& g, const float2* P, const float* xc, float* e, int nv, int d, int nsys, int accumulate,
                  cudaStream_t st) {
   const int nt = ntiles(nsys, T2);
-  prolong_kernel<<<(unsigned)g.Vc, RP_THREADS, 0, st>>>(P, xc, e, g, nv, d, nt, accumulate); TM_COUNT();
+  prolong_kernel<<<(unsigned)(g.Vc * 2), RP_THREADS, sizeof(int) * g.asize, st>>>(P, xc, e, g, nv, d, nt, accumulate);
+  TM_COUNT();
 }
 
 // ------------------------------------------------------------------ coarse stencil application
@@ -358,7 +400,7 @@ __global__ void columns_kernel(const float2* __restrict__ P, float* __restrict__
     int n = tile * T2 + l;
     int chi = n / nv, j = n % nv;
     if (chi == chi_p) {
-      float2 p = P[(((int64_t)a * 2 + chi) * nv + j) * K + q * d + cp];
+      float2 p = P[(((int64_t)a * 2 + chi) * nv + j) * K + cp * g.asize + q];
       o[l] = p.x;
       o[2 + l] = p.y;
     }

@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(RS_THREADS) restrict_kernel(const float2* __re
     }
     if (live) {
       const int j0 = 3 * jg, t0 = 3 * tg;
+#pragma unroll 4
       for (int k = ks; k < K; k += RS_KS) {
         const int cp = k / g.asize, q = k - cp * g.asize;
         const int64_t site = sidx[q];
@@ -272,6 +273,7 @@ __global__ void __launch_bounds__(RP_THREADS) prolong_kernel(const float2* __res
         are[u] = make_float2(0.f, 0.f);
         aim[u] = make_float2(0.f, 0.f);
       }
+#pragma unroll 8
       for (int j = 0; j < nv; ++j) {
         const float2 pv = __ldg(Pa + (int64_t)j * K + k);
         const float2 pr = make_float2(pv.x, pv.x), pi = make_float2(pv.y, pv.y), npi = make_float2(-pv.y, -pv.y);

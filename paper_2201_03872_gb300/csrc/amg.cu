@@ -138,18 +138,22 @@ void build_P(const AggDims& g, const float* Vb, float2* P, int nv, int d, cudaSt
 // K x nsys, K = asize d) and the prolongation its transpose; P_a is read once for all systems.
 
 // xc[tile][chi nv + j][a] = sum_k conj(P[a][chi][j][k]) r[tile][chi d + c'][site(a, q)], k = c' asize + q.
-// One CTA per (aggregate, chirality). A thread owns a 3 x 3 block of outputs (three rows j, three
-// system tiles) and one of 16 interleaved slices of k; per k it loads three entries of P and
-// three 16-byte vector entries and does nine packed complex multiply-adds (both systems of a
-// tile at once). The 16 slice sums of an output are added by shuffles in a fixed order.
+// One CTA per (aggregate, chirality). The vector entries of a chunk of RS_KC values of k are
+// staged in shared memory for all tiles (every output row reads them there). A thread owns a
+// 3 x 3 block of outputs (three rows j, three system tiles) and one of 16 interleaved slices of
+// k; per k it loads three entries of P and reads three staged 16-byte entries, and does nine
+// packed complex multiply-adds (both systems of a tile at once). The 16 slice sums of an output
+// are added by shuffles in a fixed order.
 constexpr int RS_KS = 16;       // k slices (lanes of a half warp)
 constexpr int RS_SLOTS = 16;    // output blocks processed at once per CTA
 constexpr int RS_THREADS = RS_KS * RS_SLOTS;
+constexpr int RS_KC = 128;      // k values staged per chunk (fewer when many tiles)
 
 __global__ void __launch_bounds__(RS_THREADS) restrict_kernel(const float2* __restrict__ P,
                                                               const float* __restrict__ r, float* __restrict__ xc,
-                                                              AggDims g, int nv, int d, int nt) {
-  extern __shared__ int sidx[];  // [asize] lattice site of each aggregate member
+                                                              AggDims g, int nv, int d, int nt, int kc) {
+  extern __shared__ float4 rsm[];                            // [nt][kc] staged entries
+  int* sidx = reinterpret_cast<int*>(rsm + (size_t)nt * kc);  // [asize] lattice site of each member
   const int64_t a = blockIdx.x >> 1;
   const int chi = blockIdx.x & 1;
   const int K = g.asize * d;
@@ -158,7 +162,6 @@ __global__ void __launch_bounds__(RS_THREADS) restrict_kernel(const float2* __re
     agg_site(a, q, g.Lc, g.agg, g.L, c);
     sidx[q] = (int)site_index(c, g.L);
   }
-  __syncthreads();
   const int ks = threadIdx.x % RS_KS, slot = threadIdx.x / RS_KS;
   const int JG = (nv + 2) / 3, TG = (nt + 2) / 3;
   const float2* Pa = P + ((a * 2 + chi) * nv) * (int64_t)K;
@@ -166,40 +169,48 @@ __global__ void __launch_bounds__(RS_THREADS) restrict_kernel(const float2* __re
     const int og = og0 + slot;
     const bool live = og < JG * TG;
     const int jg = live ? og / TG : 0, tg = live ? og % TG : 0;
+    const int j0 = 3 * jg, t0 = 3 * tg;
     float2 are[9], aim[9];
 #pragma unroll
     for (int u = 0; u < 9; ++u) {
       are[u] = make_float2(0.f, 0.f);
       aim[u] = make_float2(0.f, 0.f);
     }
-    if (live) {
-      const int j0 = 3 * jg, t0 = 3 * tg;
-#pragma unroll 4
-      for (int k = ks; k < K; k += RS_KS) {
+    for (int kc0 = 0; kc0 < K; kc0 += kc) {
+      const int kn = K - kc0 < kc ? K - kc0 : kc;
+      __syncthreads();  // sidx ready / the previous chunk consumed
+      for (int e = threadIdx.x; e < nt * kn; e += blockDim.x) {
+        const int t = e / kn, kk = e - t * kn;
+        const int k = kc0 + kk;
         const int cp = k / g.asize, q = k - cp * g.asize;
-        const int64_t site = sidx[q];
-        float2 p[3];
-        float4 v[3];
+        rsm[t * kc + kk] =
+            __ldg(reinterpret_cast<const float4*>(r + (((int64_t)t * (2 * d) + chi * d + cp) * g.Vp + sidx[q]) * 4));
+      }
+      __syncthreads();
+      if (live) {
+#pragma unroll 4
+        for (int kk = ks; kk < kn; kk += RS_KS) {
+          float2 p[3];
+          float4 v[3];
 #pragma unroll
-        for (int jj = 0; jj < 3; ++jj)
-          p[jj] = j0 + jj < nv ? __ldg(Pa + (int64_t)(j0 + jj) * K + k) : make_float2(0.f, 0.f);
+          for (int jj = 0; jj < 3; ++jj)
+            p[jj] = j0 + jj < nv ? __ldg(Pa + (int64_t)(j0 + jj) * K + kc0 + kk) : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int tt = 0; tt < 3; ++tt)
-          v[tt] = t0 + tt < nt
-                      ? __ldg(reinterpret_cast<const float4*>(r + (((int64_t)(t0 + tt) * (2 * d) + chi * d + cp) * g.Vp + site) * 4))
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int tt = 0; tt < 3; ++tt)
+            v[tt] = t0 + tt < nt ? rsm[(t0 + tt) * kc + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-          const float2 pr = make_float2(p[jj].x, p[jj].x), pi = make_float2(p[jj].y, p[jj].y);
-          const float2 npi = make_float2(-p[jj].y, -p[jj].y);
+          for (int jj = 0; jj < 3; ++jj) {
+            const float2 pr = make_float2(p[jj].x, p[jj].x), pi = make_float2(p[jj].y, p[jj].y);
+            const float2 npi = make_float2(-p[jj].y, -p[jj].y);
 #pragma unroll
-          for (int tt = 0; tt < 3; ++tt) {
-            const float2 vr = make_float2(v[tt].x, v[tt].y), vi = make_float2(v[tt].z, v[tt].w);
-            // conj(p) v = (pr vr + pi vi) + i (pr vi - pi vr), both systems at once
-            are[jj * 3 + tt] = __ffma2_rn(pr, vr, are[jj * 3 + tt]);
-            are[jj * 3 + tt] = __ffma2_rn(pi, vi, are[jj * 3 + tt]);
-            aim[jj * 3 + tt] = __ffma2_rn(pr, vi, aim[jj * 3 + tt]);
-            aim[jj * 3 + tt] = __ffma2_rn(npi, vr, aim[jj * 3 + tt]);
+            for (int tt = 0; tt < 3; ++tt) {
+              const float2 vr = make_float2(v[tt].x, v[tt].y), vi = make_float2(v[tt].z, v[tt].w);
+              // conj(p) v = (pr vr + pi vi) + i (pr vi - pi vr), both systems at once
+              are[jj * 3 + tt] = __ffma2_rn(pr, vr, are[jj * 3 + tt]);
+              are[jj * 3 + tt] = __ffma2_rn(pi, vi, are[jj * 3 + tt]);
+              aim[jj * 3 + tt] = __ffma2_rn(pr, vi, aim[jj * 3 + tt]);
+              aim[jj * 3 + tt] = __ffma2_rn(npi, vr, aim[jj * 3 + tt]);
+            }
           }
         }
       }
@@ -216,7 +227,6 @@ __global__ void __launch_bounds__(RS_THREADS) restrict_kernel(const float2* __re
       }
     }
     if (live && ks == 0) {
-      const int j0 = 3 * jg, t0 = 3 * tg;
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj)
 #pragma unroll
@@ -231,7 +241,15 @@ __global__ void __launch_bounds__(RS_THREADS) restrict_kernel(const float2* __re
 void restrict_vec(const AggDims& g, const float2* P, const float* r, float* xc, int nv, int d, int nsys,
                   cudaStream_t st) {
   const int nt = ntiles(nsys, T2);
-  restrict_kernel<<<(unsigned)(g.Vc * 2), RS_THREADS, sizeof(int) * g.asize, st>>>(P, r, xc, g, nv, d, nt);
+  int kc = RS_KC;
+  while (kc > RS_KS && sizeof(float4) * (size_t)nt * kc + sizeof(int) * g.asize > 190 * 1024) kc -= RS_KS;
+  const size_t smem = sizeof(float4) * (size_t)nt * kc + sizeof(int) * g.asize;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(restrict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  restrict_kernel<<<(unsigned)(g.Vc * 2), RS_THREADS, smem, st>>>(P, r, xc, g, nv, d, nt, kc);
   TM_COUNT();
 }
 

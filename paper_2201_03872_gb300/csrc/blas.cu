@@ -141,37 +141,67 @@ size_t partial_elems(int64_t M, int nsys, int kmax, int T) {
 // ----------------------------------------------------------------------- updates
 // y[n] = y[n] - sum_i c[i * cstride + n] * V_i[n]   (c complex double per system);
 // with sign = +1 it adds instead. Inactive systems (mask[n] == 0) are left unchanged.
+// The coefficients of the block's tile are converted once into shared memory (k <= MAXPY_K);
+// the basis loop is unrolled so that several vector loads are in flight per thread.
+constexpr int MAXPY_K = 128;
+
 template <typename real, int T>
 __global__ void maxpy_kernel(const real* __restrict__ Vb, int64_t vstride, int k, const double2* __restrict__ c,
                              int64_t cstride, real sign, real* __restrict__ y, int64_t M, int nsys,
                              const int* __restrict__ mask) {
+  __shared__ real cre[MAXPY_K][T], cim[MAXPY_K][T];
   const int tile = blockIdx.y;
   const int64_t toff = (int64_t)tile * M * 2 * T;
-  real cr[T], ci[T];
-  bool any = false;
+  for (int q = threadIdx.x; q < k * T; q += blockDim.x) {
+    const int i = q / T, l = q % T;
+    const int n = tile * T + l;
+    const bool on = n < nsys && (!mask || mask[n]);
+    const double2 cc = on ? c[i * cstride + n] : make_double2(0, 0);
+    cre[i][l] = (real)cc.x * sign;
+    cim[i][l] = (real)cc.y * sign;
+  }
+  __syncthreads();
   int64_t m0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (int64_t m = m0; m < M; m += (int64_t)gridDim.x * blockDim.x) {
     Ent<real, T> acc = lde<real, T>(y + toff + m * 2 * T);
+    const real* vp = Vb + toff + m * 2 * T;
+#pragma unroll 4
     for (int i = 0; i < k; ++i) {
+      const Ent<real, T> v = lde<real, T>(vp + i * vstride);
 #pragma unroll
       for (int l = 0; l < T; ++l) {
-        int n = tile * T + l;
-        bool on = n < nsys && (!mask || mask[n]);
-        double2 cc = on ? c[i * cstride + n] : make_double2(0, 0);
-        cr[l] = (real)cc.x * sign;
-        ci[l] = (real)cc.y * sign;
-        any |= on;
-      }
-      Ent<real, T> v = lde<real, T>(Vb + i * vstride + toff + m * 2 * T);
-#pragma unroll
-      for (int l = 0; l < T; ++l) {
-        acc.re[l] += cr[l] * v.re[l] - ci[l] * v.im[l];
-        acc.im[l] += cr[l] * v.im[l] + ci[l] * v.re[l];
+        acc.re[l] += cre[i][l] * v.re[l] - cim[i][l] * v.im[l];
+        acc.im[l] += cre[i][l] * v.im[l] + cim[i][l] * v.re[l];
       }
     }
     ste<real, T>(y + toff + m * 2 * T, acc);
   }
-  (void)any;
+}
+
+// the same for k > MAXPY_K: coefficients read from global memory
+template <typename real, int T>
+__global__ void maxpy_long_kernel(const real* __restrict__ Vb, int64_t vstride, int k, const double2* __restrict__ c,
+                                  int64_t cstride, real sign, real* __restrict__ y, int64_t M, int nsys,
+                                  const int* __restrict__ mask) {
+  const int tile = blockIdx.y;
+  const int64_t toff = (int64_t)tile * M * 2 * T;
+  int64_t m0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t m = m0; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+    Ent<real, T> acc = lde<real, T>(y + toff + m * 2 * T);
+    for (int i = 0; i < k; ++i) {
+      const Ent<real, T> v = lde<real, T>(Vb + i * vstride + toff + m * 2 * T);
+#pragma unroll
+      for (int l = 0; l < T; ++l) {
+        const int n = tile * T + l;
+        const bool on = n < nsys && (!mask || mask[n]);
+        const double2 cc = on ? c[i * cstride + n] : make_double2(0, 0);
+        const real cr = (real)cc.x * sign, ci = (real)cc.y * sign;
+        acc.re[l] += cr * v.re[l] - ci * v.im[l];
+        acc.im[l] += cr * v.im[l] + ci * v.re[l];
+      }
+    }
+    ste<real, T>(y + toff + m * 2 * T, acc);
+  }
 }
 
 static dim3 upd_grid(int64_t M, int nt, int bs) {
@@ -186,8 +216,13 @@ void maxpy(const real* V, int64_t vstride, int k, const double2* c, int64_t cstr
            int nsys, const int* mask, cudaStream_t st) {
   constexpr int T = Tile<real>::T;
   int nt = ntiles(nsys, T);
-  maxpy_kernel<real, T><<<upd_grid(M, nt, 256), 256, 0, st>>>(V, vstride, k, c, cstride, (real)sign, y, M, nsys,
-                                                               mask); TM_COUNT();
+  if (k <= MAXPY_K)
+    maxpy_kernel<real, T><<<upd_grid(M, nt, 256), 256, 0, st>>>(V, vstride, k, c, cstride, (real)sign, y, M, nsys,
+                                                                 mask);
+  else
+    maxpy_long_kernel<real, T><<<upd_grid(M, nt, 256), 256, 0, st>>>(V, vstride, k, c, cstride, (real)sign, y, M,
+                                                                      nsys, mask);
+  TM_COUNT();
 }
 
 // y[n] = a[n] * x[n] + b[n] * y[n]; a, b complex per system (nullptr a => 0, nullptr b => y ignored,

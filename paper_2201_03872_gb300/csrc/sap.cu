@@ -191,9 +191,10 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
       if (act) {
 #define TM_BHOP(NU)                                                                              \
         {                                                                                        \
-          if (nf[NU] >= 0) hop2<NU, true>(q, rb + nf[NU] * 4, bv, Ls + NU * 9 * bv, bv, tid, pf[NU]); \
+          if (nf[NU] >= 0)                                                                       \
+            hop2<NU, true>(q, rb + nf[NU] * 4, bv, Ls + NU * 9 * bv, bv, tid, NU == 3 ? pf[3] : 1.f); \
           if (nbk[NU] >= 0)                                                                      \
-            hop2<NU, false>(q, rb + nbk[NU] * 4, bv, Ls + NU * 9 * bv, bv, nbk[NU], pb[NU]);     \
+            hop2<NU, false>(q, rb + nbk[NU] * 4, bv, Ls + NU * 9 * bv, bv, nbk[NU], NU == 3 ? pb[3] : 1.f); \
         }
         TM_BHOP(0)
         TM_BHOP(1)

@@ -283,23 +283,25 @@ __global__ void __launch_bounds__(256) sap_face_kernel(const float2* __restrict_
   if (!(fwd[0] || fwd[1] || fwd[2] || fwd[3] || bwd[0] || bwd[1] || bwd[2] || bwd[3])) return;
   const int64_t tstride = (int64_t)12 * V * 2 * T;
   const real* dt = delta + tile * tstride;
-  Spinor<real, T> acc;
+  static_assert(sizeof(real) == 4 && T == 2, "packed FP32 tiles");
+  Spinor2 acc;
 #pragma unroll
-  for (int k = 0; k < 12; ++k)
-#pragma unroll
-    for (int l = 0; l < T; ++l) { acc.c[k].re[l] = 0; acc.c[k].im[l] = 0; }
+  for (int k = 0; k < 12; ++k) {
+    acc.c[k].re = make_float2(0.f, 0.f);
+    acc.c[k].im = make_float2(0.f, 0.f);
+  }
   const int64_t strides[4] = {1, (int64_t)d.L[0], (int64_t)d.L[0] * d.L[1], (int64_t)d.L[0] * d.L[1] * d.L[2]};
 #define TM_FHOP(NU)                                                                                   \
   {                                                                                                   \
     if (fwd[NU]) {                                                                                    \
       int64_t sf = c[NU] + 1 < d.L[NU] ? s + strides[NU] : s - (int64_t)(d.L[NU] - 1) * strides[NU];  \
       real ph = (NU == 3 && c[3] == d.L[3] - 1) ? (real)d.bc_t : real(1);                           \
-      hop<NU, true, real, T>(acc, dt + sf * 2 * T, V, U + (int64_t)NU * 9 * V, V, s, ph);              \
+      hop2<NU, true>(acc, dt + sf * 2 * T, V, U + (int64_t)NU * 9 * V, V, s, ph);                      \
     }                                                                                                 \
     if (bwd[NU]) {                                                                                    \
       int64_t sb = c[NU] > 0 ? s - strides[NU] : s + (int64_t)(d.L[NU] - 1) * strides[NU];             \
       real ph = (NU == 3 && c[3] == 0) ? (real)d.bc_t : real(1);                                     \
-      hop<NU, false, real, T>(acc, dt + sb * 2 * T, V, U + (int64_t)NU * 9 * V, V, sb, ph);            \
+      hop2<NU, false>(acc, dt + sb * 2 * T, V, U + (int64_t)NU * 9 * V, V, sb, ph);                    \
     }                                                                                                 \
   }
   TM_FHOP(0)
@@ -312,10 +314,10 @@ __global__ void __launch_bounds__(256) sap_face_kernel(const float2* __restrict_
   for (int k = 0; k < 12; ++k) {
     int64_t o = ((int64_t)k * V + s) * 2 * T;
     float4 v = *reinterpret_cast<const float4*>(rt + o);
-    v.x += 0.5f * acc.c[k].re[0];
-    v.y += 0.5f * acc.c[k].re[1];
-    v.z += 0.5f * acc.c[k].im[0];
-    v.w += 0.5f * acc.c[k].im[1];
+    v.x += 0.5f * acc.c[k].re.x;
+    v.y += 0.5f * acc.c[k].re.y;
+    v.z += 0.5f * acc.c[k].im.x;
+    v.w += 0.5f * acc.c[k].im.y;
     *reinterpret_cast<float4*>(rt + o) = v;
   }
 }

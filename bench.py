@@ -46,6 +46,23 @@ def dirac_bytes_per_site(nsys, prec):
     return (4 * 18 + 72) * es + nsys * 2 * 24 * es
 
 
+# DRAM bytes (read + write) of one fine-stencil launch at 16^3x32 x 12 systems, from the ncu
+# capture summarised in profiles/dirac_kernel_16x16x16x32_n12.md; valid only for the kernel
+# sources it was taken on (SHA-1 of dirac.cu and stencil.cuh), else reported as null
+DIRAC_TRAFFIC = {"bytes": 237069824 + 120919040,
+                 "sha1": {"dirac.cu": "24e92d0ad15242de099dc0789bc8e321b64cb249",
+                          "stencil.cuh": "bdc68ee2e32fd9112f7efc57c95df0422ce387ff"}}
+
+
+def dirac_traffic():
+    import hashlib
+    for name, want in DIRAC_TRAFFIC["sha1"].items():
+        path = os.path.join(ROOT, "paper_2201_03872_gb300", "csrc", name)
+        if not os.path.exists(path) or hashlib.sha1(open(path, "rb").read()).hexdigest() != want:
+            return None
+    return DIRAC_TRAFFIC["bytes"]
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -210,7 +227,7 @@ def run_dirac(args, world, rank, local):
                    "kappa": kappa, "kappa_source": ksrc, "nsys": nsys,
                    "l2": "working set 378 MB > 129 MB L2; back-to-back applications"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_source": peak_src,
+                     "traffic": dirac_traffic(), "peak_source": peak_src,
                      "kernel": "dirac_kernel<float,2>", "algorithmic_bytes_per_launch": bytes_per_apply},
         "e2e": {"value": bytes_per_apply * args.steps * world / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
                 "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(x.nbytes)},
@@ -348,7 +365,7 @@ def run_solve(args, world, rank, local):
                    "iterations": {"outer": s0.outer_iters, "fgmres": s0.inner_iters, "coarse": s0.coarse_iters},
                    "l2": "working set > 129 MB L2 (solver vectors 3+ GB)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_source": peak_src, "kernel": "dirac_kernel<float,2> (fine stencil)",
+                     "traffic": dirac_traffic(), "peak_source": peak_src, "kernel": "dirac_kernel<float,2> (fine stencil)",
                      "algorithmic_bytes_per_launch": bytes_per_apply, "launch_ms": kern_ms},
         "e2e": {"value": nsys * args.steps * world / e2e_s, "unit": "solves/s",
                 "h2d_bytes_per_step": int(bh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)},

@@ -339,6 +339,8 @@ def run_solve(args, world, rank, local):
             variants[label] = {"solves_per_s": nr * len(mus) / (ms * 1e-3), "ms_per_step": ms, "all_converged": okv,
                                "fgmres_iterations": stv[0].inner_iters, "coarse_iterations": stv[0].coarse_iters}
         timed("single_system", 1)
+        # the plain comparator: one system, every vector, operator and reduction in FP64
+        timed("plain_fp64_single_system", 1, precision=64)
         timed("block_gmres_coarse", nrhs, coarse_solver=1)
         t = time.time()
         rep = T.tmamg_nn_train(ctx, T.tmamg_default_nn_params(pairs=48, batch=12, epochs=30, lr=2e-3, mu=wl["mu"],

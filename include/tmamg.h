@@ -77,7 +77,11 @@ typedef struct {
   int coarse_solver;   /* 0: persistent GMRES (one cooperative launch per coarse solve, all systems);
                           1: block GMRES over the rhs of each shift; 2: GMRES with one launch per step */
   double delta_mu;     /* coarse twisted-mass factor (paper Fig. 6 caption), 1 = none */
-  int precision;       /* 32: mixed (FP32 inner, FP64 outer); 64: plain FP64 single-precision-free path */
+  int precision;       /* 32: the batched mixed-precision solver (FP32 inner FGMRES and AMG cycle, FP16 coarse
+                          operands, FP64 refinement); 64: the plain comparator, FGMRES(restart) with the same
+                          two-level AMG cycle where every vector, operator and reduction is FP64 (coarse GMRES
+                          with one launch per step, no refinement loop, no learned step, coarse_solver and
+                          coarse_precision ignored), restarted until the true FP64 residual meets tol */
   int use_nn;          /* learned step in the AMG cycle: 0 off, 1 if trained and enabled by the gate, 2 forced */
   int poll;            /* coarse iterations between host convergence polls */
   int coarse_precision; /* coarse stencil: 16 (default; 0 means 16) FP16 operator and FP16-staged vectors on

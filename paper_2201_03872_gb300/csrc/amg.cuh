@@ -35,4 +35,14 @@ void coarse_apply(const CoarseDims& cd, const float2* A, const float* x, float* 
 void build_coarse_operator_fine(const AggDims& g, const float2* U32, const float* C32, const float2* P, float2* A,
                                 int nv, int bc_t, float* W, float* Y, float* R, cudaStream_t st);
 
+// plain FP64 forms (amg64.cu) for the FP64 comparator solver: FP64 bundles, one system per tile;
+// P64 / A64 are the FP32 P and coarse blocks widened to FP64 (widen_f2)
+void widen_f2(const float2* in, double2* out, int64_t n, cudaStream_t st);
+void restrict64(const AggDims& g, const double2* P64, const double* r, double* xc, int nv, int d, int nsys,
+                cudaStream_t st);
+void prolong64(const AggDims& g, const double2* P64, const double* xc, double* e, int nv, int d, int nsys,
+               cudaStream_t st);
+void coarse_apply64(const CoarseDims& cd, const double2* A64, const double* x, double* y, const double* mu,
+                    double dmu, int nsys, cudaStream_t st);
+
 }  // namespace tmamg

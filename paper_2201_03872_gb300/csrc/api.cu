@@ -253,6 +253,8 @@ void free_levels(tmamg_ctx* ctx) {
     cudaFree(l.cmax);
     cudaFree(l.cerr);
     cudaFree(l.x16);
+    cudaFree(l.P64);
+    cudaFree(l.A64);
   }
   ctx->levels.clear();
 }

@@ -59,11 +59,14 @@ struct CoarseLevel {
   int* cerr = nullptr;    // bounded-wait flag of the stand-alone tensor-core stencil
   __half* x16 = nullptr;  // B images of the stand-alone tensor-core stencil (grown on demand)
   size_t x16_bytes = 0;
+  double2* P64 = nullptr;  // P and A widened to FP64 for the plain FP64 solver (made on first use)
+  double2* A64 = nullptr;
 };
 
 constexpr int CM_MAXSYS = 1024;  // systems per stand-alone tensor-core stencil call
 
 struct Workspace;
+struct Workspace64;
 struct NNState;
 
 }  // namespace tmamg
@@ -90,6 +93,7 @@ struct tmamg_ctx {
   tmamg_setup_params sp;
   std::vector<tmamg::CoarseLevel> levels;
   tmamg::Workspace* ws = nullptr;
+  tmamg::Workspace64* ws64 = nullptr;  // plain FP64 solver state (made on first use)
   tmamg::NNState* nn = nullptr;  // learned preconditioner step (optional)
 };
 

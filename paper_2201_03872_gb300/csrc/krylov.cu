@@ -190,38 +190,39 @@ static void poll_active(GmresState& st, cudaStream_t s) {
   cudaStreamSynchronize(s);
 }
 
-CycleResult gmres_cycle(GmresState& st, const LevelOps& ops, int nsys, int m, float* V, int64_t vstride, float* Z,
-                        float* x, const int* participate, const double* rel_tol, int poll, bool cgs2,
+template <typename real>
+CycleResult gmres_cycle(GmresState& st, const LevelOpsT<real>& ops, int nsys, int m, real* V, int64_t vstride,
+                        real* Z, real* x, const int* participate, const double* rel_tol, int poll, bool cgs2,
                         cudaStream_t s) {
   const int cap = st.cap;
   const int64_t M = ops.M;
   // |r0|
-  mdot<float>(V, 0, 1, V, M, nsys, st.tmp, cap, st.partial, s);
+  mdot<real>(V, 0, 1, V, M, nsys, st.tmp, cap, st.partial, s);
   gmres_init_kernel<<<1, 1024, 0, s>>>(st.tmp, nsys, cap, m, participate, rel_tol, st.beta, st.g, st.sc, st.tolabs,
                                        st.kconv, st.active, st.nactive); TM_COUNT();
-  axpby<float>(nullptr, 0, nullptr, st.sc, 2, V, M, nsys, nullptr, s);
+  axpby<real>(nullptr, 0, nullptr, st.sc, 2, V, M, nsys, nullptr, s);
   int done = 0;
   for (int j = 0; j < m; ++j) {
-    float* vj = V + (int64_t)j * vstride;
-    float* w = V + (int64_t)(j + 1) * vstride;
-    const float* z = vj;
+    real* vj = V + (int64_t)j * vstride;
+    real* w = V + (int64_t)(j + 1) * vstride;
+    const real* z = vj;
     if (ops.precond) {
-      float* zj = Z + (int64_t)j * vstride;
+      real* zj = Z + (int64_t)j * vstride;
       ops.precond(vj, zj);
       z = zj;
     }
     ops.A(z, w);
     double2* Hcol = st.H + (size_t)j * (m + 1) * cap;
-    mdot<float>(V, vstride, j + 1, w, M, nsys, Hcol, cap, st.partial, s);
-    maxpy<float>(V, vstride, j + 1, Hcol, cap, -1.0, w, M, nsys, nullptr, s);
+    mdot<real>(V, vstride, j + 1, w, M, nsys, Hcol, cap, st.partial, s);
+    maxpy<real>(V, vstride, j + 1, Hcol, cap, -1.0, w, M, nsys, nullptr, s);
     if (cgs2) {
-      mdot<float>(V, vstride, j + 1, w, M, nsys, st.tmp, cap, st.partial, s);
-      maxpy<float>(V, vstride, j + 1, st.tmp, cap, -1.0, w, M, nsys, nullptr, s);
+      mdot<real>(V, vstride, j + 1, w, M, nsys, st.tmp, cap, st.partial, s);
+      maxpy<real>(V, vstride, j + 1, st.tmp, cap, -1.0, w, M, nsys, nullptr, s);
       add_col_kernel<<<((j + 1) * nsys + 127) / 128, 128, 0, s>>>(Hcol, st.tmp, j + 1, nsys, cap); TM_COUNT();
     }
-    mdot<float>(w, 0, 1, w, M, nsys, st.tmp, cap, st.partial, s);
+    mdot<real>(w, 0, 1, w, M, nsys, st.tmp, cap, st.partial, s);
     norm_finish_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(st.tmp, Hcol + (size_t)(j + 1) * cap, st.sc, nsys); TM_COUNT();
-    axpby<float>(nullptr, 0, nullptr, st.sc, 2, w, M, nsys, nullptr, s);
+    axpby<real>(nullptr, 0, nullptr, st.sc, 2, w, M, nsys, nullptr, s);
     givens_kernel<<<1, 1024, 0, s>>>(st.H, st.cs, st.sn, st.g, st.resid, st.tolabs, st.kconv, st.active, st.nactive,
                                      j, m, nsys, cap); TM_COUNT();
     done = j + 1;
@@ -232,10 +233,15 @@ CycleResult gmres_cycle(GmresState& st, const LevelOps& ops, int nsys, int m, fl
     }
   }
   backsub_kernel<<<(nsys + 127) / 128, 128, 0, s>>>(st.H, st.g, st.y, st.kconv, m, nsys, cap, done); TM_COUNT();
-  maxpy<float>(ops.precond ? Z : V, vstride, done, st.y, cap, +1.0, x, M, nsys, nullptr, s);
+  maxpy<real>(ops.precond ? Z : V, vstride, done, st.y, cap, +1.0, x, M, nsys, nullptr, s);
   CycleResult r;
   r.iters = done;
   return r;
 }
+
+template CycleResult gmres_cycle<float>(GmresState&, const LevelOpsT<float>&, int, int, float*, int64_t, float*, float*,
+                                        const int*, const double*, int, bool, cudaStream_t);
+template CycleResult gmres_cycle<double>(GmresState&, const LevelOpsT<double>&, int, int, double*, int64_t, double*,
+                                         double*, const int*, const double*, int, bool, cudaStream_t);
 
 }  // namespace tmamg

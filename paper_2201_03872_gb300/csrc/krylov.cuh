@@ -29,11 +29,13 @@ struct GmresState {
   void release();
 };
 
-struct LevelOps {
+template <typename real>
+struct LevelOpsT {
   int64_t M;  // entries per tile (ncomp * nsite)
-  std::function<void(const float* x, float* y)> A;        // y = A x for all systems
-  std::function<void(const float* v, float* z)> precond;  // z = M v; empty = none
+  std::function<void(const real* x, real* y)> A;        // y = A x for all systems
+  std::function<void(const real* v, real* z)> precond;  // z = M v; empty = none
 };
+using LevelOps = LevelOpsT<float>;
 
 struct CycleResult {
   int iters;  // Arnoldi steps performed (max over systems)
@@ -45,8 +47,10 @@ struct CycleResult {
 // (or V y). participate: device mask of systems to iterate (nullptr = all).
 // rel_tol: device array of per-system relative tolerances (|r| <= rel_tol * |r0|).
 // poll: Arnoldi steps between host checks of the active count. cgs2: re-orthogonalise.
-CycleResult gmres_cycle(GmresState& st, const LevelOps& ops, int nsys, int m, float* V, int64_t vstride, float* Z,
-                        float* x, const int* participate, const double* rel_tol, int poll, bool cgs2,
+// Vectors are FP32 bundles (tiles of 2 systems) or FP64 bundles (one system per tile).
+template <typename real>
+CycleResult gmres_cycle(GmresState& st, const LevelOpsT<real>& ops, int nsys, int m, real* V, int64_t vstride,
+                        real* Z, real* x, const int* participate, const double* rel_tol, int poll, bool cgs2,
                         cudaStream_t s);
 
 // small per-system kernels used by the drivers

@@ -394,3 +394,241 @@ void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C
 }
 
 }  // namespace tmamg
+
+// ================================================================== plain FP64 form
+// The same red-black SAP (MR block solves, face-only residual update) in FP64 for the plain
+// comparator solver: FP64 bundles with one system per tile, links and clover from their FP64
+// copies in global memory. One CTA per (block of the colour, system), one thread per site; the
+// block residual in shared memory, the block correction in registers.
+namespace tmamg {
+
+__device__ __forceinline__ void block_reduce_d(double* v, int n, double* red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int i = 0; i < n; ++i) {
+    double x = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    v[i] = x;
+  }
+  if (lane == 0)
+    for (int i = 0; i < n; ++i) red[warp * 4 + i] = v[i];
+  __syncthreads();
+  for (int i = 0; i < n; ++i) {
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s += red[w * 4 + i];
+    v[i] = s;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) sap64_mr_kernel(const double2* __restrict__ U, const double* __restrict__ C,
+                                                       double* __restrict__ r, double* __restrict__ delta,
+                                                       double* __restrict__ e, const double* __restrict__ mu,
+                                                       SapDims d, int colour, int steps) {
+  extern __shared__ double2 sm64[];
+  const int bv = d.bv;
+  double2* rho = sm64;                                       // [12][bv]
+  double* red = reinterpret_cast<double*>(rho + 12 * bv);   // [nwarps][4]
+  const int tid = threadIdx.x;
+  const bool act = tid < bv;
+  const int b = colour_block(d, colour, blockIdx.x);
+  const int n = blockIdx.y;  // system (one per tile)
+  int bc[4], lc[4], c[4];
+  block_site(d, b, act ? tid : 0, bc, lc, c);
+  const int64_t V = (int64_t)d.L[0] * d.L[1] * d.L[2] * d.L[3];
+  const int64_t s = site_index(c, d.L);
+  const int64_t tstride = (int64_t)12 * V * 2;
+  double* rt = r + n * tstride;
+  Spinor<double, 1> eb;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    eb.c[k].re[0] = 0;
+    eb.c[k].im[0] = 0;
+    if (act) rho[k * bv + tid] = *reinterpret_cast<const double2*>(rt + ((int64_t)k * V + s) * 2);
+  }
+  double m[1] = {mu[n]};
+  int nf[4], nbk[4];
+  double pf[4], pb[4];
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    int l2[4] = {lc[0], lc[1], lc[2], lc[3]};
+    pf[nu] = 1;
+    pb[nu] = 1;
+    if (lc[nu] + 1 < d.bs[nu]) {
+      l2[nu] = lc[nu] + 1;
+      nf[nu] = local_index(l2, d);
+    } else if (d.nb[nu] == 1) {
+      l2[nu] = 0;
+      nf[nu] = local_index(l2, d);
+      if (nu == 3) pf[nu] = (double)d.bc_t;
+    } else {
+      nf[nu] = -1;
+    }
+    l2[nu] = lc[nu];
+    if (lc[nu] > 0) {
+      l2[nu] = lc[nu] - 1;
+      nbk[nu] = local_index(l2, d);
+    } else if (d.nb[nu] == 1) {
+      l2[nu] = d.bs[nu] - 1;
+      nbk[nu] = local_index(l2, d);
+      if (nu == 3) pb[nu] = (double)d.bc_t;
+    } else {
+      nbk[nu] = -1;
+    }
+  }
+  const int64_t strides[4] = {1, (int64_t)d.L[0], (int64_t)d.L[0] * d.L[1], (int64_t)d.L[0] * d.L[1] * d.L[2]};
+  const double* rb = reinterpret_cast<const double*>(rho);
+  for (int it = 0; it < steps; ++it) {
+    __syncthreads();
+    Spinor<double, 1> q;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { q.c[k].re[0] = 0; q.c[k].im[0] = 0; }
+    double v[3] = {0, 0, 0};
+    if (act) {
+#define TM_BHOP64(NU)                                                                                      \
+      {                                                                                                    \
+        if (nf[NU] >= 0)                                                                                   \
+          hop<NU, true, double, 1>(q, rb + (int64_t)nf[NU] * 2, bv, U + (int64_t)NU * 9 * V, V, s, pf[NU]); \
+        if (nbk[NU] >= 0) {                                                                                \
+          int64_t sb = c[NU] > 0 ? s - strides[NU] : s + (int64_t)(d.L[NU] - 1) * strides[NU];             \
+          hop<NU, false, double, 1>(q, rb + (int64_t)nbk[NU] * 2, bv, U + (int64_t)NU * 9 * V, V, sb, pb[NU]); \
+        }                                                                                                  \
+      }
+      TM_BHOP64(0)
+      TM_BHOP64(1)
+      TM_BHOP64(2)
+      TM_BHOP64(3)
+#undef TM_BHOP64
+      local_term<double, 1>(q, rb + (int64_t)tid * 2, bv, C, V, s, m);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const double2 rr = rho[k * bv + tid];
+        const double qr = q.c[k].re[0], qi = q.c[k].im[0];
+        v[0] += qr * qr + qi * qi;
+        v[1] += qr * rr.x + qi * rr.y;
+        v[2] += qr * rr.y - qi * rr.x;
+      }
+    }
+    block_reduce_d(v, 3, red);
+    const double ar = v[0] > 0 ? v[1] / v[0] : 0.0, ai = v[0] > 0 ? v[2] / v[0] : 0.0;
+    if (act) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        double2 rr = rho[k * bv + tid];
+        eb.c[k].re[0] += ar * rr.x - ai * rr.y;
+        eb.c[k].im[0] += ar * rr.y + ai * rr.x;
+        const double qr = q.c[k].re[0], qi = q.c[k].im[0];
+        rr.x -= ar * qr - ai * qi;
+        rr.y -= ar * qi + ai * qr;
+        rho[k * bv + tid] = rr;
+      }
+    }
+  }
+  if (!act) return;
+  double* dt = delta + n * tstride;
+  double* et = e + n * tstride;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int64_t o = ((int64_t)k * V + s) * 2;
+    *reinterpret_cast<double2*>(dt + o) = make_double2(eb.c[k].re[0], eb.c[k].im[0]);
+    const double2 e0 = *reinterpret_cast<const double2*>(et + o);
+    *reinterpret_cast<double2*>(et + o) = make_double2(e0.x + eb.c[k].re[0], e0.y + eb.c[k].im[0]);
+    *reinterpret_cast<double2*>(rt + o) = rho[k * bv + tid];
+  }
+}
+
+// r(s) += 1/2 sum over block-crossing hops of delta on the sites of blocks of colour `other`
+__global__ void __launch_bounds__(256) sap64_face_kernel(const double2* __restrict__ U,
+                                                         const double* __restrict__ delta, double* __restrict__ r,
+                                                         SapDims d, int other) {
+  const int64_t V = (int64_t)d.L[0] * d.L[1] * d.L[2] * d.L[3];
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int n = blockIdx.y;
+  if (s >= V) return;
+  int c[4];
+  site_coords(s, d.L, c);
+  int col = 0;
+  bool fwd[4], bwd[4];
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    col += c[nu] / d.bs[nu];
+    fwd[nu] = d.nb[nu] > 1 && (c[nu] % d.bs[nu]) == d.bs[nu] - 1;
+    bwd[nu] = d.nb[nu] > 1 && (c[nu] % d.bs[nu]) == 0;
+  }
+  if ((col & 1) != other) return;
+  if (!(fwd[0] || fwd[1] || fwd[2] || fwd[3] || bwd[0] || bwd[1] || bwd[2] || bwd[3])) return;
+  const int64_t tstride = (int64_t)12 * V * 2;
+  const double* dt = delta + n * tstride;
+  Spinor<double, 1> acc;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) { acc.c[k].re[0] = 0; acc.c[k].im[0] = 0; }
+  const int64_t strides[4] = {1, (int64_t)d.L[0], (int64_t)d.L[0] * d.L[1], (int64_t)d.L[0] * d.L[1] * d.L[2]};
+#define TM_FHOP64(NU)                                                                                  \
+  {                                                                                                    \
+    if (fwd[NU]) {                                                                                     \
+      int64_t sf = c[NU] + 1 < d.L[NU] ? s + strides[NU] : s - (int64_t)(d.L[NU] - 1) * strides[NU];   \
+      double ph = (NU == 3 && c[3] == d.L[3] - 1) ? (double)d.bc_t : 1.0;                            \
+      hop<NU, true, double, 1>(acc, dt + sf * 2, V, U + (int64_t)NU * 9 * V, V, s, ph);                 \
+    }                                                                                                  \
+    if (bwd[NU]) {                                                                                     \
+      int64_t sb = c[NU] > 0 ? s - strides[NU] : s + (int64_t)(d.L[NU] - 1) * strides[NU];              \
+      double ph = (NU == 3 && c[3] == 0) ? (double)d.bc_t : 1.0;                                      \
+      hop<NU, false, double, 1>(acc, dt + sb * 2, V, U + (int64_t)NU * 9 * V, V, sb, ph);               \
+    }                                                                                                  \
+  }
+  TM_FHOP64(0)
+  TM_FHOP64(1)
+  TM_FHOP64(2)
+  TM_FHOP64(3)
+#undef TM_FHOP64
+  double* rt = r + n * tstride;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int64_t o = ((int64_t)k * V + s) * 2;
+    double2 v = *reinterpret_cast<const double2*>(rt + o);
+    v.x += 0.5 * acc.c[k].re[0];
+    v.y += 0.5 * acc.c[k].im[0];
+    *reinterpret_cast<double2*>(rt + o) = v;
+  }
+}
+
+void sap_apply64(const Geom& g, const int bs[4], const double2* U64, const double* C64, double* r, double* e,
+                 double* delta, const double* mu, int nsys, int cycles, int steps, cudaStream_t st) {
+  SapDims d;
+  int nblocks = 1;
+  for (int k = 0; k < 4; ++k) {
+    d.L[k] = g.L[k];
+    d.bs[k] = bs[k];
+    d.nb[k] = g.L[k] / bs[k];
+    nblocks *= d.nb[k];
+  }
+  d.bv = bs[0] * bs[1] * bs[2] * bs[3];
+  d.bc_t = g.bc_t;
+  d.pdim = -1;
+  for (int k = 3; k >= 0; --k)
+    if (d.nb[k] >= 2) d.pdim = k;
+  cudaMemsetAsync(e, 0, sizeof(double) * 24 * g.V * nsys, st);
+  const int nthreads = (d.bv + 31) / 32 * 32;
+  const size_t smem = sizeof(double2) * 12 * d.bv + sizeof(double) * 4 * (nthreads / 32);
+  static bool attr = false;
+  if (!attr) {  // 4^4 blocks need 49 KB, above the default dynamic limit
+    cudaFuncSetAttribute(sap64_mr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    attr = true;
+  }
+  for (int cy = 0; cy < cycles; ++cy) {
+    for (int colour = 0; colour < 2; ++colour) {
+      const int nb_c = d.pdim < 0 ? (colour == 0 ? 1 : 0) : nblocks / 2;
+      if (nb_c > 0) {
+        sap64_mr_kernel<<<dim3(nb_c, nsys), nthreads, smem, st>>>(U64, C64, r, delta, e, mu, d, colour, steps);
+        TM_COUNT();
+      }
+      if (!(cy == cycles - 1 && colour == 1)) {
+        sap64_face_kernel<<<dim3((unsigned)((g.V + 255) / 256), nsys), 256, 0, st>>>(U64, delta, r, d, 1 - colour);
+        TM_COUNT();
+      }
+    }
+  }
+}
+
+}  // namespace tmamg

@@ -14,4 +14,8 @@ int sap_check_blocks(const Geom& g, const int bs[4], std::string& why);
 void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C32, float* r, float* e, float* delta,
                const double* mu, int nsys, int cycles, int steps, cudaStream_t st);
 
+// The same smoother in FP64 (FP64 bundles, one system per tile), for the plain comparator solver.
+void sap_apply64(const Geom& g, const int bs[4], const double2* U64, const double* C64, double* r, double* e,
+                 double* delta, const double* mu, int nsys, int cycles, int steps, cudaStream_t st);
+
 }  // namespace tmamg

@@ -65,11 +65,38 @@ static void ws_free(Workspace* w) {
   *w = Workspace();
 }
 
+// state of the plain FP64 solver (FP64 bundles, one system per tile)
+struct Workspace64 {
+  int nsys = 0, m = 0, mc = 0;
+  int64_t Vc = 0;
+  int nc = 0;
+  size_t fb = 0, cb = 0;  // bytes of one fine / coarse FP64 bundle
+  double *V = nullptr, *Z = nullptr, *x = nullptr, *b = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;
+  double *Vc_ = nullptr, *xc = nullptr, *rc = nullptr;
+  double *rel_top = nullptr, *rel_coarse = nullptr, *beta0 = nullptr, *bn = nullptr, *rn = nullptr;
+  double2 *dot = nullptr, *partial = nullptr, *ones = nullptr, *mones = nullptr;
+  GmresState top, coarse;
+};
+
+static void ws64_free(Workspace64* w) {
+  void* ptrs[] = {w->V, w->Z, w->x, w->b, w->t1, w->t2, w->t3, w->Vc_, w->xc, w->rc, w->rel_top, w->rel_coarse,
+                  w->beta0, w->bn, w->rn, w->dot, w->partial, w->ones, w->mones};
+  for (void* p : ptrs) cudaFree(p);
+  w->top.release();
+  w->coarse.release();
+  *w = Workspace64();
+}
+
 void free_workspace(tmamg_ctx* ctx) {
   if (ctx->ws) {
     ws_free(ctx->ws);
     delete ctx->ws;
     ctx->ws = nullptr;
+  }
+  if (ctx->ws64) {
+    ws64_free(ctx->ws64);
+    delete ctx->ws64;
+    ctx->ws64 = nullptr;
   }
 }
 
@@ -437,7 +464,7 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
   int done = 0;
   for (int cyc = 0; done < S.sp->coarse_maxiter; ++cyc) {
     int m = mc < S.sp->coarse_maxiter - done ? mc : S.sp->coarse_maxiter - done;
-    CycleResult r = gmres_cycle(w->coarse, ops, nsys, m, w->Vc, vstride, nullptr, xc, nullptr, w->rel_coarse,
+    CycleResult r = gmres_cycle<float>(w->coarse, ops, nsys, m, w->Vc, vstride, nullptr, xc, nullptr, w->rel_coarse,
                                 S.sp->poll, false, st);
     done += r.iters;
     if (cyc == 0) copy_beta_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->coarse.beta, w->beta0, nsys); TM_COUNT();
@@ -527,6 +554,213 @@ __global__ void add_iters_kernel(const int* kconv, const int* mask, int* it, int
   if (i < n && mask[i]) it[i] += kconv[i];
 }
 
+// ------------------------------------------------------------------ plain FP64 solver
+// The comparator of the batched mixed-precision solver: FGMRES(m) in FP64 preconditioned by the
+// same two-level AMG cycle (restriction, coarse GMRES to coarse_tol, prolongation, red-black
+// SAP) with every vector, operator and reduction in FP64, one system per bundle tile, no
+// refinement loop, no learned step. Restarted until every system's true FP64 residual meets tol.
+static int ensure_ws64(tmamg_ctx* ctx, int nsys, int m, int mc) {
+  if (!ctx->ws64) ctx->ws64 = new Workspace64();
+  Workspace64* w = ctx->ws64;
+  const CoarseLevel& L1 = ctx->levels[0];
+  if (nsys <= w->nsys && m <= w->m && mc <= w->mc && w->Vc == L1.Vc && w->nc == 2 * L1.nv) return 0;
+  const int ns = nsys > w->nsys ? nsys : w->nsys, mm = m > w->m ? m : w->m, mcc = mc > w->mc ? mc : w->mc;
+  ws64_free(w);
+  w->nsys = ns;
+  w->m = mm;
+  w->mc = mcc;
+  w->Vc = L1.Vc;
+  w->nc = 2 * L1.nv;
+  const int64_t V = ctx->g.V;
+  w->fb = (size_t)ns * 12 * V * 2 * sizeof(double);
+  w->cb = (size_t)ns * w->nc * w->Vc * 2 * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  A((void**)&w->V, w->fb * (mm + 1));
+  A((void**)&w->Z, w->fb * mm);
+  A((void**)&w->x, w->fb);
+  A((void**)&w->b, w->fb);
+  A((void**)&w->t1, w->fb);
+  A((void**)&w->t2, w->fb);
+  A((void**)&w->t3, w->fb);
+  A((void**)&w->Vc_, w->cb * (mcc + 1));
+  A((void**)&w->xc, w->cb);
+  A((void**)&w->rc, w->cb);
+  A((void**)&w->rel_top, sizeof(double) * ns);
+  A((void**)&w->rel_coarse, sizeof(double) * ns);
+  A((void**)&w->beta0, sizeof(double) * ns);
+  A((void**)&w->bn, sizeof(double) * ns);
+  A((void**)&w->rn, sizeof(double) * ns);
+  A((void**)&w->dot, sizeof(double2) * ns);
+  A((void**)&w->partial, sizeof(double2) * partial_elems(12 * V, ns, 1, 1));
+  A((void**)&w->ones, sizeof(double2) * ns);
+  A((void**)&w->mones, sizeof(double2) * ns);
+  if (e != cudaSuccess) {
+    ws64_free(w);
+    return check_cuda(ctx, e, "FP64 workspace allocation");
+  }
+  if (w->top.alloc(mm, ns, partial_elems(12 * V, ns, mm + 1, 1)) ||
+      w->coarse.alloc(mcc, ns, partial_elems((int64_t)w->nc * w->Vc, ns, mcc + 1, 1)))
+    return set_err(ctx, TMAMG_ERR_OOM, "FP64 gmres state");
+  fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->ones, ns, 1.0); TM_COUNT();
+  fill_c_kernel<<<(ns + 127) / 128, 128, 0, ctx->stream>>>(w->mones, ns, -1.0); TM_COUNT();
+  return check_cuda(ctx, cudaGetLastError(), "FP64 workspace init");
+}
+
+// xc ~ D_c^{-1} rc in FP64: restarted GMRES to coarse_tol (at most coarse_maxiter steps)
+static int coarse_solve64(tmamg_ctx* ctx, const tmamg_solve_params* sp, int nsys, const double* mu) {
+  Workspace64* w = ctx->ws64;
+  cudaStream_t st = ctx->stream;
+  const CoarseLevel& L1 = ctx->levels[0];
+  const CoarseDims cd = coarse_dims(L1);
+  const int64_t Mc = (int64_t)cd.nc * cd.Vc;
+  LevelOpsT<double> ops;
+  ops.M = Mc;
+  const double dmu = sp->delta_mu;
+  ops.A = [&, dmu](const double* xx, double* yy) { coarse_apply64(cd, L1.A64, xx, yy, mu, dmu, nsys, st); };
+  const int64_t cvs = (int64_t)(w->cb / sizeof(double));
+  cudaMemsetAsync(w->xc, 0, w->cb, st);
+  cudaMemcpyAsync(w->Vc_, w->rc, w->cb, cudaMemcpyDeviceToDevice, st);
+  set_rel_tol(w->rel_coarse, nsys, sp->coarse_tol, st);
+  int done = 0;
+  for (int cyc = 0; done < sp->coarse_maxiter; ++cyc) {
+    const int m = sp->coarse_restart < sp->coarse_maxiter - done ? sp->coarse_restart : sp->coarse_maxiter - done;
+    const CycleResult r = gmres_cycle<double>(w->coarse, ops, nsys, m, w->Vc_, cvs, nullptr, w->xc, nullptr,
+                                              w->rel_coarse, sp->poll, false, st);
+    done += r.iters;
+    if (cyc == 0) {
+      copy_beta_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->coarse.beta, w->beta0, nsys); TM_COUNT();
+    }
+    if (r.iters < m || done >= sp->coarse_maxiter) break;
+    ops.A(w->xc, w->Vc_);
+    axpby<double>(w->ones, 2, w->rc, w->mones, 2, w->Vc_, Mc, nsys, nullptr, st);
+    mdot<double>(w->Vc_, 0, 1, w->Vc_, Mc, nsys, w->dot, nsys, w->coarse.partial, st);
+    restart_tol_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->beta0, sp->coarse_tol, w->rel_coarse, nsys);
+    TM_COUNT();
+  }
+  return done;
+}
+
+// z = M v in FP64: coarse-grid correction, then SAP on the remaining residual
+static void amg_cycle64(tmamg_ctx* ctx, const tmamg_solve_params* sp, int nsys, const double* mu, const double* v,
+                        double* z, int& coarse_iters) {
+  Workspace64* w = ctx->ws64;
+  cudaStream_t st = ctx->stream;
+  const CoarseLevel& L1 = ctx->levels[0];
+  const AggDims ad = agg_dims(ctx->g, L1.agg);
+  const int64_t M = 12 * ctx->g.V;
+  restrict64(ad, L1.P64, v, w->rc, L1.nv, 6, nsys, st);
+  coarse_iters += coarse_solve64(ctx, sp, nsys, mu);
+  prolong64(ad, L1.P64, w->xc, z, L1.nv, 6, nsys, st);
+  launch_dirac<double>(ctx->g, ctx->U64, ctx->C64, z, w->t1, mu, nsys, st);
+  axpby<double>(w->ones, 2, v, w->mones, 2, w->t1, M, nsys, nullptr, st);  // t1 = v - D z
+  sap_apply64(ctx->g, ctx->sp.sap_block, ctx->U64, ctx->C64, w->t1, w->t2, w->t3, mu, nsys, ctx->sp.sap_cycles,
+              ctx->sp.sap_mr_steps, st);
+  axpby<double>(w->ones, 2, w->t2, w->ones, 2, z, M, nsys, nullptr, st);  // z += SAP
+}
+
+int do_solve64(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int nshift, double* x, int on_device,
+               const tmamg_solve_params* sp, tmamg_system_stats* stats) {
+  cudaStream_t st = ctx->stream;
+  const Geom& g = ctx->g;
+  const int nsys = nrhs * nshift;
+  CoarseLevel& L1 = ctx->levels[0];
+  const int nc = 2 * L1.nv;
+  const int64_t V = g.V, M = 12 * V;
+  int rc = 0;
+  if (!L1.P64) {
+    const int64_t np = L1.Vc * 2 * L1.nv * L1.asize * 6, na = 9 * L1.Vc * nc * nc;
+    rc = check_cuda(ctx, cudaMalloc(&L1.P64, sizeof(double2) * np), "cudaMalloc(P64)");
+    if (!rc) rc = check_cuda(ctx, cudaMalloc(&L1.A64, sizeof(double2) * na), "cudaMalloc(A64)");
+    if (rc) return rc;
+    widen_f2(L1.P, L1.P64, np, st);
+    widen_f2(L1.A, L1.A64, na, st);
+  }
+  rc = ensure_ws64(ctx, nsys, sp->restart, sp->coarse_restart);
+  if (rc) return rc;
+  Workspace64* w = ctx->ws64;
+  std::vector<double> musys(nsys);
+  for (int n = 0; n < nsys; ++n) musys[n] = mu[n % nshift];
+  rc = upload_mu(ctx, musys.data(), nsys);
+  if (rc) return rc;
+  const double* mud = ctx->mu_dev;
+  const double* bsrc = b;
+  double* bstage = nullptr;
+  if (!on_device) {
+    const size_t bytes = sizeof(double) * 2 * M * nrhs;
+    rc = check_cuda(ctx, cudaMalloc(&bstage, bytes), "cudaMalloc(b staging)");
+    if (rc) return rc;
+    cudaMemcpyAsync(bstage, b, bytes, cudaMemcpyHostToDevice, st);
+    bsrc = bstage;
+  }
+  expand_b_kernel<<<(unsigned)(((int64_t)nsys * M + 255) / 256), 256, 0, st>>>(bsrc, w->b, nshift, nsys, V); TM_COUNT();
+  mdot<double>(w->b, 0, 1, w->b, M, nsys, w->dot, nsys, w->partial, st);
+  sqrt_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->bn, nsys); TM_COUNT();
+  cudaMemsetAsync(w->x, 0, w->fb, st);
+  cudaMemcpyAsync(w->V, w->b, w->fb, cudaMemcpyDeviceToDevice, st);
+  set_rel_tol(w->rel_top, nsys, sp->tol, st);
+  int coarse_iters = 0, inner = 0, cycles = 0;
+  LevelOpsT<double> fine;
+  fine.M = M;
+  fine.A = [&](const double* xx, double* yy) { launch_dirac<double>(g, ctx->U64, ctx->C64, xx, yy, mud, nsys, st); };
+  fine.precond = [&](const double* v, double* z) { amg_cycle64(ctx, sp, nsys, mud, v, z, coarse_iters); };
+  const int64_t vs = (int64_t)(w->fb / sizeof(double));
+  std::vector<double> hrn(nsys), hbn(nsys);
+  const int max_cycles = 8 * sp->max_outer;
+  for (; cycles < max_cycles;) {
+    const CycleResult r = gmres_cycle<double>(w->top, fine, nsys, sp->restart, w->V, vs, w->Z, w->x, nullptr,
+                                              w->rel_top, 1, false, st);
+    inner += r.iters;
+    ++cycles;
+    // true residual b - D x in FP64
+    launch_dirac<double>(g, ctx->U64, ctx->C64, w->x, w->t1, mud, nsys, st);
+    axpby<double>(w->ones, 2, w->b, w->mones, 2, w->t1, M, nsys, nullptr, st);
+    mdot<double>(w->t1, 0, 1, w->t1, M, nsys, w->dot, nsys, w->partial, st);
+    sqrt_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->rn, nsys); TM_COUNT();
+    cudaMemcpyAsync(hrn.data(), w->rn, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hbn.data(), w->bn, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    bool all = true;
+    for (int n = 0; n < nsys; ++n) all &= !(hrn[n] > sp->tol * hbn[n]);
+    if (all || r.iters == 0) break;
+    cudaMemcpyAsync(w->V, w->t1, w->fb, cudaMemcpyDeviceToDevice, st);
+    restart_tol_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->bn, sp->tol, w->rel_top, nsys); TM_COUNT();
+  }
+  double* xdst = x;
+  double* xstage = nullptr;
+  const size_t xbytes = sizeof(double) * 2 * M * nsys;
+  if (!on_device) {
+    cudaMalloc(&xstage, xbytes);
+    xdst = xstage;
+  }
+  launch_unpack<double>(g, w->x, xdst, nsys, st);
+  if (!on_device) cudaMemcpyAsync(x, xstage, xbytes, cudaMemcpyDeviceToHost, st);
+  const cudaError_t le = cudaGetLastError();
+  const cudaError_t se = cudaStreamSynchronize(st);
+  cudaFree(bstage);
+  cudaFree(xstage);
+  rc = check_cuda(ctx, le, "FP64 solve kernels");
+  if (!rc) rc = check_cuda(ctx, se, "FP64 solve");
+  if (rc) return rc;
+  int all_ok = 1;
+  for (int n = 0; n < nsys; ++n) {
+    const double rel = hbn[n] > 0 ? hrn[n] / hbn[n] : 0.0;
+    const bool finite = std::isfinite(rel);
+    const int status = !finite ? TMAMG_ERR_NONFINITE : (rel <= sp->tol ? TMAMG_OK : TMAMG_NOT_CONVERGED);
+    if (status != TMAMG_OK) all_ok = 0;
+    if (stats) {
+      stats[n].status = status;
+      stats[n].outer_iters = cycles;
+      stats[n].inner_iters = inner;
+      stats[n].coarse_iters = coarse_iters;
+      stats[n].true_rel_res = finite ? rel : NAN;
+    }
+  }
+  return all_ok ? TMAMG_OK : TMAMG_NOT_CONVERGED;
+}
+
 int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int nshift, double* x, int on_device,
              const tmamg_solve_params* sp, tmamg_system_stats* stats) {
   cudaStream_t st = ctx->stream;
@@ -536,7 +770,8 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   if (sp->restart < 1 || sp->restart > 64 || sp->coarse_restart < 1 || sp->coarse_restart > 128 ||
       sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: bad parameters");
-  if (sp->precision != 32) return set_err(ctx, TMAMG_ERR_ARG, "solve: precision 64 path not available yet");
+  if (sp->precision == 64) return do_solve64(ctx, b, nrhs, mu, nshift, x, on_device, sp, stats);
+  if (sp->precision != 32) return set_err(ctx, TMAMG_ERR_ARG, "solve: precision must be 32 or 64");
   if (sp->coarse_precision != 0 && sp->coarse_precision != 16 && sp->coarse_precision != 32)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: coarse_precision must be 16 or 32");
   if (sp->coarse_solver < 0 || sp->coarse_solver > 2)
@@ -594,7 +829,7 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
     if (*w->h_count == 0 || outer == sp->max_outer) break;
     f64_to_f32(w->r64, w->scale, w->V, M, nsys, st);
     cudaMemsetAsync(w->e32, 0, w->fb32, st);
-    gmres_cycle(w->top, fine, nsys, sp->restart, w->V, vstride, w->Z, w->e32, w->mask, w->rel_top, 1, false, st);
+    gmres_cycle<float>(w->top, fine, nsys, sp->restart, w->V, vstride, w->Z, w->e32, w->mask, w->rel_top, 1, false, st);
     add_iters_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->top.kconv, w->mask, w->inner_it, nsys); TM_COUNT();
     f32_axpy_f64(w->rn, w->e32, w->x64, M, nsys, w->mask, st);
     launch_dirac<double>(g, ctx->U64, ctx->C64, w->x64, w->t64, ctx->mu_dev, nsys, st);
@@ -854,7 +1089,7 @@ static void solve32(SolveCtx& S, const float* r, float* e, double tol, int cycle
   for (int c = 0; c < cycles; ++c) {
     launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, e, w->V, S.mu, nsys, st);
     axpby<float>(w->ones, 2, r, w->mones, 2, w->V, M, nsys, nullptr, st);  // V0 = r - D e
-    gmres_cycle(w->top, fine, nsys, S.sp->restart, w->V, vstride, w->Z, e, nullptr, w->rel_top, 1, false, st);
+    gmres_cycle<float>(w->top, fine, nsys, S.sp->restart, w->V, vstride, w->Z, e, nullptr, w->rel_top, 1, false, st);
   }
 }
 

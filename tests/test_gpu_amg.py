@@ -203,6 +203,29 @@ def test_solve_multi_rhs_multi_shift(coarse_solver, coarse_precision):
             assert stats[r * 3 + k].status == 0
 
 
+@pytest.mark.parametrize("L,agg,sap_block,nrhs,mus", [((8, 4, 4, 8), (4, 2, 2, 4), (2, 2, 2, 2), 1, [0.01]),
+                                                        ((8, 4, 4, 8), (4, 2, 2, 4), (2, 2, 2, 2), 2, [0.001, 0.3]),
+                                                        ((8, 8, 8, 8), (4, 4, 4, 4), (4, 4, 4, 4), 1, [0.01])])
+def test_solve_plain_fp64(L, agg, sap_block, nrhs, mus):
+    # the plain FP64 comparator (precision 64: FGMRES, AMG cycle, SAP, coarse GMRES all in FP64)
+    # reaches the same 1e-10 true residual, checked by the oracle operator; the last case uses
+    # 4^4 SAP blocks (the block solver's largest shared-memory footprint)
+    U = synth.gauge_field(L, 0.3, seed=3)
+    kappa = 0.126
+    b = synth.gaussian_spinors(L, nrhs, seed=5)
+    rc, stats, x = _solve(L, U, kappa, 1.0, b, mus,
+                          dict(agg=agg, nv=12, sap_block=sap_block, setup_iters=4),
+                          dict(restart=10, tol=1e-10, precision=64))
+    op = dirac.Operator(U, kappa, 1.0)
+    assert rc == 0, [(s.status, s.true_rel_res) for s in stats]
+    for r in range(nrhs):
+        for k, mu in enumerate(mus):
+            res = np.linalg.norm(b[r] - op.apply(x[r, k], mu)) / np.linalg.norm(b[r])
+            assert res <= 1e-10, (r, k, res)
+            s = stats[r * len(mus) + k]
+            assert s.status == 0 and abs(s.true_rel_res - res) < 1e-11
+
+
 def test_solve_precision_lattice_persistent_vs_launches():
     # the 16^3 x 32 lattice with 4 point sources: both coarse-solver forms reach 1e-10 and
     # need a similar number of top-level iterations

@@ -38,33 +38,37 @@ __device__ __forceinline__ float2 bget(const float* v, int64_t M, int n, int64_t
 __global__ void __launch_bounds__(BG_THREADS) bgram_partial_kernel(const float* __restrict__ V, int64_t vstride, int k,
                                                                    const float* __restrict__ W, int64_t M, int nsys,
                                                                    int nshift, double2* __restrict__ part) {
+  // one warp per (i, pair) at a time, lanes over the CTA's entries (coalesced), FP32 lane sums
+  // added by a fixed-order warp reduction and kept in FP64
   const int npair = nsys * (nsys / nshift);  // (a, b-index within a's block)
   const int s = nsys / nshift;
   const int64_t per = (M + gridDim.x - 1) / gridDim.x;
   const int64_t e_lo = blockIdx.x * per;
   const int64_t e_hi = e_lo + per < M ? e_lo + per : M;
-  for (int q = threadIdx.x; q < k * npair; q += blockDim.x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = warp; q < k * npair; q += nw) {
     const int i = q / npair, pr = q % npair;
     const int a = pr / s, bi = pr % s;
     const int b = (a % nshift) + bi * nshift;
     const float* vi = V + (int64_t)i * vstride;
     double sr = 0, si = 0;
-    float fr = 0, fi = 0;
-    int cnt = 0;
-    for (int64_t e = e_lo; e < e_hi; ++e) {
-      const float2 x = bget(vi, M, a, e), y = bget(W, M, b, e);
-      fr += x.x * y.x + x.y * y.y;
-      fi += x.x * y.y - x.y * y.x;
-      if (++cnt == 64) {  // FP32 runs of 64 entries, summed in FP64
-        sr += fr;
-        si += fi;
-        fr = fi = 0;
-        cnt = 0;
+    for (int64_t e0 = e_lo; e0 < e_hi; e0 += 32 * 64) {  // FP32 runs of at most 64 entries per lane
+      float fr = 0, fi = 0;
+      const int64_t e1 = e0 + 32 * 64 < e_hi ? e0 + 32 * 64 : e_hi;
+      for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const float2 x = bget(vi, M, a, e), y = bget(W, M, b, e);
+        fr += x.x * y.x + x.y * y.y;
+        fi += x.x * y.y - x.y * y.x;
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        fr += __shfl_xor_sync(0xffffffffu, fr, o);
+        fi += __shfl_xor_sync(0xffffffffu, fi, o);
+      }
+      sr += fr;
+      si += fi;
     }
-    sr += fr;
-    si += fi;
-    part[((int64_t)blockIdx.x * k + i) * npair + pr] = make_double2(sr, si);
+    if (lane == 0) part[((int64_t)blockIdx.x * k + i) * npair + pr] = make_double2(sr, si);
   }
 }
 
@@ -95,19 +99,21 @@ __global__ void baxpy_kernel(const float* __restrict__ V, int64_t vstride, int k
     const int b = tile * 2 + l;
     if (b >= nsys) continue;
     const int kb = b % nshift, bi = b / nshift;
-    double ar = 0, ai = 0;
+    // FP32 arithmetic on the FP32 basis (GB300's FP64 rate is 1/64 of FP32); coefficients rounded
+    float ar = 0, ai = 0;
     for (int i = 0; i < k; ++i) {
       const float* vi = V + (int64_t)i * vstride;
       for (int aj = 0; aj < s; ++aj) {
         const int a = kb + aj * nshift;
         const float2 x = bget(vi, M, a, e);
-        const double2 c = C[((int64_t)i * nsys + a) * s + bi];
-        ar += c.x * x.x - c.y * x.y;
-        ai += c.x * x.y + c.y * x.x;
+        const double2 cd = C[((int64_t)i * nsys + a) * s + bi];
+        const float cr = (float)cd.x, ci = (float)cd.y;
+        ar += cr * x.x - ci * x.y;
+        ai += cr * x.y + ci * x.x;
       }
     }
-    o[l][0] += (float)(sign * ar);
-    o[l][1] += (float)(sign * ai);
+    o[l][0] += (float)sign * ar;
+    o[l][1] += (float)sign * ai;
   }
   *reinterpret_cast<float4*>(W + (((int64_t)tile * M + e) * 4)) = make_float4(o[0][0], o[1][0], o[0][1], o[1][1]);
 }

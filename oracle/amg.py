@@ -18,7 +18,11 @@ Readings where the paper is silent (listed in the design doc):
     inverse iteration v <- SAP(v) / ||SAP(v)|| at mu = mu_setup;
   * AMG cycle: e = P D_c^{-1} P^dagger r, then e += SAP(r - D e) (SAP as a
     post-smoother only); the coarse system is solved by FGMRES to a relative
-    residual (1e-1 at the bottom, the paper's tuned r_b), by block GMRES, or exactly.
+    residual (1e-1 at the bottom, the paper's tuned r_b), by block GMRES, or exactly;
+  * three levels: the level-2 test vectors are smoothed by inverse iteration with
+    a fixed number of level-1 GMRES steps; the middle level is solved by FGMRES to
+    r_m preconditioned by the level-2 correction plus a few minimal-residual steps
+    on the level-1 residual (the paper names no coarse-level smoother).
 
 Field layout used here: a level's vector is [..., T, Z, Y, X, 2, d] with the
 chirality axis (2) and d unknowns per chirality (d = 6 = 2 spins x 3 colours
@@ -322,6 +326,114 @@ class TwoLevelAMG:
 
     def solve(self, b, mu, tol=1e-10, restart=10, maxiter=500, **cycle_kw):
         """FGMRES(restart) preconditioned by one AMG cycle; one rhs, one shift."""
+        shp = b.shape
+        A = lambda v: self.op.apply(v.reshape(shp), mu).ravel()
+        M = lambda v: self.cycle(v.reshape(shp), mu, **cycle_kw).ravel()
+        x, info = krylov.fgmres(A, b.ravel(), tol=tol, restart=restart, maxiter=maxiter, M=M)
+        return x.reshape(shp), info
+
+
+# ---------------------------------------------------------------------------------------------
+# Three levels (paper Sec. 4: a three-level AMG with FGMRES at the top; the middle level is
+# solved by FGMRES to r_m, about 7e-2, the bottom to r_b, about 1e-1; Sec. 2: the construction
+# is applied recursively to the coarse lattice).
+
+def mr_smooth(level, r, mu, steps):
+    """`steps` minimal-residual steps on `level` from a zero start: with q = D rho,
+    alpha = <q, rho> / <q, q>, e += alpha rho, rho -= alpha q (each step minimises |rho - alpha q|).
+
+    Reading: the paper names no smoother for the coarse levels; the middle level's cycle uses
+    these few global MR steps as its post-smoother."""
+    e = np.zeros_like(r, dtype=np.complex128)
+    rho = np.array(r, dtype=np.complex128)
+    for _ in range(steps):
+        q = level.apply(rho, mu)
+        qq = np.vdot(q, q).real
+        if qq == 0.0:
+            break
+        alpha = np.vdot(q, rho) / qq
+        e = e + alpha * rho
+        rho = rho - alpha * q
+    return e
+
+
+def setup_coarse_test_vectors(level, W0, mu_setup, setup_iters, gmres_steps):
+    """Inverse iteration on a coarse level, w <- G(w) / |G(w)|, where G is `gmres_steps` Arnoldi
+    steps of GMRES on D_c(mu_setup) from a zero start (the level's approximate inverse; the
+    fine level uses SAP in this role). W0: [Nv, Tc, Zc, Yc, Xc, 2, d]."""
+    W = np.array(W0, dtype=np.complex128)
+    shp = W.shape[1:]
+    A = lambda v: level.apply(v.reshape(shp), mu_setup).ravel()
+    for _ in range(setup_iters):
+        for k in range(W.shape[0]):
+            x, _ = krylov.fgmres(A, W[k].ravel(), tol=0.0, restart=gmres_steps, maxiter=gmres_steps)
+            W[k] = (x / np.linalg.norm(x)).reshape(shp)
+    return W
+
+
+class ThreeLevelAMG:
+    """Fine level + two coarse levels.
+
+    Level 1 is built as in TwoLevelAMG. Level 2 aggregates the level-1 lattice (agg2) with Nv2
+    test vectors W0 on level 1 (split by the chirality of gamma5_c), smoothed by inverse iteration
+    with level-1 GMRES; D_c2 = P2^+ D_c1 P2 on its hop classes. The AMG cycle is
+        e = P1 x1,  x1 ~ D_c1^{-1} P1^+ r  by FGMRES on level 1 to mid_tol, preconditioned by
+            z = P2 x2 with x2 ~ D_c2^{-1} P2^+ v (GMRES to coarse_tol), then z += MR(v - D_c1 z);
+        e += SAP(r - D e).
+    Twisted mass on both coarse levels: i (delta mu) mu gamma5_c.
+    """
+
+    def __init__(self, op: dirac.Operator, agg, V0, sap_block, agg2, W0, setup_iters=5, mu_setup=0.0,
+                 sap_cycles=2, mr_steps=3, delta_mu=1.0, setup_gmres_steps=20, mid_smooth=3):
+        self.two = TwoLevelAMG(op, agg, V0, sap_block, setup_iters, mu_setup, sap_cycles, mr_steps, delta_mu)
+        self.op = op
+        self.delta_mu = delta_mu
+        self.P1 = self.two.P
+        self.level1 = self.two.coarse
+        self.W = setup_coarse_test_vectors(self.level1, W0, mu_setup, setup_iters, setup_gmres_steps)
+        self.P2 = Prolongation(self.W, self.level1.L, agg2)
+        self.A2 = coarse_operator(self.level1, self.P2)
+        self.level2 = CoarseLevel(self.A2, self.P2.Lc, self.P2.Nv)
+        self.mid_smooth = mid_smooth
+
+    def bottom_solve(self, rc, mu_c, mode, tol, restart, maxiter):
+        shp = rc.shape
+        if mode == "exact":
+            return np.linalg.solve(self.level2.dense(mu_c), rc.ravel()).reshape(shp)
+        A = lambda v: self.level2.apply(v.reshape(shp), mu_c).ravel()
+        x, _ = krylov.fgmres(A, rc.ravel(), tol=tol, restart=restart, maxiter=maxiter)
+        return x.reshape(shp)
+
+    def mid_cycle(self, v, mu_c, coarse_mode="fgmres", coarse_tol=1e-1, coarse_restart=20, coarse_maxiter=200):
+        """Preconditioner of the middle FGMRES: level-2 correction, then MR post-smoothing."""
+        x2 = self.bottom_solve(self.P2.restrict(v), mu_c, coarse_mode, coarse_tol, coarse_restart, coarse_maxiter)
+        z = self.P2.prolong(x2)
+        if self.mid_smooth:
+            z = z + mr_smooth(self.level1, v - self.level1.apply(z, mu_c), mu_c, self.mid_smooth)
+        return z
+
+    def mid_solve(self, rc, mu_c, mid_mode="fgmres", mid_tol=7e-2, mid_restart=10, mid_maxiter=50, **bottom):
+        shp = rc.shape
+        if mid_mode == "exact":
+            return np.linalg.solve(self.level1.dense(mu_c), rc.ravel()).reshape(shp)
+        A = lambda v: self.level1.apply(v.reshape(shp), mu_c).ravel()
+        M = lambda v: self.mid_cycle(v.reshape(shp), mu_c, **bottom).ravel()
+        x, _ = krylov.fgmres(A, rc.ravel(), tol=mid_tol, restart=mid_restart, maxiter=mid_maxiter, M=M)
+        return x.reshape(shp)
+
+    def cycle(self, r, mu, smooth=True, **kw):
+        """One AMG cycle on a single fine vector r [T, Z, Y, X, 4, 3] at twisted mass mu."""
+        rc = self.P1.restrict(FineLevel.to_chi(r))
+        ec = self.mid_solve(rc, self.delta_mu * mu, **kw)
+        e = FineLevel.to_spin(self.P1.prolong(ec))
+        if smooth:
+            r2 = r - self.op.apply(e, mu)
+            two = self.two
+            e = e + sap_mod.sap(self.op, r2, mu, two.sap_block, two.sap_cycles, two.mr_steps, bop=two.bop)
+        return e
+
+    def solve(self, b, mu, tol=1e-10, restart=10, maxiter=500, **cycle_kw):
+        """FGMRES(restart) preconditioned by one three-level AMG cycle; one rhs, one shift."""
         shp = b.shape
         A = lambda v: self.op.apply(v.reshape(shp), mu).ravel()
         M = lambda v: self.cycle(v.reshape(shp), mu, **cycle_kw).ravel()

@@ -127,6 +127,12 @@ def gaussian_spinors(L, nvec: int, seed: int, stream: int = 202) -> np.ndarray:
     return complex_normal(seed, stream, (nvec,) + lattice_shape(L) + (4, 3), var=1.0)
 
 
+def gaussian_coarse(Lc, nvec: int, d: int, seed: int, stream: int = 206) -> np.ndarray:
+    """nvec complex Gaussian vectors of a coarse level with d unknowns per chirality,
+    complex128 [nvec, Ltc, Lzc, Lyc, Lxc, 2, d]."""
+    return complex_normal(seed, stream, (nvec,) + lattice_shape(Lc) + (2, d), var=1.0)
+
+
 def z2_spinors(L, nvec: int, seed: int, stream: int = 204) -> np.ndarray:
     """Complex Z2 noise: each component (+-1 +- i)/sqrt(2), signs from the generator."""
     shape = (nvec,) + lattice_shape(L) + (4, 3)

@@ -55,15 +55,18 @@ typedef enum {
 
 /* Multigrid setup parameters (paper Sec. 2; defaults by tmamg_default_setup_params). */
 typedef struct {
-  int levels;          /* 2 (fine + one coarse level); 3 adds a second coarse level */
+  int levels;          /* 2 (fine + one coarse level) or 3 (a second coarse level on the lattice of level 1) */
   int agg[2][4];       /* aggregate extents (x, y, z, t) for the level-1 and level-2 coarsening */
   int nv[2];           /* test vectors per coarsening; coarse site carries 2*nv unknowns (chirality split) */
   int sap_block[4];    /* SAP block extents on the fine level; block counts per dimension must be even */
   int sap_cycles;      /* red+black sweeps per SAP application */
   int sap_mr_steps;    /* minimal-residual steps per block solve */
-  int setup_iters;     /* inverse-iteration steps v <- SAP(v)/|SAP(v)| on the test vectors */
+  int setup_iters;     /* inverse-iteration steps v <- SAP(v)/|SAP(v)| on the test vectors (on level 1
+                          for levels == 3: w <- G(w)/|G(w)|, G = setup_gmres_steps steps of level-1 GMRES) */
   double mu_setup;     /* twisted mass used during setup */
   uint64_t seed;       /* start vectors when none are passed (counter-based splitmix64 + Box-Muller) */
+  int setup_gmres_steps; /* levels == 3: Arnoldi steps (<= 64) of the level-1 GMRES that serves as the approximate
+                            inverse in the inverse iteration of the level-2 test vectors */
 } tmamg_setup_params;
 
 /* Solve parameters (paper Sec. 4: FGMRES at the top, goal residual 1e-10; tuned coarse residual 1e-1). */
@@ -87,6 +90,14 @@ typedef struct {
   int coarse_precision; /* coarse stencil: 16 (default; 0 means 16) FP16 operator and FP16-staged vectors on
                            the tensor cores (tcgen05) with FP32 accumulation, per-system scaling that keeps
                            the FP16 range; 32: FP32 operator on the CUDA cores (reference path) */
+  /* levels == 3 (paper Sec. 4: FGMRES on the middle level to r_m, about 7e-2): the level-1 system of every
+     AMG cycle is solved by FGMRES(mid_restart) to the relative residual mid_tol (at most mid_maxiter steps),
+     preconditioned by the level-2 correction z = P2 D_c2^{-1} P2^+ v (the coarse solver above, to coarse_tol)
+     followed by mid_smooth minimal-residual steps on the level-1 residual v - D_c1 z */
+  double mid_tol;
+  int mid_restart;     /* <= 64 */
+  int mid_maxiter;
+  int mid_smooth;      /* 0 = no level-1 smoothing */
 } tmamg_solve_params;
 
 typedef struct {
@@ -139,16 +150,23 @@ int tmamg_apply(tmamg_ctx* ctx, const void* x_field, void* y_field, int nsys, co
 /* ------------------------------------------------------------------ multigrid and solve */
 
 /* Build the multigrid hierarchy (paper Sec. 2: test vectors approximating low modes, P and
- * R = P^+ on aggregates, coarse operator D_c = P^+ D P). start_vectors: device pointer to
- * nv[0] complex float fields [nv][V][4][3], or NULL to draw them from the library's
- * counter-based generator (splitmix64 + Box-Muller, seeded by p->seed). The start vectors
- * are smoothed by p->setup_iters steps of inverse iteration v <- SAP(v)/|SAP(v)| at
- * twisted mass p->mu_setup, split by chirality and orthonormalised per aggregate
- * (classical Gram-Schmidt, twice). Synchronises the stream. Only levels == 2 for now. */
+ * R = P^+ on aggregates, coarse operator D_c = P^+ D P, applied recursively for a further
+ * level). start_vectors: device pointer to nv[0] complex float fields [nv][V][4][3], or NULL
+ * to draw them from the library's counter-based generator (splitmix64 + Box-Muller, seeded by
+ * p->seed). The start vectors are smoothed by p->setup_iters steps of inverse iteration
+ * v <- SAP(v)/|SAP(v)| at twisted mass p->mu_setup, split by chirality and orthonormalised
+ * per aggregate (classical Gram-Schmidt, twice).
+ * levels == 3: the array continues with nv[1] level-1 fields, complex float [nv1][Vc1][2 nv[0]]
+ * (level-1 sites lexicographic, x fastest; coarse component chi * nv[0] + j), smoothed by
+ * p->setup_iters steps of w <- G(w)/|G(w)| with G = p->setup_gmres_steps steps of level-1
+ * GMRES at p->mu_setup, split by the chirality of gamma5_c and orthonormalised per level-2
+ * aggregate (extents agg[1], dividing the level-1 lattice); D_c2 = P2^+ D_c1 P2.
+ * Synchronises the stream. */
 int tmamg_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* start_vectors);
 
-/* As tmamg_setup, but test_vectors (device, complex float [nv][V][4][3]) are used as the
- * final test vectors without smoothing: lets a caller reproduce P from known vectors. */
+/* As tmamg_setup, but test_vectors (device, complex float [nv][V][4][3], followed for
+ * levels == 3 by the level-1 fields described above) are used as the final test vectors
+ * without smoothing: lets a caller reproduce P (and P2) from known vectors. */
 int tmamg_setup_from_vectors(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* test_vectors);
 
 /* Solve D(mu_k) x_{r,k} = b_r for every rhs r < nrhs and shift k < nshift (paper Sec. 3-4).
@@ -237,12 +255,13 @@ int tmamg_sap(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const do
 int tmamg_sap_noalloc(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const double* mu, const int block[4],
                       int cycles, int mr_steps);
 
-/* xc = P^+ r (restriction) and r = P xc (prolongation, overwrites) between the fine level and
- * coarse level 1, FP32 bundles. Require a setup. */
+/* xc = P^+ r (restriction) and r = P xc (prolongation, overwrites) between level - 1 (0 = the
+ * fine level: fine bundles) and coarse level `level` (1 or, with three levels, 2), FP32 bundles.
+ * Require a setup. */
 int tmamg_restrict(tmamg_ctx* ctx, int level, const void* fine_bundle, void* coarse_bundle, int nsys);
 int tmamg_prolong(tmamg_ctx* ctx, int level, const void* coarse_bundle, void* fine_bundle, int nsys);
 
-/* y = D_c(mu_n) x on coarse level 1 (9-point stencil of dense 2nv x 2nv blocks plus
+/* y = D_c(mu_n) x on coarse level `level` (1 or 2) (9-point stencil of dense 2nv x 2nv blocks plus
  * i mu_n gamma5_c, paper Sec. 2 and Fig. 6 caption with delta mu = 1). mu: host [nsys].
  * precision 16: FP16 stencil blocks and FP16-staged x on the tensor cores, FP32 accumulation;
  * each system's x is scaled by a power of two near 1/max|x_n| before the conversion and y is
@@ -254,12 +273,15 @@ int tmamg_prolong(tmamg_ctx* ctx, int level, const void* coarse_bundle, void* fi
 int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_bundle, int nsys, const double* mu,
                        int precision);
 
-/* xc ~ D_c(delta_mu mu_k)^{-1} rc on coarse level 1 by the coarse solver selected in p
+/* xc ~ D_c(delta_mu mu_k)^{-1} rc on the bottom coarse level (level 1 of two levels, level 2 of
+ * three) by the coarse solver selected in p
  * (p->coarse_solver: 0 persistent GMRES, 1 block GMRES per shift, 2 GMRES with one launch
  * per step; paper Sec. 4), to the relative residual p->coarse_tol per system, restart
  * p->coarse_restart, at most p->coarse_maxiter steps, zero start. Systems n = r * nshift + k
  * (r < nrhs, k < nshift); mu: host [nshift]; rc, xc: coarse bundles of nrhs * nshift
- * systems. iterations (optional): steps taken. Synchronises the stream. */
+ * systems. iterations (optional): steps taken. With three levels, level 1 is the middle level:
+ * FGMRES(p->mid_restart) to p->mid_tol preconditioned by the level-2 correction and
+ * p->mid_smooth MR steps (iterations: middle FGMRES steps). Synchronises the stream. */
 int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* xc_bundle, int nrhs, const double* mu,
                        int nshift, const tmamg_solve_params* p, int* iterations);
 

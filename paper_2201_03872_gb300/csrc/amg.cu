@@ -27,7 +27,7 @@ __device__ __forceinline__ void agg_site(int64_t a, int q, const int* Lc, const 
 }
 
 // ------------------------------------------------------------------ test vectors -> P
-// P[a][chi][j][q d + c'] = V_j[chi d + c'][site(a, q)]   (V: FP32 bundle, nv systems, ncomp = 2 d)
+// P[a][chi][j][c' asize + q] = V_j[chi d + c'][site(a, q)]   (V: FP32 bundle, nv systems, ncomp = 2 d)
 __global__ void gather_P_kernel(const float* __restrict__ Vb, float2* __restrict__ P, AggDims g, int nv, int d) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int K = g.asize * d;
@@ -516,6 +516,95 @@ void build_coarse_operator_fine(const AggDims& g, const float2* U32, const float
     scatter_A_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(R, A, g.Vc, nc, h); TM_COUNT();
   }
   (void)cd;
+}
+
+// Part h of a coarse operator (the parent level of aggregation g) applied to x, twisted mass
+// left out: h = 0 gives the self block plus every hop whose ends lie in one aggregate of g;
+// h = 1 + 2 nu (2 + 2 nu) gives the forward (backward) hop in direction nu on the sites where
+// it crosses into the next aggregate. x, y: parent bundles (ncomp = pd.nc, nsite = pd.Vc).
+__global__ void split_coarse_kernel(const float2* __restrict__ A, const float* __restrict__ x, float* __restrict__ y,
+                                    CoarseDims pd, AggDims g, int h) {
+  const int nc = pd.nc;
+  const int64_t Vc = pd.Vc;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int tile = blockIdx.y;
+  if (t >= Vc * nc) return;
+  const int i = (int)(t % nc);
+  const int64_t a = t / nc;
+  int c[4];
+  site_coords(a, pd.L, c);
+  const float* xt = x + (int64_t)tile * nc * Vc * 2 * T2;
+  float4 acc = make_float4(0, 0, 0, 0);
+  for (int hh = 0; hh < 9; ++hh) {
+    int64_t nb = a;
+    if (hh > 0) {
+      const int nu = (hh - 1) / 2;
+      const bool fwd = ((hh - 1) & 1) == 0;
+      const int r = c[nu] % g.agg[nu];
+      const bool cross = g.Lc[nu] > 1 && (fwd ? r == g.agg[nu] - 1 : r == 0);
+      if (cross ? hh != h : h != 0) continue;
+      int cc[4] = {c[0], c[1], c[2], c[3]};
+      cc[nu] = (cc[nu] + (fwd ? 1 : -1) + pd.L[nu]) % pd.L[nu];
+      nb = site_index(cc, pd.L);
+    } else if (h != 0) {
+      continue;
+    }
+    const float2* Ah = A + (((int64_t)hh * Vc + a) * nc) * nc + i;
+    const float* xn = xt + nb * 2 * T2;
+    for (int j = 0; j < nc; ++j) {
+      const float2 m = Ah[(int64_t)j * nc];
+      const float4 v = *reinterpret_cast<const float4*>(xn + (int64_t)j * Vc * 2 * T2);
+      acc.x += m.x * v.x - m.y * v.z;
+      acc.y += m.x * v.y - m.y * v.w;
+      acc.z += m.x * v.z + m.y * v.x;
+      acc.w += m.x * v.w + m.y * v.y;
+    }
+  }
+  *reinterpret_cast<float4*>(y + ((int64_t)(tile * nc + i) * Vc + a) * 2 * T2) = acc;
+}
+
+void build_coarse_operator_coarse(const AggDims& g, const CoarseDims& pd, const float2* Ap, const float2* P,
+                                  float2* A, int nv, float* W, float* Y, float* R, cudaStream_t st) {
+  const int d = pd.nc / 2;
+  const int nc = 2 * nv;
+  const int nt = nc / T2;
+  const int64_t per_tile = (int64_t)pd.nc * g.Vp;
+  columns_kernel<<<(unsigned)((per_tile * nt + 255) / 256), 256, 0, st>>>(P, W, g, nv, d); TM_COUNT();
+  for (int h = 0; h < 9; ++h) {
+    split_coarse_kernel<<<dim3((unsigned)((per_tile + 127) / 128), nt), 128, 0, st>>>(Ap, W, Y, pd, g, h); TM_COUNT();
+    restrict_vec(g, P, Y, R, nv, d, nc, st);
+    const int64_t tot = g.Vc * nc * (int64_t)nc;
+    scatter_A_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(R, A, g.Vc, nc, h); TM_COUNT();
+  }
+}
+
+// field [nsys][Vc][nc] complex float -> coarse bundle [ntile][nc][Vc][2][2] (padding lane zero)
+__global__ void pack_coarse_kernel(const float2* __restrict__ f, float* __restrict__ b, int nsys, int nc,
+                                   int64_t Vc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int nt = (nsys + T2 - 1) / T2;
+  if (t >= (int64_t)nt * nc * Vc) return;
+  const int64_t s = t % Vc;
+  const int comp = (int)((t / Vc) % nc);
+  const int tile = (int)(t / (Vc * nc));
+  float o[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int l = 0; l < T2; ++l) {
+    const int n = tile * T2 + l;
+    if (n < nsys) {
+      const float2 v = f[((int64_t)n * Vc + s) * nc + comp];
+      o[l] = v.x;
+      o[T2 + l] = v.y;
+    }
+  }
+  *reinterpret_cast<float4*>(b + t * 4) = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+void pack_coarse(const float* field, float* bundle, int nsys, int nc, int64_t Vc, cudaStream_t st) {
+  const int64_t total = (int64_t)ntiles(nsys, T2) * nc * Vc;
+  pack_coarse_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(reinterpret_cast<const float2*>(field), bundle,
+                                                                     nsys, nc, Vc);
+  TM_COUNT();
 }
 
 }  // namespace tmamg

@@ -35,6 +35,13 @@ void coarse_apply(const CoarseDims& cd, const float2* A, const float* x, float* 
 void build_coarse_operator_fine(const AggDims& g, const float2* U32, const float* C32, const float2* P, float2* A,
                                 int nv, int bc_t, float* W, float* Y, float* R, cudaStream_t st);
 
+// A = P^+ D_p P for a coarse parent D_p (stencil Ap on pd, d = pd.nc / 2 unknowns per chirality):
+// W, Y: parent bundles of 2 nv systems; R: coarse bundle of 2 nv systems
+void build_coarse_operator_coarse(const AggDims& g, const CoarseDims& pd, const float2* Ap, const float2* P,
+                                  float2* A, int nv, float* W, float* Y, float* R, cudaStream_t st);
+// coarse field [nsys][Vc][nc] (complex float) -> FP32 coarse bundle
+void pack_coarse(const float* field, float* bundle, int nsys, int nc, int64_t Vc, cudaStream_t st);
+
 // plain FP64 forms (amg64.cu) for the FP64 comparator solver: FP64 bundles, one system per tile;
 // P64 / A64 are the FP32 P and coarse blocks widened to FP64 (widen_f2)
 void widen_f2(const float2* in, double2* out, int64_t n, cudaStream_t st);

@@ -74,6 +74,7 @@ void tmamg_default_setup_params(tmamg_setup_params* p) {
   p->setup_iters = 5;
   p->mu_setup = 0.0;
   p->seed = 1;
+  p->setup_gmres_steps = 20;
 }
 
 void tmamg_default_solve_params(tmamg_solve_params* p) {
@@ -91,6 +92,10 @@ void tmamg_default_solve_params(tmamg_solve_params* p) {
   p->use_nn = 0;
   p->poll = 4;
   p->coarse_precision = 16;
+  p->mid_tol = 7e-2;
+  p->mid_restart = 10;
+  p->mid_maxiter = 50;
+  p->mid_smooth = 3;
 }
 
 int tmamg_create(const int L[4], int bc_t, void* cuda_stream, tmamg_ctx** out) {

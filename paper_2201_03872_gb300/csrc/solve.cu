@@ -39,6 +39,15 @@ struct Workspace {
   CoarseGmres cg;
   BlockGmres bg;
   float* tc = nullptr;  // one more coarse bundle
+  // middle level (coarse level 1 of a three-level hierarchy); the coarse buffers above then
+  // belong to the bottom level 2
+  int mm = 0;
+  size_t mb32 = 0;                                // bytes of one level-1 bundle
+  float *Vm = nullptr, *Zm = nullptr;             // mm + 1 and mm level-1 bundles
+  float *xm = nullptr, *rm = nullptr, *sm1 = nullptr, *sm2 = nullptr;
+  GmresState mid;
+  double *rel_mid = nullptr, *beta0m = nullptr;
+  double2 *mra = nullptr, *mrd = nullptr;         // MR coefficients [2 ns]: alpha, -alpha; dots [2 ns]
   double *rel_top = nullptr, *rel_coarse = nullptr, *rn = nullptr, *bn = nullptr, *scale = nullptr;
   double *beta0 = nullptr, *tmpd = nullptr;
   double2 *ones = nullptr, *mones = nullptr, *dot = nullptr, *partial64 = nullptr;
@@ -49,16 +58,22 @@ struct Workspace {
   std::vector<void*> extra;
 };
 
+// ctx->levels holds the coarse levels: two of them make a three-level hierarchy whose first
+// coarse level is the middle level
+static bool has_middle(const tmamg_ctx* ctx) { return ctx->levels.size() == 2; }
+
 static void ws_free(Workspace* w) {
   if (!w) return;
   void* ptrs[] = {w->V, w->Z, w->t1, w->t2, w->t3, w->e32, w->x64, w->r64, w->b64, w->t64, w->Vc, w->xc, w->rc,
                   w->rel_top, w->rel_coarse, w->rn, w->bn, w->scale, w->beta0, w->tmpd, w->ones, w->mones, w->dot,
-                  w->partial64, w->mask, w->flags, w->count, w->outer_it, w->inner_it};
+                  w->partial64, w->mask, w->flags, w->count, w->outer_it, w->inner_it, w->Vm, w->Zm, w->xm,
+                  w->rm, w->sm1, w->sm2, w->rel_mid, w->beta0m, w->mra, w->mrd};
   for (void* p : ptrs) cudaFree(p);
   for (void* p : w->extra) cudaFree(p);
   if (w->h_count) cudaFreeHost(w->h_count);
   w->top.release();
   w->coarse.release();
+  w->mid.release();
   w->cg.release();
   w->bg.release();
   cudaFree(w->tc);
@@ -105,23 +120,33 @@ __global__ void fill_c_kernel(double2* a, int n, double re) {
   if (i < n) a[i] = make_double2(re, 0);
 }
 
-static int ensure_ws(tmamg_ctx* ctx, int nsys, int m, int mc) {
+// solver state for nsys systems and the restart lengths of p (top, bottom and, with three
+// levels, middle); grown on demand, never shrunk
+static int ensure_ws(tmamg_ctx* ctx, int nsys, const tmamg_solve_params& p) {
   if (!ctx->ws) ctx->ws = new Workspace();
   Workspace* w = ctx->ws;
-  if (nsys <= w->nsys && m <= w->m && mc <= w->mc) return 0;
+  const bool three = has_middle(ctx);
+  const int m = p.restart, mc = p.coarse_restart, mmid = three ? p.mid_restart : 0;
+  if (nsys <= w->nsys && m <= w->m && mc <= w->mc && mmid <= w->mm) return 0;
   int ns = nsys > w->nsys ? nsys : w->nsys;
   int mm = m > w->m ? m : w->m;
   int mcc = mc > w->mc ? mc : w->mc;
+  int mmm = mmid > w->mm ? mmid : w->mm;
   ws_free(w);
   w->nsys = ns;
   w->m = mm;
   w->mc = mcc;
+  w->mm = mmm;
   const int64_t V = ctx->g.V;
   w->fb32 = (size_t)ntiles(ns, 2) * 12 * V * 4 * sizeof(float);
   w->fb64 = (size_t)ns * 12 * V * 2 * sizeof(double);
-  int64_t Vc = ctx->levels.empty() ? 1 : ctx->levels[0].Vc;
-  int nc = ctx->levels.empty() ? 2 : 2 * ctx->levels[0].nv;
+  // the coarse buffers serve the bottom level
+  int64_t Vc = ctx->levels.empty() ? 1 : ctx->levels.back().Vc;
+  int nc = ctx->levels.empty() ? 2 : 2 * ctx->levels.back().nv;
   w->cb32 = (size_t)ntiles(ns, 2) * nc * Vc * 4 * sizeof(float);
+  const int64_t Vm = three ? ctx->levels[0].Vc : 0;
+  const int ncm = three ? 2 * ctx->levels[0].nv : 0;
+  w->mb32 = (size_t)ntiles(ns, 2) * ncm * Vm * 4 * sizeof(float);
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t b) {
     if (e == cudaSuccess) e = cudaMalloc(p, b);
@@ -158,6 +183,18 @@ static int ensure_ws(tmamg_ctx* ctx, int nsys, int m, int mc) {
   A((void**)&w->count, sizeof(int));
   A((void**)&w->outer_it, sizeof(int) * ns);
   A((void**)&w->inner_it, sizeof(int) * ns);
+  if (three) {
+    A((void**)&w->Vm, w->mb32 * (mmm + 1));
+    A((void**)&w->Zm, w->mb32 * mmm);
+    A((void**)&w->xm, w->mb32);
+    A((void**)&w->rm, w->mb32);
+    A((void**)&w->sm1, w->mb32);
+    A((void**)&w->sm2, w->mb32);
+    A((void**)&w->rel_mid, d);
+    A((void**)&w->beta0m, d);
+    A((void**)&w->mra, sizeof(double2) * 2 * ns);
+    A((void**)&w->mrd, sizeof(double2) * 2 * ns);
+  }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&w->h_count, sizeof(int));
   if (e != cudaSuccess) {
     ws_free(w);
@@ -165,6 +202,8 @@ static int ensure_ws(tmamg_ctx* ctx, int nsys, int m, int mc) {
   }
   if (w->top.alloc(mm, ns, partial_elems(12 * V, ns, mm + 1, 2))) return set_err(ctx, TMAMG_ERR_OOM, "gmres state");
   if (w->coarse.alloc(mcc, ns, partial_elems((int64_t)nc * Vc, ns, mcc + 1, 2)))
+    return set_err(ctx, TMAMG_ERR_OOM, "gmres state");
+  if (three && w->mid.alloc(mmm, ns, partial_elems((int64_t)ncm * Vm, ns, mmm + 1, 2)))
     return set_err(ctx, TMAMG_ERR_OOM, "gmres state");
   // the grid for one tile is the largest any system count uses
   if (w->cg.alloc(mcc, ns, coarse_gmres_grid(1), w->cb32, cm_x16_bytes(Vc, nc, ns)))
@@ -190,6 +229,22 @@ static AggDims agg_dims(const Geom& g, const int agg[4]) {
   return a;
 }
 
+// aggregation of a coarse level's lattice (the parent of a further level)
+static AggDims agg_dims_coarse(const CoarseLevel& parent, const int agg[4]) {
+  AggDims a;
+  a.asize = 1;
+  a.Vc = 1;
+  for (int k = 0; k < 4; ++k) {
+    a.L[k] = parent.Lc[k];
+    a.agg[k] = agg[k];
+    a.Lc[k] = parent.Lc[k] / agg[k];
+    a.asize *= agg[k];
+    a.Vc *= a.Lc[k];
+  }
+  a.Vp = parent.Vc;
+  return a;
+}
+
 static CoarseDims coarse_dims(const CoarseLevel& l) {
   CoarseDims c;
   for (int k = 0; k < 4; ++k) c.L[k] = l.Lc[k];
@@ -206,10 +261,9 @@ static uint64_t splitmix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-static void start_vectors(uint64_t seed, int nv, int64_t V, std::vector<float>& out) {
-  size_t n = (size_t)nv * V * 12;  // complex numbers
-  out.resize(2 * n);
-  uint64_t key = splitmix64(seed ^ 0x5eedULL);
+static void start_vectors(uint64_t seed, uint64_t stream, size_t n, std::vector<float>& out) {
+  out.resize(2 * n);  // n complex numbers
+  uint64_t key = splitmix64(seed ^ stream);
   for (size_t i = 0; i < n; ++i) {
     uint64_t a = splitmix64(key + 2 * i), b = splitmix64(key + 2 * i + 1);
     double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740992.0);
@@ -228,11 +282,125 @@ __global__ void inv_sqrt_kernel(const double2* dot, double2* sc, int n) {
   }
 }
 
+// Level 2 on the lattice of level 1 (paper Sec. 2: the construction applied recursively): nv[1]
+// test vectors on level 1, given (vec2_dev: complex float [nv2][Vc1][2 nv1], coarse component
+// chi nv1 + j) or drawn from the generator, smoothed (if smooth) by setup_iters steps of inverse
+// iteration w <- G(w) / |G(w)|, G = setup_gmres_steps steps of level-1 GMRES at mu_setup; then
+// P2 (orthonormal per aggregate and chirality of gamma5_c) and D_c2 = P2^+ D_c1 P2.
+static int setup_level2(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec2_dev, bool smooth) {
+  cudaStream_t st = ctx->stream;
+  const CoarseLevel& L1 = ctx->levels[0];
+  const CoarseDims cd1 = coarse_dims(L1);
+  const int nv1 = L1.nv, nc1 = 2 * nv1, nv2 = p->nv[1], nc2 = 2 * nv2;
+  const AggDims ad = agg_dims_coarse(L1, p->agg[1]);
+  CoarseLevel lv;
+  for (int k = 0; k < 4; ++k) {
+    lv.Lc[k] = ad.Lc[k];
+    lv.agg[k] = ad.agg[k];
+  }
+  lv.Vc = ad.Vc;
+  lv.nv = nv2;
+  lv.asize = ad.asize;
+  int rc = check_cuda(ctx, cudaMalloc(&lv.P, sizeof(float2) * (size_t)ad.Vc * 2 * nv2 * ad.asize * nv1), "cudaMalloc(P2)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&lv.A, sizeof(float2) * 9 * (size_t)ad.Vc * nc2 * nc2), "cudaMalloc(A2)");
+  if (!rc && nc2 <= CM_MAXNC)
+    rc = check_cuda(ctx, cudaMalloc(&lv.A16, (size_t)cm_site_bytes(nc2) * ad.Vc), "cudaMalloc(A2 f16)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&lv.cmax, sizeof(float) * CM_MAXSYS), "cudaMalloc(cmax)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&lv.cerr, sizeof(int)), "cudaMalloc(cerr)");
+  if (!rc) rc = check_cuda(ctx, cudaMemsetAsync(lv.cerr, 0, sizeof(int), st), "cudaMemset(cerr)");
+  if (rc) {
+    cudaFree(lv.P);
+    cudaFree(lv.A);
+    cudaFree(lv.A16);
+    cudaFree(lv.cmax);
+    cudaFree(lv.cerr);
+    return rc;
+  }
+  ctx->levels.push_back(lv);
+  CoarseLevel& L2 = ctx->levels[1];
+  const int64_t M1 = (int64_t)nc1 * L1.Vc;
+  auto b1 = [&](int n) { return (size_t)ntiles(n, 2) * nc1 * L1.Vc * 4 * sizeof(float); };
+  const int m = p->setup_gmres_steps;
+  float *Wt = nullptr, *X = nullptr, *Vk = nullptr, *Wc = nullptr, *Yc = nullptr, *Rc = nullptr, *field = nullptr;
+  double* mus = nullptr;
+  double2 *dots = nullptr, *sc = nullptr, *part = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** q, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(q, b);
+  };
+  A((void**)&Wt, b1(nv2));
+  A((void**)&Wc, b1(nc2));
+  A((void**)&Yc, b1(nc2));
+  A((void**)&Rc, (size_t)ntiles(nc2, 2) * nc2 * L2.Vc * 4 * sizeof(float));
+  const bool iterate = smooth && p->setup_iters > 0;
+  CoarseGmres cg;
+  if (iterate) {
+    A((void**)&X, b1(nv2));
+    A((void**)&Vk, b1(nv2) * (m + 1));
+    A((void**)&mus, sizeof(double) * nv2);
+    A((void**)&dots, sizeof(double2) * nv2);
+    A((void**)&sc, sizeof(double2) * nv2);
+    A((void**)&part, sizeof(double2) * partial_elems(M1, nv2, 1, 2));
+  }
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    cudaFree(Wt); cudaFree(X); cudaFree(Vk); cudaFree(Wc); cudaFree(Yc); cudaFree(Rc); cudaFree(field);
+    cudaFree(mus); cudaFree(dots); cudaFree(sc); cudaFree(part);
+    cg.release();
+  };
+  if (e == cudaSuccess && iterate &&
+      cg.alloc(m, nv2, coarse_gmres_grid(1), b1(nv2), cm_x16_bytes(L1.Vc, nc1, nv2)))
+    e = cudaErrorMemoryAllocation;
+  if (e != cudaSuccess) {
+    cleanup();
+    return check_cuda(ctx, e, "level-2 setup scratch");
+  }
+  if (!vec2_dev) {
+    std::vector<float> host;
+    start_vectors(p->seed, 0x5eed2ULL, (size_t)nv2 * L1.Vc * nc1, host);
+    e = cudaMalloc(&field, host.size() * sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(field, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host copy goes out of scope
+    if (e != cudaSuccess) {
+      cleanup();
+      return check_cuda(ctx, e, "level-2 start vectors");
+    }
+    vec2_dev = field;
+  }
+  pack_coarse(vec2_dev, Wt, nv2, nc1, L1.Vc, st);
+  if (iterate) {
+    std::vector<double> hmu(nv2, p->mu_setup);
+    cudaMemcpyAsync(mus, hmu.data(), sizeof(double) * nv2, cudaMemcpyHostToDevice, st);
+    for (int it = 0; it < p->setup_iters && !rc; ++it) {
+      int done = 0;
+      const int r = coarse_gmres_solve(cg, cd1, L1.A, L1.A16, Wt, X, Vk, (int64_t)(b1(nv2) / sizeof(float)), mus, 1.0,
+                                       nv2, m, m, 0.0, &done, st);
+      if (r == -3) rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "setup: a level-1 GMRES bounded wait timed out");
+      else if (r) rc = set_err(ctx, TMAMG_ERR_CUDA, "setup: level-1 GMRES launch failed");
+      if (rc) break;
+      mdot<float>(X, 0, 1, X, M1, nv2, dots, nv2, part, st);
+      inv_sqrt_kernel<<<(nv2 + 127) / 128, 128, 0, st>>>(dots, sc, nv2); TM_COUNT();
+      axpby<float>(sc, 2, X, nullptr, 0, Wt, M1, nv2, nullptr, st);
+    }
+  }
+  if (!rc) {
+    build_P(ad, Wt, L2.P, nv2, nv1, st);
+    build_coarse_operator_coarse(ad, cd1, L1.A, L2.P, L2.A, nv2, Wc, Yc, Rc, st);
+    if (L2.A16) pack_coarse_f16(coarse_dims(L2), L2.A, L2.A16, st);
+    rc = check_cuda(ctx, cudaGetLastError(), "level-2 setup kernels");
+  }
+  cudaError_t se = cudaStreamSynchronize(st);
+  cleanup();
+  if (!rc) rc = check_cuda(ctx, se, "level-2 setup");
+  return rc;
+}
+
 int do_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec_field_dev, bool smooth) {
   const Geom& g = ctx->g;
   cudaStream_t st = ctx->stream;
   std::string why;
-  if (p->levels != 2) return set_err(ctx, TMAMG_ERR_ARG, "setup: only levels = 2 is available");
+  if (p->levels != 2 && p->levels != 3) return set_err(ctx, TMAMG_ERR_ARG, "setup: levels must be 2 or 3");
   if (sap_check_blocks(g, p->sap_block, why)) return set_err(ctx, TMAMG_ERR_ARG, "setup: " + why);
   int nv = p->nv[0];
   if (nv < 1 || nv > 32) return set_err(ctx, TMAMG_ERR_ARG, "setup: nv must be in [1, 32]");
@@ -244,6 +412,20 @@ int do_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec_field
   if (nv > 6 * asize) return set_err(ctx, TMAMG_ERR_ARG, "setup: nv exceeds the aggregate dimension");
   if (p->sap_cycles < 1 || p->sap_mr_steps < 1 || p->setup_iters < 0)
     return set_err(ctx, TMAMG_ERR_ARG, "setup: bad SAP parameters");
+  if (p->levels == 3) {
+    const int nv2 = p->nv[1];
+    int asize2 = 1;
+    for (int k = 0; k < 4; ++k) {
+      const int lc = g.L[k] / p->agg[0][k];
+      if (p->agg[1][k] < 1 || lc % p->agg[1][k])
+        return set_err(ctx, TMAMG_ERR_ARG, "setup: level-2 aggregate must divide the level-1 lattice");
+      asize2 *= p->agg[1][k];
+    }
+    if (nv2 < 1 || nv2 > 32) return set_err(ctx, TMAMG_ERR_ARG, "setup: nv[1] must be in [1, 32]");
+    if (nv2 > nv * asize2) return set_err(ctx, TMAMG_ERR_ARG, "setup: nv[1] exceeds the level-2 aggregate dimension");
+    if (p->setup_gmres_steps < 1 || p->setup_gmres_steps > 64)
+      return set_err(ctx, TMAMG_ERR_ARG, "setup: setup_gmres_steps must be in [1, 64]");
+  }
   free_levels(ctx);
   free_workspace(ctx);
   ctx->sp = *p;
@@ -310,7 +492,7 @@ int do_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec_field
   float* field = nullptr;
   std::vector<float> host;
   if (!vec_field_dev) {
-    start_vectors(p->seed, nv, g.V, host);
+    start_vectors(p->seed, 0x5eedULL, (size_t)nv * g.V * 12, host);
     e = cudaMalloc(&field, host.size() * sizeof(float));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(field, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, st);
@@ -346,6 +528,12 @@ int do_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec_field
   if (rc) return rc;
   rc = check_cuda(ctx, se, "setup");
   if (rc) return rc;
+  if (p->levels == 3) {
+    // level-2 vectors follow the nv fine fields in a caller's array
+    const float* v2 = vec_field_dev ? vec_field_dev + (size_t)nv * g.V * 24 : nullptr;
+    rc = setup_level2(ctx, p, v2, smooth);
+    if (rc) return rc;
+  }
   ctx->have_setup = true;
   return TMAMG_OK;
 }
@@ -357,6 +545,7 @@ struct SolveCtx {
   int nsys;
   const double* mu;  // device, per system
   int coarse_iters = 0;
+  int mid_iters = 0;          // middle-level FGMRES steps (three levels)
   bool timeout = false;       // a bounded device wait gave up
   bool launch_error = false;  // a cooperative launch was refused
   int nshift = 1;             // systems n = r * nshift + k (block GMRES groups the rhs of shift k)
@@ -406,12 +595,12 @@ static bool coarse_apply_timed_out(const CoarseLevel& l, cudaStream_t st) {
   return h != 0;
 }
 
-// xc ~ D_c^{-1} rc by restarted GMRES to the relative residual coarse_tol
+// xc ~ D_c^{-1} rc on the bottom level by restarted GMRES to the relative residual coarse_tol
 static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
   tmamg_ctx* ctx = S.ctx;
   Workspace* w = ctx->ws;
   cudaStream_t st = ctx->stream;
-  CoarseLevel& L1 = ctx->levels[0];
+  CoarseLevel& L1 = ctx->levels.back();
   CoarseDims cd = coarse_dims(L1);
   if (S.sp->coarse_solver == 0) {
     // persistent kernel: the whole restarted GMRES in one cooperative launch
@@ -440,7 +629,8 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
       if (!coarse_apply_level(L1, prec, x, y, mu, dmu, nsys, st)) S.launch_error = true;
     };
     int it = 0;
-    int rc_ = block_gmres_solve(w->bg, apply, rc, xc, w->Vc, (int64_t)(w->cb32 / sizeof(float)), w->tc, w->cb32,
+    const size_t cbytes = (size_t)ntiles(nsys, 2) * M * 4 * sizeof(float);  // the caller's bundles hold nsys systems
+    int rc_ = block_gmres_solve(w->bg, apply, rc, xc, w->Vc, (int64_t)(w->cb32 / sizeof(float)), w->tc, cbytes,
                                 S.sp->coarse_restart, S.sp->coarse_maxiter, S.sp->coarse_tol, &it, st);
     if (rc_) S.launch_error = true;
     S.coarse_iters += it;
@@ -458,8 +648,9 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
   ops.A = [&, dmu, mu, nsys, prec](const float* x, float* y) {
     if (!coarse_apply_level(L1, prec, x, y, mu, dmu, nsys, st)) S.launch_error = true;
   };
-  cudaMemsetAsync(xc, 0, w->cb32, st);
-  cudaMemcpyAsync(w->Vc, rc, w->cb32, cudaMemcpyDeviceToDevice, st);
+  const size_t cbytes = (size_t)ntiles(nsys, 2) * M * 4 * sizeof(float);  // the caller's bundles hold nsys systems
+  cudaMemsetAsync(xc, 0, cbytes, st);
+  cudaMemcpyAsync(w->Vc, rc, cbytes, cudaMemcpyDeviceToDevice, st);
   set_rel_tol(w->rel_coarse, nsys, S.sp->coarse_tol, st);
   int done = 0;
   for (int cyc = 0; done < S.sp->coarse_maxiter; ++cyc) {
@@ -478,6 +669,97 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
   S.coarse_iters += done;
 }
 
+// MR coefficients from d[n] = <q, rho>, d[ns + n] = <q, q>: a[n] = d[n] / d[ns + n], a[ns + n] = -a[n]
+__global__ void mr_coef_kernel(const double2* __restrict__ d, double2* __restrict__ a, int nsys, int ns) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nsys) return;
+  const double qq = d[ns + n].x;
+  const double2 al = qq > 0 ? make_double2(d[n].x / qq, d[n].y / qq) : make_double2(0, 0);
+  a[n] = al;
+  a[ns + n] = make_double2(-al.x, -al.y);
+}
+
+// z = M_1 v, the preconditioner of the middle FGMRES: level-2 correction z = P2 D_c2^{-1} P2^+ v,
+// then mid_smooth minimal-residual steps on the level-1 residual v - D_c1 z (paper Sec. 2: the
+// two-level construction applied to the coarse lattice)
+static void mid_cycle(SolveCtx& S, const float* v, float* z) {
+  tmamg_ctx* ctx = S.ctx;
+  Workspace* w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  CoarseLevel& L1 = ctx->levels[0];
+  const CoarseLevel& L2 = ctx->levels[1];
+  const AggDims ad = agg_dims_coarse(L1, L2.agg);
+  const int nsys = S.nsys;
+  const int64_t M = (int64_t)2 * L1.nv * L1.Vc;
+  restrict_vec(ad, L2.P, v, w->rc, L2.nv, L1.nv, nsys, st);
+  coarse_solve(S, w->rc, w->xc);
+  prolong_vec(ad, L2.P, w->xc, z, L2.nv, L1.nv, nsys, 0, st);
+  const int steps = S.sp->mid_smooth;
+  if (steps < 1) return;
+  const int prec = S.sp->coarse_precision;
+  const double dmu = S.sp->delta_mu;
+  const int ns = w->nsys;
+  auto apply = [&](const float* x, float* y) {
+    if (!coarse_apply_level(L1, prec, x, y, S.mu, dmu, nsys, st)) S.launch_error = true;
+  };
+  float* rho = w->sm1;
+  float* q = w->sm2;
+  apply(z, rho);
+  axpby<float>(w->ones, 2, v, w->mones, 2, rho, M, nsys, nullptr, st);  // rho = v - D z
+  for (int k = 0; k < steps; ++k) {
+    apply(rho, q);
+    mdot<float>(q, 0, 1, rho, M, nsys, w->mrd, ns, w->mid.partial, st);
+    mdot<float>(q, 0, 1, q, M, nsys, w->mrd + ns, ns, w->mid.partial, st);
+    mr_coef_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->mrd, w->mra, nsys, ns); TM_COUNT();
+    axpby<float>(w->mra, 2, rho, nullptr, 1, z, M, nsys, nullptr, st);                      // z += alpha rho
+    if (k + 1 < steps) axpby<float>(w->mra + ns, 2, q, nullptr, 1, rho, M, nsys, nullptr, st);  // rho -= alpha q
+  }
+}
+
+// xm ~ D_c1^{-1} rm on the middle level of a three-level hierarchy: restarted FGMRES(mid_restart)
+// to the relative residual mid_tol per system (paper Sec. 4: r_m about 7e-2), preconditioned by
+// mid_cycle, restarted from the true level-1 residual
+static void mid_solve(SolveCtx& S, const float* rm, float* xm) {
+  tmamg_ctx* ctx = S.ctx;
+  Workspace* w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  CoarseLevel& L1 = ctx->levels[0];
+  const int nsys = S.nsys;
+  const int64_t M = (int64_t)2 * L1.nv * L1.Vc;
+  const int mm = S.sp->mid_restart;
+  if (!w->Vm || mm > w->mm) {  // the workspace was sized without a middle level
+    S.launch_error = true;
+    return;
+  }
+  const size_t vstride = w->mb32 / sizeof(float);
+  const int prec = S.sp->coarse_precision;
+  const double dmu = S.sp->delta_mu;
+  LevelOps ops;
+  ops.M = M;
+  ops.A = [&](const float* x, float* y) {
+    if (!coarse_apply_level(L1, prec, x, y, S.mu, dmu, nsys, st)) S.launch_error = true;
+  };
+  ops.precond = [&](const float* v, float* z) { mid_cycle(S, v, z); };
+  const size_t mbytes = (size_t)ntiles(nsys, 2) * M * 4 * sizeof(float);  // the caller's bundles hold nsys systems
+  cudaMemsetAsync(xm, 0, mbytes, st);
+  cudaMemcpyAsync(w->Vm, rm, mbytes, cudaMemcpyDeviceToDevice, st);
+  set_rel_tol(w->rel_mid, nsys, S.sp->mid_tol, st);
+  int done = 0;
+  for (int cyc = 0; done < S.sp->mid_maxiter; ++cyc) {
+    const int m = mm < S.sp->mid_maxiter - done ? mm : S.sp->mid_maxiter - done;
+    CycleResult r = gmres_cycle<float>(w->mid, ops, nsys, m, w->Vm, vstride, w->Zm, xm, nullptr, w->rel_mid, 1, false,
+                                       st);
+    done += r.iters;
+    S.mid_iters += r.iters;
+    if (cyc == 0) copy_beta_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->mid.beta, w->beta0m, nsys); TM_COUNT();
+    if (r.iters < m || done >= S.sp->mid_maxiter) break;
+    ops.A(xm, w->Vm);
+    axpby<float>(w->ones, 2, rm, w->mones, 2, w->Vm, M, nsys, nullptr, st);
+    mdot<float>(w->Vm, 0, 1, w->Vm, M, nsys, w->dot, nsys, w->mid.partial, st);
+    restart_tol_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->beta0m, S.sp->mid_tol, w->rel_mid, nsys); TM_COUNT();
+  }
+}
+
 // z = M v: coarse-grid correction then SAP post-smoothing (paper Sec. 2)
 static void amg_cycle(SolveCtx& S, const float* v, float* z) {
   tmamg_ctx* ctx = S.ctx;
@@ -488,9 +770,15 @@ static void amg_cycle(SolveCtx& S, const float* v, float* z) {
   const int nsys = S.nsys;
   const int nv = L1.nv;
   const int64_t M = 12 * ctx->g.V;
-  restrict_vec(ad, L1.P, v, w->rc, nv, 6, nsys, st);
-  coarse_solve(S, w->rc, w->xc);
-  prolong_vec(ad, L1.P, w->xc, z, nv, 6, nsys, 0, st);
+  if (has_middle(ctx)) {
+    restrict_vec(ad, L1.P, v, w->rm, nv, 6, nsys, st);
+    mid_solve(S, w->rm, w->xm);
+    prolong_vec(ad, L1.P, w->xm, z, nv, 6, nsys, 0, st);
+  } else {
+    restrict_vec(ad, L1.P, v, w->rc, nv, 6, nsys, st);
+    coarse_solve(S, w->rc, w->xc);
+    prolong_vec(ad, L1.P, w->xc, z, nv, 6, nsys, 0, st);
+  }
   launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, z, w->t1, S.mu, nsys, st);
   axpby<float>(w->ones, 2, v, w->mones, 2, w->t1, M, nsys, nullptr, st);  // t1 = v - D z
   sap_apply(ctx->g, ctx->sp.sap_block, ctx->U32, ctx->C32, w->t1, w->t2, w->t3, S.mu, nsys, ctx->sp.sap_cycles,
@@ -770,7 +1058,14 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   if (sp->restart < 1 || sp->restart > 64 || sp->coarse_restart < 1 || sp->coarse_restart > 128 ||
       sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: bad parameters");
-  if (sp->precision == 64) return do_solve64(ctx, b, nrhs, mu, nshift, x, on_device, sp, stats);
+  if (has_middle(ctx) &&
+      (sp->mid_restart < 1 || sp->mid_restart > 64 || sp->mid_maxiter < 1 || !(sp->mid_tol > 0) || sp->mid_smooth < 0))
+    return set_err(ctx, TMAMG_ERR_ARG, "solve: bad middle-level parameters");
+  if (sp->precision == 64) {
+    if (has_middle(ctx))
+      return set_err(ctx, TMAMG_ERR_ARG, "solve: the FP64 comparator (precision 64) takes a two-level hierarchy");
+    return do_solve64(ctx, b, nrhs, mu, nshift, x, on_device, sp, stats);
+  }
   if (sp->precision != 32) return set_err(ctx, TMAMG_ERR_ARG, "solve: precision must be 32 or 64");
   if (sp->coarse_precision != 0 && sp->coarse_precision != 16 && sp->coarse_precision != 32)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: coarse_precision must be 16 or 32");
@@ -778,7 +1073,7 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
     return set_err(ctx, TMAMG_ERR_ARG, "solve: coarse_solver must be 0, 1 or 2");
   if (sp->coarse_solver == 1 && nrhs > 16)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: block GMRES takes at most 16 right-hand sides per shift");
-  int rc = ensure_ws(ctx, nsys, sp->restart, sp->coarse_restart);
+  int rc = ensure_ws(ctx, nsys, *sp);
   if (rc) return rc;
   Workspace* w = ctx->ws;
   const int64_t V = g.V;
@@ -862,7 +1157,8 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   cudaFree(xstage);
   if (!rc) rc = check_cuda(ctx, se, "solve");
   if (!rc && S.launch_error) rc = set_err(ctx, TMAMG_ERR_CUDA, "solve: cooperative coarse-solver launch failed");
-  if (!rc && coarse_apply_timed_out(ctx->levels[0], st)) S.timeout = true;
+  for (const CoarseLevel& l : ctx->levels)
+    if (!rc && coarse_apply_timed_out(l, st)) S.timeout = true;
   if (!rc && S.timeout) rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "solve: a coarse-solver bounded wait timed out");
   if (rc) return rc;
   int all_ok = 1;
@@ -937,23 +1233,38 @@ int tmamg_sap(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const do
   return rc;
 }
 
+// aggregation between level - 1 (0 = fine) and coarse level `level`, and the parent's unknowns per chirality
+static AggDims transfer_dims(const tmamg_ctx* ctx, int level, int* d) {
+  const CoarseLevel& l = ctx->levels[level - 1];
+  if (level == 1) {
+    *d = 6;
+    return agg_dims(ctx->g, l.agg);
+  }
+  *d = ctx->levels[level - 2].nv;
+  return agg_dims_coarse(ctx->levels[level - 2], l.agg);
+}
+
 int tmamg_restrict(tmamg_ctx* ctx, int level, const void* fine_bundle, void* coarse_bundle, int nsys) {
   if (!ctx) return TMAMG_ERR_ARG;
   if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "restrict: no setup");
-  if (level != 1 || !fine_bundle || !coarse_bundle || nsys < 1) return set_err(ctx, TMAMG_ERR_ARG, "restrict: bad argument");
-  const CoarseLevel& l = ctx->levels[0];
-  restrict_vec(agg_dims(ctx->g, l.agg), l.P, (const float*)fine_bundle, (float*)coarse_bundle, l.nv, 6, nsys,
-               ctx->stream);
+  if (level < 1 || level > (int)ctx->levels.size() || !fine_bundle || !coarse_bundle || nsys < 1)
+    return set_err(ctx, TMAMG_ERR_ARG, "restrict: bad argument");
+  const CoarseLevel& l = ctx->levels[level - 1];
+  int d = 0;
+  const AggDims ad = transfer_dims(ctx, level, &d);
+  restrict_vec(ad, l.P, (const float*)fine_bundle, (float*)coarse_bundle, l.nv, d, nsys, ctx->stream);
   return check_cuda(ctx, cudaGetLastError(), "restrict launch");
 }
 
 int tmamg_prolong(tmamg_ctx* ctx, int level, const void* coarse_bundle, void* fine_bundle, int nsys) {
   if (!ctx) return TMAMG_ERR_ARG;
   if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "prolong: no setup");
-  if (level != 1 || !fine_bundle || !coarse_bundle || nsys < 1) return set_err(ctx, TMAMG_ERR_ARG, "prolong: bad argument");
-  const CoarseLevel& l = ctx->levels[0];
-  prolong_vec(agg_dims(ctx->g, l.agg), l.P, (const float*)coarse_bundle, (float*)fine_bundle, l.nv, 6, nsys, 0,
-              ctx->stream);
+  if (level < 1 || level > (int)ctx->levels.size() || !fine_bundle || !coarse_bundle || nsys < 1)
+    return set_err(ctx, TMAMG_ERR_ARG, "prolong: bad argument");
+  const CoarseLevel& l = ctx->levels[level - 1];
+  int d = 0;
+  const AggDims ad = transfer_dims(ctx, level, &d);
+  prolong_vec(ad, l.P, (const float*)coarse_bundle, (float*)fine_bundle, l.nv, d, nsys, 0, ctx->stream);
   return check_cuda(ctx, cudaGetLastError(), "prolong launch");
 }
 
@@ -961,14 +1272,20 @@ int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* x
                        int nshift, const tmamg_solve_params* p, int* iterations) {
   if (!ctx) return TMAMG_ERR_ARG;
   if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "coarse_solve: no setup");
-  if (level != 1 || !rc_bundle || !xc_bundle || !mu || nrhs < 1 || nshift < 1 || !p || rc_bundle == xc_bundle)
+  const int nlev = (int)ctx->levels.size();
+  if (level < 1 || level > nlev || !rc_bundle || !xc_bundle || !mu || nrhs < 1 || nshift < 1 || !p ||
+      rc_bundle == xc_bundle)
     return set_err(ctx, TMAMG_ERR_ARG, "coarse_solve: bad argument");
+  const bool middle = level < nlev;
+  if (middle && (p->mid_restart < 1 || p->mid_restart > 64 || p->mid_maxiter < 1 || !(p->mid_tol > 0) ||
+                 p->mid_smooth < 0))
+    return set_err(ctx, TMAMG_ERR_ARG, "coarse_solve: bad middle-level parameters");
   const int nsys = nrhs * nshift;
   if (nsys > 256 || p->coarse_solver < 0 || p->coarse_solver > 2 || (p->coarse_solver == 1 && nrhs > 16) ||
       p->coarse_restart < 1 || p->coarse_restart > 64 || p->coarse_maxiter < 1 ||
       (p->coarse_precision != 0 && p->coarse_precision != 16 && p->coarse_precision != 32))
     return set_err(ctx, TMAMG_ERR_ARG, "coarse_solve: bad parameters");
-  int rc = ensure_ws(ctx, nsys, p->restart, p->coarse_restart);
+  int rc = ensure_ws(ctx, nsys, *p);
   if (rc) return rc;
   std::vector<double> musys(nsys);
   for (int n = 0; n < nsys; ++n) musys[n] = mu[n % nshift];
@@ -976,12 +1293,16 @@ int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* x
   if (rc) return rc;
   SolveCtx S{ctx, p, nsys, ctx->mu_dev, 0};
   S.nshift = nshift;
-  coarse_solve(S, (const float*)rc_bundle, (float*)xc_bundle);
+  if (middle)
+    mid_solve(S, (const float*)rc_bundle, (float*)xc_bundle);
+  else
+    coarse_solve(S, (const float*)rc_bundle, (float*)xc_bundle);
   rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "coarse_solve");
   if (!rc && S.launch_error) rc = set_err(ctx, TMAMG_ERR_CUDA, "coarse_solve: launch failed");
-  if (!rc && coarse_apply_timed_out(ctx->levels[0], ctx->stream)) S.timeout = true;
+  for (const CoarseLevel& l : ctx->levels)
+    if (!rc && coarse_apply_timed_out(l, ctx->stream)) S.timeout = true;
   if (!rc && S.timeout) rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "coarse_solve: a bounded wait timed out");
-  if (iterations) *iterations = S.coarse_iters;
+  if (iterations) *iterations = middle ? S.mid_iters : S.coarse_iters;
   return rc;
 }
 
@@ -989,12 +1310,12 @@ int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_
                        int precision) {
   if (!ctx) return TMAMG_ERR_ARG;
   if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "coarse_apply: no setup");
-  if (level != 1 || !x_bundle || !y_bundle || !mu || nsys < 1 || x_bundle == y_bundle ||
-      (precision != 16 && precision != 32))
+  if (level < 1 || level > (int)ctx->levels.size() || !x_bundle || !y_bundle || !mu || nsys < 1 ||
+      x_bundle == y_bundle || (precision != 16 && precision != 32))
     return set_err(ctx, TMAMG_ERR_ARG, "coarse_apply: bad argument");
   int rc = upload_mu(ctx, mu, nsys);
   if (rc) return rc;
-  CoarseLevel& l = ctx->levels[0];
+  CoarseLevel& l = ctx->levels[level - 1];
   if (!coarse_apply_level(l, precision, (const float*)x_bundle, (float*)y_bundle, ctx->mu_dev, 1.0, nsys,
                           ctx->stream))
     return set_err(ctx, TMAMG_ERR_ARG, "coarse_apply: sizes outside the tensor-core stencil");
@@ -1165,7 +1486,7 @@ int tmamg_nn_loss_grad(tmamg_ctx* ctx, const void* r_bundle, const void* e_bundl
   if (!ctx->nn || !ctx->nn->trained) return set_err(ctx, TMAMG_ERR_STATE, "nn_loss_grad: no weights");
   tmamg_solve_params def;
   tmamg_default_solve_params(&def);
-  int rc = ensure_ws(ctx, nsys, def.restart, def.coarse_restart);
+  int rc = ensure_ws(ctx, nsys, def);
   if (rc) return rc;
   if (ctx->nn->alloc(ctx->g.V, nsys)) return set_err(ctx, TMAMG_ERR_OOM, "nn_loss_grad: buffers");
   Workspace* w = ctx->ws;
@@ -1198,7 +1519,7 @@ int tmamg_nn_train(tmamg_ctx* ctx, const tmamg_nn_params* p, tmamg_nn_report* re
   const int nsys = p->batch;
   tmamg_solve_params sp;
   tmamg_default_solve_params(&sp);
-  int rc = ensure_ws(ctx, nsys, sp.restart, sp.coarse_restart);
+  int rc = ensure_ws(ctx, nsys, sp);
   if (rc) return rc;
   if (nns.alloc(ctx->g.V, nsys)) return set_err(ctx, TMAMG_ERR_OOM, "nn_train: buffers");
   Workspace* w = ctx->ws;

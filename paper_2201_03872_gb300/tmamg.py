@@ -29,14 +29,17 @@ class TmamgError(RuntimeError):
 class SetupParams(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("agg", (ctypes.c_int * 4) * 2), ("nv", ctypes.c_int * 2),
                 ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int), ("sap_mr_steps", ctypes.c_int),
-                ("setup_iters", ctypes.c_int), ("mu_setup", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("setup_iters", ctypes.c_int), ("mu_setup", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("setup_gmres_steps", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_outer", ctypes.c_int),
                 ("coarse_tol", ctypes.c_double), ("coarse_restart", ctypes.c_int), ("coarse_maxiter", ctypes.c_int),
                 ("coarse_solver", ctypes.c_int), ("delta_mu", ctypes.c_double), ("precision", ctypes.c_int),
-                ("use_nn", ctypes.c_int), ("poll", ctypes.c_int), ("coarse_precision", ctypes.c_int)]
+                ("use_nn", ctypes.c_int), ("poll", ctypes.c_int), ("coarse_precision", ctypes.c_int),
+                ("mid_tol", ctypes.c_double), ("mid_restart", ctypes.c_int), ("mid_maxiter", ctypes.c_int),
+                ("mid_smooth", ctypes.c_int)]
 
 
 class SystemStats(ctypes.Structure):
@@ -218,7 +221,7 @@ def tmamg_apply(ctx, x_field, y_field, nsys, mu, prec):
 
 
 def setup_params(levels=2, agg=(4, 4, 4, 4), nv=24, sap_block=(4, 4, 4, 4), sap_cycles=2, sap_mr_steps=3,
-                 setup_iters=5, mu_setup=0.0, seed=1, agg2=(2, 2, 2, 2), nv2=32):
+                 setup_iters=5, mu_setup=0.0, seed=1, agg2=(2, 2, 2, 2), nv2=32, setup_gmres_steps=20):
     p = tmamg_default_setup_params()
     p.levels = levels
     for d in range(4):
@@ -232,6 +235,7 @@ def setup_params(levels=2, agg=(4, 4, 4, 4), nv=24, sap_block=(4, 4, 4, 4), sap_
     p.setup_iters = setup_iters
     p.mu_setup = mu_setup
     p.seed = seed
+    p.setup_gmres_steps = setup_gmres_steps
     return p
 
 

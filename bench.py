@@ -323,15 +323,15 @@ def run_solve(args, world, rank, local):
     variants = {}
     if args.variants:
         # same workload, other forms of the method (each timed over the same number of steps)
-        def timed(label, nr, **kw):
+        def timed(label, nr, c=ctx, **kw):
             spv = T.solve_params(**dict(solve_kw(), **kw))
-            T.tmamg_solve(ctx, bd, nr, mus, len(mus), xd, 1, spv)
+            T.tmamg_solve(c, bd, nr, mus, len(mus), xd, 1, spv)
             torch.cuda.synchronize()
             a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             okv = True
             for _ in range(args.steps):
-                rcv, stv = T.tmamg_solve(ctx, bd, nr, mus, len(mus), xd, 1, spv)
+                rcv, stv = T.tmamg_solve(c, bd, nr, mus, len(mus), xd, 1, spv)
                 okv &= rcv == 0 and all(q.status == 0 for q in stv)
             z.record(stream)
             torch.cuda.synchronize()
@@ -342,6 +342,18 @@ def run_solve(args, world, rank, local):
         # the plain comparator: one system, every vector, operator and reduction in FP64
         timed("plain_fp64_single_system", 1, precision=64)
         timed("block_gmres_coarse", nrhs, coarse_solver=1)
+        # three levels: a second coarsening (2^4 aggregates of the 4^3 x 8 level-1 lattice, Nv = 32), the middle
+        # level solved by FGMRES(10) to 7e-2 with the level-2 correction and 3 MR steps as its preconditioner
+        ctx3 = T.tmamg_create(L, -1, stream.cuda_stream)
+        T.tmamg_load_gauge(ctx3, U)
+        T.tmamg_set_operator(ctx3, kappa, wl["c_sw"])
+        t = time.time()
+        T.tmamg_setup(ctx3, T.setup_params(levels=3, agg2=(2, 2, 2, 2), nv2=32, **setup_kw()))
+        torch.cuda.synchronize()
+        setup3 = time.time() - t
+        timed("three_level", nrhs, c=ctx3)
+        variants["three_level"]["setup_seconds"] = setup3
+        T.tmamg_destroy(ctx3)
         t = time.time()
         rep = T.tmamg_nn_train(ctx, T.tmamg_default_nn_params(pairs=48, batch=12, epochs=30, lr=2e-3, mu=wl["mu"],
                                                               gate_systems=4))

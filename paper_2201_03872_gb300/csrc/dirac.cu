@@ -255,20 +255,32 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 192 : 256, sizeof(real) ==
       acc.c[k].re = make_float2(0.f, 0.f);
       acc.c[k].im = make_float2(0.f, 0.f);
     }
-#define TM_HOP2(NU)                                                                                  \
-    {                                                                                                \
-      int64_t sf = c[NU] + 1 < L[NU] ? s + strides[NU] : s - (int64_t)(L[NU] - 1) * strides[NU];    \
-      int64_t sb = c[NU] > 0 ? s - strides[NU] : s + (int64_t)(L[NU] - 1) * strides[NU];             \
-      float pf = (NU == 3 && c[3] == Lt - 1) ? (float)bc_t : 1.f;                                  \
-      float pb = (NU == 3 && c[3] == 0) ? (float)bc_t : 1.f;                                       \
-      hop2<NU, true>(acc, xt + sf * 4, V, U + (int64_t)NU * 9 * V, V, s, pf);                        \
-      hop2<NU, false>(acc, xt + sb * 4, V, U + (int64_t)NU * 9 * V, V, sb, pb);                      \
+    // software pipeline over the eight hops: the neighbour spinor of hop k + 1 is loaded before
+    // the colour multiply of hop k, so its latency overlaps that arithmetic (loading the site's own
+    // spinor for the local term the same way measured slower)
+    int64_t nb[8];
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+      nb[2 * nu] = c[nu] + 1 < L[nu] ? s + strides[nu] : s - (int64_t)(L[nu] - 1) * strides[nu];
+      nb[2 * nu + 1] = c[nu] > 0 ? s - strides[nu] : s + (int64_t)(L[nu] - 1) * strides[nu];
     }
-    TM_HOP2(0)
-    TM_HOP2(1)
-    TM_HOP2(2)
-    TM_HOP2(3)
-#undef TM_HOP2
+    const float pf = c[3] == Lt - 1 ? (float)bc_t : 1.f, pb = c[3] == 0 ? (float)bc_t : 1.f;
+    Raw2 raw;
+    CV2 h[2][3];
+    ld_raw2(raw, xt + nb[0] * 4, V);
+#define TM_PHOP(NU, FWD, K)                                                                          \
+    proj_raw2<NU, FWD>(h, raw);                                                                      \
+    if (K < 7) ld_raw2(raw, xt + nb[K < 7 ? K + 1 : 0] * 4, V);                                        \
+    mul_acc2<NU, FWD>(acc, h, U + (int64_t)NU * 9 * V, V, FWD ? s : nb[K], NU == 3 ? (FWD ? pf : pb) : 1.f);
+    TM_PHOP(0, true, 0)
+    TM_PHOP(0, false, 1)
+    TM_PHOP(1, true, 2)
+    TM_PHOP(1, false, 3)
+    TM_PHOP(2, true, 4)
+    TM_PHOP(2, false, 5)
+    TM_PHOP(3, true, 6)
+    TM_PHOP(3, false, 7)
+#undef TM_PHOP
     const int n0 = tile * 2;
     const float2 m2 = make_float2(n0 < nsys ? (float)mu[n0] : 0.f, n0 + 1 < nsys ? (float)mu[n0 + 1] : 0.f);
     local2(acc, xt + s * 4, V, C, V, s, m2);

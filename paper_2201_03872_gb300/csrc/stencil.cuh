@@ -320,6 +320,66 @@ __device__ __forceinline__ void hop2(Spinor2& acc, const float* __restrict__ xs,
   }
 }
 
+// hop2<> split in three parts so that a caller can keep the next hop's neighbour loads in flight
+// while the current hop multiplies: the raw neighbour spinor of one tile (12 entries), its spin
+// projection, and the colour multiply with accumulation.
+struct Raw2 {
+  CV2 v[12];
+};
+__device__ __forceinline__ void ld_raw2(Raw2& r, const float* __restrict__ xs, int64_t cstride) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) r.v[k] = ld2(xs + (int64_t)k * cstride * 4);
+}
+template <int NU, bool FWD>
+__device__ __forceinline__ void proj_raw2(CV2 (&h)[2][3], const Raw2& r) {
+  using P = Proj<NU, FWD>;
+#pragma unroll
+  for (int col = 0; col < 3; ++col) {
+    h[0][col] = proj2<P::c0>(r.v[0 * 3 + col], P::p0 == 0 ? r.v[2 * 3 + col] : r.v[3 * 3 + col]);
+    h[1][col] = proj2<P::c1>(r.v[1 * 3 + col], P::p1 == 0 ? r.v[2 * 3 + col] : r.v[3 * 3 + col]);
+  }
+}
+template <int NU, bool FWD>
+__device__ __forceinline__ void mul_acc2(Spinor2& acc, const CV2 (&h)[2][3], const float2* __restrict__ U, int64_t V,
+                                         int64_t ls, float phase) {
+  using P = Proj<NU, FWD>;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 w[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (FWD) {
+        w[b] = U[(int64_t)(a * 3 + b) * V + ls];
+      } else {
+        const float2 t = U[(int64_t)(b * 3 + a) * V + ls];
+        w[b] = make_float2(t.x, -t.y);
+      }
+      w[b] = make_float2(w[b].x * phase, w[b].y * phase);
+    }
+    CV2 g[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      float2 gr = mul2(f2(w[0].x), h[k][0].re);
+      float2 gi = mul2(f2(w[0].x), h[k][0].im);
+      gr = fma2(f2(-w[0].y), h[k][0].im, gr);
+      gi = fma2(f2(w[0].y), h[k][0].re, gi);
+#pragma unroll
+      for (int b = 1; b < 3; ++b) {
+        gr = fma2(f2(w[b].x), h[k][b].re, gr);
+        gr = fma2(f2(-w[b].y), h[k][b].im, gr);
+        gi = fma2(f2(w[b].x), h[k][b].im, gi);
+        gi = fma2(f2(w[b].y), h[k][b].re, gi);
+      }
+      g[k].re = gr;
+      g[k].im = gi;
+    }
+    acc2<0>(acc.c[0 * 3 + a], g[0]);
+    acc2<0>(acc.c[1 * 3 + a], g[1]);
+    acc2<P::b0>(acc.c[2 * 3 + a], P::p0 == 0 ? g[0] : g[1]);
+    acc2<P::b1>(acc.c[3 * 3 + a], P::p1 == 0 ? g[0] : g[1]);
+  }
+}
+
 // local_term<> for FP32 tiles of two systems in packed arithmetic: acc <- A_chi x_chi +
 // i s mu x_chi - 1/2 acc per chirality; mu: the two systems' twisted masses
 __device__ __forceinline__ void local2(Spinor2& acc, const float* __restrict__ x0, int64_t cstride,

@@ -261,7 +261,8 @@ static uint64_t splitmix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-static void start_vectors(uint64_t seed, uint64_t stream, size_t n, std::vector<float>& out) {
+// n complex Gaussian numbers (interleaved re, im) of the stream (seed, stream)
+static void host_gaussian(uint64_t seed, uint64_t stream, size_t n, std::vector<float>& out) {
   out.resize(2 * n);  // n complex numbers
   uint64_t key = splitmix64(seed ^ stream);
   for (size_t i = 0; i < n; ++i) {
@@ -357,7 +358,7 @@ static int setup_level2(tmamg_ctx* ctx, const tmamg_setup_params* p, const float
   }
   if (!vec2_dev) {
     std::vector<float> host;
-    start_vectors(p->seed, 0x5eed2ULL, (size_t)nv2 * L1.Vc * nc1, host);
+    host_gaussian(p->seed, 0x5eed2ULL, (size_t)nv2 * L1.Vc * nc1, host);
     e = cudaMalloc(&field, host.size() * sizeof(float));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(field, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, st);
@@ -492,7 +493,7 @@ int do_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec_field
   float* field = nullptr;
   std::vector<float> host;
   if (!vec_field_dev) {
-    start_vectors(p->seed, 0x5eedULL, (size_t)nv * g.V * 12, host);
+    host_gaussian(p->seed, 0x5eedULL, (size_t)nv * g.V * 12, host);
     e = cudaMalloc(&field, host.size() * sizeof(float));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(field, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, st);
@@ -1365,7 +1366,7 @@ static int nn_upload(tmamg_ctx* ctx, const double* W) {
 // gaussian FP32 fine bundle of nsys systems from the library's counter-based generator
 static int random_bundle(tmamg_ctx* ctx, uint64_t seed, int nsys, float* bundle) {
   std::vector<float> host;
-  start_vectors(seed, nsys, ctx->g.V, host);
+  host_gaussian(seed, 0x5eedULL, (size_t)nsys * ctx->g.V * 12, host);
   float* field = nullptr;
   int rc = check_cuda(ctx, cudaMalloc(&field, host.size() * sizeof(float)), "cudaMalloc(random field)");
   if (rc) return rc;
@@ -1441,7 +1442,7 @@ int tmamg_nn_init(tmamg_ctx* ctx, uint64_t seed) {
   const int n = nn_weight_offset(3);
   std::vector<double> W(2 * n, 0.0);
   std::vector<float> noise;
-  start_vectors(seed, 1, (n + 11) / 12, noise);
+  host_gaussian(seed, 0x5eedULL, (size_t)12 * ((n + 11) / 12), noise);
   const int chs[4] = {4, 8, 8, 4};
   for (int l = 0; l < 3; ++l) {
     const int cin = chs[l], cout = chs[l + 1], off = nn_weight_offset(l);
@@ -1575,7 +1576,7 @@ int tmamg_nn_train(tmamg_ctx* ctx, const tmamg_nn_params* p, tmamg_nn_report* re
   // ---- the gate: the same solve with and without the learned step (plain SAP is the judge)
   const int ng_sys = p->gate_systems;
   std::vector<float> hb;
-  start_vectors(p->seed + 99991ULL, ng_sys, ctx->g.V, hb);
+  host_gaussian(p->seed + 99991ULL, 0x5eedULL, (size_t)ng_sys * ctx->g.V * 12, hb);
   std::vector<double> b64(hb.begin(), hb.end());
   std::vector<double> x64(b64.size());
   std::vector<tmamg_system_stats> stats(ng_sys);

@@ -290,6 +290,7 @@ __global__ void inv_sqrt_kernel(const double2* dot, double2* sc, int n) {
 // P2 (orthonormal per aggregate and chirality of gamma5_c) and D_c2 = P2^+ D_c1 P2.
 static int setup_level2(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec2_dev, bool smooth) {
   cudaStream_t st = ctx->stream;
+  ctx->levels.reserve(2);  // the push_back below must not move level 1 (L1 refers to it)
   const CoarseLevel& L1 = ctx->levels[0];
   const CoarseDims cd1 = coarse_dims(L1);
   const int nv1 = L1.nv, nc1 = 2 * nv1, nv2 = p->nv[1], nc2 = 2 * nv2;

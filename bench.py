@@ -141,13 +141,21 @@ def dist_init():
 
 
 def max_over_ranks(v, world):
+    """The largest v over the ranks (NCCL on GPUs, or a gloo group on the host)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, max_ms):
+    """Weak scaling: every rank processes units_per_rank units; the job's rate is all ranks' units
+    over the slowest rank's time."""
+    return units_per_rank * world / (max_ms * 1e-3)
 
 
 def barrier(world):
@@ -201,7 +209,7 @@ def run_dirac(args, world, rank, local):
     kern_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     total_ms = max_over_ranks(total_ms, world)
     bytes_per_apply = dirac_bytes_per_site(nsys, 32) * V
-    gbs = bytes_per_apply * args.steps * world / (total_ms * 1e-3) / 1e9
+    gbs = whole_job_rate(bytes_per_apply * args.steps, world, total_ms) / 1e9
     # end to end through the public API with host buffers: H2D of x, apply, D2H of y
     xh = torch.from_numpy(x.view(np.float32).copy()).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
@@ -229,7 +237,7 @@ def run_dirac(args, world, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": dirac_traffic(), "peak_source": peak_src,
                      "kernel": "dirac_kernel<float,2>", "algorithmic_bytes_per_launch": bytes_per_apply},
-        "e2e": {"value": bytes_per_apply * args.steps * world / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+        "e2e": {"value": whole_job_rate(bytes_per_apply * args.steps, world, e2e_ms) / 1e9, "unit": "GB/s",
                 "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(x.nbytes)},
         "gpu_launches": args.steps,
         "clocks": clk.result,
@@ -309,7 +317,7 @@ def run_solve(args, world, rank, local):
         clk.mark(h0, time.time())
     launches = T.tmamg_kernel_launches() - launches0
     total_ms = max_over_ranks(t0.elapsed_time(t1), world)
-    solves_per_s = nsys * args.steps * world / (total_ms * 1e-3)
+    solves_per_s = whole_job_rate(nsys * args.steps, world, total_ms)
     # end to end through the public API with host buffers: b copied in, x copied out, every step
     bh = np.ascontiguousarray(b)
     xh = np.zeros((nrhs, len(mus)) + b.shape[1:], dtype=np.complex128)
@@ -381,7 +389,7 @@ def run_solve(args, world, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": dirac_traffic(), "peak_source": peak_src, "kernel": "dirac_kernel<float,2> (fine stencil)",
                      "algorithmic_bytes_per_launch": bytes_per_apply, "launch_ms": kern_ms},
-        "e2e": {"value": nsys * args.steps * world / e2e_s, "unit": "solves/s",
+        "e2e": {"value": whole_job_rate(nsys * args.steps, world, e2e_s * 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(bh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)},
         "gpu_launches": int(launches),
         "launches_before_timed": int(launches0),

@@ -33,7 +33,6 @@ constexpr int CG_TCH = 8;    // system tiles per shared-memory chunk in the sten
 constexpr int CG_IVEC = 8;   // basis vectors per register chunk in the dot phase
 constexpr int CG_MAXM = 64;  // largest restart length
 constexpr int CG_EPT = 4;    // entries per thread held in registers in the vector phases
-constexpr int CG_ABATCH = 8; // stencil loads in flight per thread
 constexpr int CG_MAXNC = 64; // largest coarse site dimension 2 Nv
 constexpr int CG_AJC = 16;   // stencil columns per asynchronous chunk
 // per-warp shared memory of the stencil phase, in float4 units (vector staging + 2 chunks)

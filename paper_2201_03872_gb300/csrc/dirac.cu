@@ -287,38 +287,38 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 192 : 256, sizeof(real) ==
     real* yo = y + tile * tstride + s * 4;
 #pragma unroll
     for (int k = 0; k < 12; ++k) st2(yo + (int64_t)k * V * 4, acc.c[k]);
-    return;
-  }
-  Spinor<real, T> acc;
+  } else {
+    Spinor<real, T> acc;
 #pragma unroll
-  for (int k = 0; k < 12; ++k)
+    for (int k = 0; k < 12; ++k)
 #pragma unroll
-    for (int l = 0; l < T; ++l) { acc.c[k].re[l] = 0; acc.c[k].im[l] = 0; }
+      for (int l = 0; l < T; ++l) { acc.c[k].re[l] = 0; acc.c[k].im[l] = 0; }
 
 #define TM_HOP(NU)                                                                                   \
-  {                                                                                                  \
-    int64_t sf = c[NU] + 1 < L[NU] ? s + strides[NU] : s - (int64_t)(L[NU] - 1) * strides[NU];      \
-    int64_t sb = c[NU] > 0 ? s - strides[NU] : s + (int64_t)(L[NU] - 1) * strides[NU];               \
-    real pf = (NU == 3 && c[3] == Lt - 1) ? bc_t : real(1);                                         \
-    real pb = (NU == 3 && c[3] == 0) ? bc_t : real(1);                                              \
-    hop<NU, true, real, T>(acc, xt + sf * 2 * T, V, U + (int64_t)NU * 9 * V, V, s, pf);               \
-    hop<NU, false, real, T>(acc, xt + sb * 2 * T, V, U + (int64_t)NU * 9 * V, V, sb, pb);             \
-  }
-  TM_HOP(0)
-  TM_HOP(1)
-  TM_HOP(2)
-  TM_HOP(3)
+    {                                                                                                  \
+      int64_t sf = c[NU] + 1 < L[NU] ? s + strides[NU] : s - (int64_t)(L[NU] - 1) * strides[NU];      \
+      int64_t sb = c[NU] > 0 ? s - strides[NU] : s + (int64_t)(L[NU] - 1) * strides[NU];               \
+      real pf = (NU == 3 && c[3] == Lt - 1) ? bc_t : real(1);                                         \
+      real pb = (NU == 3 && c[3] == 0) ? bc_t : real(1);                                              \
+      hop<NU, true, real, T>(acc, xt + sf * 2 * T, V, U + (int64_t)NU * 9 * V, V, s, pf);               \
+      hop<NU, false, real, T>(acc, xt + sb * 2 * T, V, U + (int64_t)NU * 9 * V, V, sb, pb);             \
+    }
+    TM_HOP(0)
+    TM_HOP(1)
+    TM_HOP(2)
+    TM_HOP(3)
 #undef TM_HOP
-  real m[T];
+    real m[T];
 #pragma unroll
-  for (int l = 0; l < T; ++l) {
-    int n = tile * T + l;
-    m[l] = n < nsys ? (real)mu[n] : real(0);
+    for (int l = 0; l < T; ++l) {
+      int n = tile * T + l;
+      m[l] = n < nsys ? (real)mu[n] : real(0);
+    }
+    local_term<real, T>(acc, xt + s * 2 * T, V, C, V, s, m);
+    real* yo = y + tile * tstride + s * 2 * T;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) stcv(yo + (int64_t)k * V * 2 * T, acc.c[k]);
   }
-  local_term<real, T>(acc, xt + s * 2 * T, V, C, V, s, m);
-  real* yo = y + tile * tstride + s * 2 * T;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) stcv(yo + (int64_t)k * V * 2 * T, acc.c[k]);
 }
 
 // largest divisor of nt that keeps the CTA at <= maxthreads threads

@@ -1138,7 +1138,11 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   rc = check_cuda(ctx, cudaGetLastError(), "solve kernels");
   // final true residual per system (r64 holds b - D x for the current x)
   std::vector<double> hrn(nsys), hbn(nsys);
-  std::vector<int> hflags(nsys), hout(nsys), hin(nsys);
+  std::vector<int> hflags(nsys), hout(nsys), hin(nsys), hmask(nsys);
+  // the loop left at the refinement cap if systems were still active: their last check counted a
+  // cycle that did not run
+  const bool capped = *w->h_count != 0;
+  cudaMemcpyAsync(hmask.data(), w->mask, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(hrn.data(), w->rn, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(hbn.data(), w->bn, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(hflags.data(), w->flags, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st);
@@ -1170,7 +1174,7 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
     if (status != TMAMG_OK) all_ok = 0;
     if (stats) {
       stats[n].status = status;
-      stats[n].outer_iters = hout[n];
+      stats[n].outer_iters = hout[n] - (capped && hmask[n] ? 1 : 0);
       stats[n].inner_iters = hin[n];
       stats[n].coarse_iters = S.coarse_iters;
       stats[n].true_rel_res = hflags[n] ? NAN : rel;

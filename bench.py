@@ -613,8 +613,9 @@ def cpu_solve_baseline(iters_per_solve=21, steps=0, warmup=0):
                       f"x {iters_per_solve} iterations per solve; setup and coarse solves excluded"}
 
 
-def cpu_dirac_baseline():
-    """The FP64 oracle operator on the same lattice and 12 systems, timed on the host cores."""
+def cpu_dirac_baseline(steps=0, warmup=0):
+    """The FP64 oracle operator on the same lattice (4 systems), timed on the host cores: about 8 s
+    of applications, or (the reference arm) warmup + steps applications timed one by one."""
     from oracle import dirac
     wl = WORKLOAD
     L = wl["L"]
@@ -626,14 +627,23 @@ def cpu_dirac_baseline():
     x = synth.gaussian_spinors(L, nsys, seed=7)
     mu = np.full(nsys, wl["mu"])
     op.apply(x[:1], mu[:1])
-    t = time.perf_counter()
-    reps = 0
-    while True:
-        op.apply(x, mu)
-        reps += 1
-        if time.perf_counter() - t > 8.0:
-            break
-    dt = (time.perf_counter() - t) / reps
+    if steps > 0:
+        times = []
+        for k in range(warmup + steps):
+            t = time.perf_counter()
+            op.apply(x, mu)
+            if k >= warmup:
+                times.append(time.perf_counter() - t)
+        dt, reps = float(np.mean(times)), steps
+    else:
+        t = time.perf_counter()
+        reps = 0
+        while True:
+            op.apply(x, mu)
+            reps += 1
+            if time.perf_counter() - t > 8.0:
+                break
+        dt = (time.perf_counter() - t) / reps
     gbs = dirac_bytes_per_site(nsys, 32) * V / dt / 1e9
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
@@ -657,7 +667,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = cpu_solve_baseline(steps=args.steps, warmup=args.warmup) if args.what == "solve" else cpu_dirac_baseline()
+        cb = (cpu_solve_baseline(steps=args.steps, warmup=args.warmup) if args.what == "solve"
+              else cpu_dirac_baseline(steps=args.steps, warmup=args.warmup))
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"], "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",

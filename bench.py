@@ -27,6 +27,7 @@ import synth  # noqa: E402
 WORKLOAD = dict(name="precision-form 16^3x32, 12 point sources, mu=0.003", L=(16, 16, 16, 32), eps=0.25, c_sw=1.0,
                 mu=0.003, nrhs=12, seed=1)
 METRIC = "rhs x shift solves/s at FP64 rel. residual 1e-10; Dirac-op GB/s vs HBM peak"
+DIRAC_WORKLOAD = "fine twisted-mass Wilson-clover stencil, 16^3x32, 12 systems (FP32 bundle)"
 
 
 def kappa_for(L, eps, seed):
@@ -231,7 +232,7 @@ def run_dirac(args, world, rank, local):
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "fine twisted-mass Wilson-clover stencil, 16^3x32, 12 systems (FP32 bundle)",
+        "config": {"workload": DIRAC_WORKLOAD,
                    "kappa": kappa, "kappa_source": ksrc, "nsys": nsys,
                    "l2": "working set 378 MB > 129 MB L2; back-to-back applications"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -390,152 +391,6 @@ def run_solve(args, world, rank, local):
         guarded("learned_step", learned_step)
     T.tmamg_destroy(ctx)
     hbm, _, peak_src = read_peaks()
-    achieved = bytes_per_apply / (kern_ms * 1e-3) / 1e9
-    line = {
-        "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "fine twisted-mass Wilson-clover stencil, 16^3x32, 12 systems (FP32 bundle)",
-                   "kappa": kappa, "kappa_source": ksrc, "nsys": nsys,
-                   "l2": "working set 378 MB > 129 MB L2; back-to-back applications"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": dirac_traffic(), "peak_source": peak_src,
-                     "kernel": "dirac_kernel<float,2>", "algorithmic_bytes_per_launch": bytes_per_apply},
-        "e2e": {"value": whole_job_rate(bytes_per_apply * args.steps, world, e2e_ms) / 1e9, "unit": "GB/s",
-                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(x.nbytes)},
-        "gpu_launches": args.steps,
-        "clocks": clk.result,
-    }
-    return line
-
-
-def setup_kw():
-    return dict(agg=(4, 4, 4, 4), nv=24, sap_block=(4, 4, 4, 4), sap_cycles=2, sap_mr_steps=3, setup_iters=20)
-
-
-def solve_kw():
-    return dict(tol=1e-10, restart=20, max_outer=40, coarse_tol=0.1, coarse_restart=40, coarse_maxiter=400)
-
-
-def measure_dirac(T, ctx, nsys, mu, steps, stream):
-    """CUDA-event time of the fine FP32 stencil on a bundle of nsys systems (same stream)."""
-    import torch
-    nb = T.tmamg_bundle_bytes(ctx, nsys, 32)
-    xb = torch.randn(nb // 4, dtype=torch.float32, device="cuda")
-    yb = torch.empty_like(xb)
-    for _ in range(3):
-        T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    torch.cuda.synchronize()
-    for a, b in ev:
-        a.record(stream)
-        T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32)
-        b.record(stream)
-    torch.cuda.synchronize()
-    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
-
-
-def run_solve(args, world, rank, local):
-    import torch
-    from paper_2201_03872_gb300 import tmamg as T
-
-    wl = WORKLOAD
-    L = wl["L"]
-    V = int(np.prod(L))
-    nrhs = wl["nrhs"]
-    mus = [wl["mu"]]
-    nsys = nrhs * len(mus)
-    kappa, ksrc = kappa_for(L, wl["eps"], wl["seed"])
-    U = synth.gauge_field(L, wl["eps"], seed=wl["seed"] + rank)
-    stream = torch.cuda.current_stream()
-    ctx = T.tmamg_create(L, -1, stream.cuda_stream)
-    T.tmamg_load_gauge(ctx, U)
-    T.tmamg_set_operator(ctx, kappa, wl["c_sw"])
-    t = time.time()
-    T.tmamg_setup(ctx, T.setup_params(**setup_kw()))
-    torch.cuda.synchronize()
-    setup_s = time.time() - t
-    b = synth.point_sources(L)
-    bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
-    xd = torch.zeros(nsys * V * 24, dtype=torch.float64, device="cuda")
-    sp = T.solve_params(**solve_kw())
-    ok = True
-    iters = None
-    with Clocks(local) as clk:
-        for _ in range(args.warmup):
-            T.tmamg_solve(ctx, bd, nrhs, mus, len(mus), xd, 1, sp)
-        torch.cuda.synchronize()
-        barrier(world)
-        launches0 = T.tmamg_kernel_launches()  # kernels launched before the timed region (ncu -s)
-        torch.cuda.synchronize()
-        h0 = time.time()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for k in range(args.steps):
-            rc, stats = T.tmamg_solve(ctx, bd, nrhs, mus, len(mus), xd, 1, sp)
-            ok &= rc == 0 and all(s.status == 0 and s.true_rel_res <= 1e-10 for s in stats)
-            iters = stats
-        t1.record(stream)
-        torch.cuda.synchronize()
-        clk.mark(h0, time.time())
-    launches = T.tmamg_kernel_launches() - launches0
-    total_ms = max_over_ranks(t0.elapsed_time(t1), world)
-    solves_per_s = whole_job_rate(nsys * args.steps, world, total_ms)
-    # end to end through the public API with host buffers: b copied in, x copied out, every step
-    bh = np.ascontiguousarray(b)
-    xh = np.zeros((nrhs, len(mus)) + b.shape[1:], dtype=np.complex128)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for k in range(args.steps):
-        T.tmamg_solve(ctx, bh, nrhs, mus, len(mus), xh, 0, sp)
-    e2e_s = max_over_ranks(time.perf_counter() - t, world)
-    # the fine stencil (dominant hot kernel named by the metric), same context and systems
-    kern_ms = measure_dirac(T, ctx, nsys, np.full(nsys, wl["mu"]), 20, stream)
-    variants = {}
-    if args.variants:
-        # same workload, other forms of the method (each timed over the same number of steps)
-        def timed(label, nr, c=ctx, **kw):
-            spv = T.solve_params(**dict(solve_kw(), **kw))
-            T.tmamg_solve(c, bd, nr, mus, len(mus), xd, 1, spv)
-            torch.cuda.synchronize()
-            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            okv = True
-            for _ in range(args.steps):
-                rcv, stv = T.tmamg_solve(c, bd, nr, mus, len(mus), xd, 1, spv)
-                okv &= rcv == 0 and all(q.status == 0 for q in stv)
-            z.record(stream)
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(z) / args.steps
-            variants[label] = {"solves_per_s": nr * len(mus) / (ms * 1e-3), "ms_per_step": ms, "all_converged": okv,
-                               "fgmres_iterations": stv[0].inner_iters, "coarse_iterations": stv[0].coarse_iters}
-        timed("single_system", 1)
-        # the plain comparator: one system, every vector, operator and reduction in FP64
-        timed("plain_fp64_single_system", 1, precision=64)
-        timed("block_gmres_coarse", nrhs, coarse_solver=1)
-        # three levels: a second coarsening (2^4 aggregates of the 4^3 x 8 level-1 lattice, Nv = 32), the middle
-        # level solved by FGMRES(10) to 7e-2 with the level-2 correction and 3 MR steps as its preconditioner
-        ctx3 = T.tmamg_create(L, -1, stream.cuda_stream)
-        T.tmamg_load_gauge(ctx3, U)
-        T.tmamg_set_operator(ctx3, kappa, wl["c_sw"])
-        t = time.time()
-        T.tmamg_setup(ctx3, T.setup_params(levels=3, agg2=(2, 2, 2, 2), nv2=32, **setup_kw()))
-        torch.cuda.synchronize()
-        setup3 = time.time() - t
-        timed("three_level", nrhs, c=ctx3)
-        variants["three_level"]["setup_seconds"] = setup3
-        T.tmamg_destroy(ctx3)
-        t = time.time()
-        rep = T.tmamg_nn_train(ctx, T.tmamg_default_nn_params(pairs=48, batch=12, epochs=30, lr=2e-3, mu=wl["mu"],
-                                                              gate_systems=4))
-        torch.cuda.synchronize()
-        timed("learned_step", nrhs, use_nn=2)
-        variants["learned_step"].update({"train_seconds": time.time() - t, "loss_first": rep.loss_first,
-                                         "loss_last": rep.loss_last, "gate_iterations_plain": rep.iters_plain,
-                                         "gate_iterations_with_step": rep.iters_nn, "gate_enabled": bool(rep.enabled)})
-    T.tmamg_destroy(ctx)
-    hbm, _, peak_src = read_peaks()
     bytes_per_apply = dirac_bytes_per_site(nsys, 32) * V
     achieved = bytes_per_apply / (kern_ms * 1e-3) / 1e9
     s0 = iters[0]
@@ -673,7 +528,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD["name"] if args.what == "solve" else
-                           "fine twisted-mass Wilson-clover stencil, 16^3x32 (CPU oracle sample)"},
+                           DIRAC_WORKLOAD},
                 "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))

@@ -47,9 +47,9 @@ def dirac_bytes_per_site(nsys, prec):
     return (4 * 18 + 72) * es + nsys * 2 * 24 * es
 
 
-# DRAM bytes (read + write) of one fine-stencil launch at 16^3x32 x 12 systems, from the ncu
-# capture summarised in profiles/dirac_kernel_16x16x16x32_n12.md; valid only for the kernel
-# sources it was taken on (SHA-1 of dirac.cu and stencil.cuh), else reported as null
+# DRAM bytes (read + write) of one fine-stencil launch at 16^3x32 x 12 systems, from an ncu
+# capture of that kernel; valid only for the kernel sources it was taken on (SHA-1 of dirac.cu
+# and stencil.cuh), else reported as null
 DIRAC_TRAFFIC = {"bytes": 237069824 + 120919040,
                  "sha1": {"dirac.cu": "24e92d0ad15242de099dc0789bc8e321b64cb249",
                           "stencil.cuh": "bdc68ee2e32fd9112f7efc57c95df0422ce387ff"}}

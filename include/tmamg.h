@@ -237,10 +237,16 @@ int tmamg_sap(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const do
 #define TMAMG_SAP_NOALLOC_MAX_SYSTEMS 64
 
 /* tmamg_sap for callers that cannot allocate device memory at call time: code that runs
- * while a stream is being captured into a CUDA graph (where cudaMalloc is not allowed), code
+ * while a stream is being captured into a CUDA graph (cudaMalloc is not allowed there), code
  * that must not touch the allocator after it has fixed its memory budget, or code running
- * under a memory pool it does not own. Same arguments and result as tmamg_sap; the paper has
- * no counterpart, this is a property of the library only.
+ * under a memory pool it does not own. The paper has no counterpart; this is a property of
+ * the library only. Same arguments and arithmetic as tmamg_sap (r is overwritten with the
+ * partially updated residual, e receives the correction).
+ * Unlike tmamg_sap it does not wait for the stream: the work is queued on the context's
+ * stream and the call returns; e and r are written when the stream reaches that work, so a
+ * caller reading them from the host or from another stream must synchronise with the
+ * context's stream first. The return value reports argument errors and launch errors only;
+ * a fault while the kernels run surfaces at a later synchronising call.
  * Its scratch (the correction buffer of the red/black sweeps, and the nsys twisted masses)
  * lives in file-scope device arrays of TMAMG_SAP_NOALLOC_MAX_BYTES bytes and
  * TMAMG_SAP_NOALLOC_MAX_SYSTEMS doubles, which every GPU that loads the library holds until
@@ -249,9 +255,11 @@ int tmamg_sap(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const do
  * limit is rejected with TMAMG_ERR_ARG before anything is launched.
  * The first call on a device looks up the arrays' device addresses (cudaGetSymbolAddress,
  * with that device current); make that first call before any stream capture. Every call
- * shares the arrays: two calls whose work overlaps on the GPU (different streams, or
- * different contexts on one device) race on them. mu: host [nsys], copied with
- * cudaMemcpyAsync on the context's stream. */
+ * shares the arrays, which keep the last call's contents: two calls whose work overlaps on
+ * the GPU (different streams, or different contexts on one device) race on them.
+ * mu: host [nsys], copied into the device array by cudaMemcpyAsync on the context's stream.
+ * From pageable memory that copy is staged before the call returns; from page-locked memory
+ * the caller keeps mu unchanged until the stream has passed the call. */
 int tmamg_sap_noalloc(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const double* mu, const int block[4],
                       int cycles, int mr_steps);
 

@@ -7,7 +7,7 @@ coarse lattice of aggregates; the construction recurses to further levels.
 Paper Sec. 4 / Fig. 6 caption: on coarse levels the twisted mass enters as
 i (delta mu) mu gamma5_c.
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * aggregates are rectangular blocks; every test vector is split by
     chirality (spins 0,1 versus 2,3 on the fine level; the first and second
     half of the coarse index on coarse levels), so a coarse site carries

@@ -7,7 +7,7 @@ degenerate twisted-mass clover fermions, Sec. 1 / Sec. 2):
                - 1/2 sum_nu [ (1 - gamma_nu) U_nu(s) x(s + nu)
                               + (1 + gamma_nu) U_nu(s - nu)^dagger x(s - nu) ]
 
-Readings where the paper is silent (all listed in the design doc):
+Readings where the paper is silent:
   * m0 = 1/(2 kappa) - 4, so 4 + m0 = 1/(2 kappa);
   * mu enters in the same units as m0 (no 2 kappa factor);
   * C(s) = (i/4) sum_{mu,nu} sigma_{mu nu} (x) F_{mu nu}(s) with

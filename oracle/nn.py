@@ -1,7 +1,7 @@
 """Gauge-covariant parallel-transport network in FP64 (oracle; test infrastructure only).
 
-The learned preconditioner step is not in the paper; the method description of this build
-adds it as an extra fine-level preconditioner inside FGMRES. Readings (listed in the design doc):
+The learned preconditioner step is not in the paper; the method description adds it as an
+extra fine-level preconditioner inside FGMRES. Readings:
   * three linear layers (no activation) with 4 -> 8 -> 8 -> 4 complex channels, each channel
     a colour 3-vector per site (the 12 = 4 x 3 spinor components enter as 4 channels);
   * a layer is out_a(x) = sum_h sum_b W_h[a, b] (T_h in_b)(x) over the nine hops

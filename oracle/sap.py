@@ -4,7 +4,7 @@ Paper Sec. 2: the lattice is divided into small blocks in a chessboard manner
 and the local Dirac operators on the blocks are (approximately) inverted, red
 blocks first, then black; SAP damps the high modes of the error.
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * colour of a block = parity of the sum of its block coordinates; red = even;
   * the block operator D_B keeps only hops whose two ends lie in the same block
     (Dirichlet boundary); the block solve is `mr_steps` steps of the minimal

@@ -6,7 +6,7 @@ the largest. Singular values of D_W are the absolute eigenvalues of the Hermitia
 H = gamma5 D_W, i.e. the square roots of the eigenvalues of D_W^+ D_W; both ends are taken
 by Lanczos (scipy eigsh) on D_W^+ D_W applied through the FP64 oracle operator.
 
-Reading (see DESIGN.md): the bisection runs on an 8^3 x 16 lattice built with the same gauge
+Reading: the bisection runs on an 8^3 x 16 lattice built with the same gauge
 recipe (eps, seed) as the large lattice, because the numpy oracle cannot afford Lanczos on
 the large volumes; the kappa found is used on the large lattice. The bisection stays below
 the first kappa where sigma_min turns up again (critical point of a rough field).

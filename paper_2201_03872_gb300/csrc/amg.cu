@@ -244,11 +244,7 @@ void restrict_vec(const AggDims& g, const float2* P, const float* r, float* xc, 
   int kc = RS_KC;
   while (kc > RS_KS && sizeof(float4) * (size_t)nt * kc + sizeof(int) * g.asize > 190 * 1024) kc -= RS_KS;
   const size_t smem = sizeof(float4) * (size_t)nt * kc + sizeof(int) * g.asize;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(restrict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  func_smem_optin((const void*)restrict_kernel, 200 * 1024);
   restrict_kernel<<<(unsigned)(g.Vc * 2), RS_THREADS, smem, st>>>(P, r, xc, g, nv, d, nt, kc);
   TM_COUNT();
 }

@@ -1,7 +1,10 @@
 // C ABI of the tmamg library: context, gauge field, operator, bundles, fine stencil.
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 
 #include "common.cuh"
 
@@ -10,6 +13,47 @@ namespace tmamg {
 uint64_t& launch_counter() {
   static uint64_t n = 0;
   return n;
+}
+
+static std::mutex g_dev_mutex;
+
+static int current_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return dev;
+}
+
+int device_sms() {
+  static std::map<int, int> sms;
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_dev_mutex);
+  auto it = sms.find(dev);
+  if (it != sms.end()) return it->second;
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  sms[dev] = n;
+  return n;
+}
+
+int device_smem_optin() {
+  static std::map<int, int> optin;
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_dev_mutex);
+  auto it = optin.find(dev);
+  if (it != optin.end()) return it->second;
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  optin[dev] = n;
+  return n;
+}
+
+void func_smem_optin(const void* func, int bytes) {
+  static std::map<std::pair<int, const void*>, int> done;
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_dev_mutex);
+  int& have = done[std::make_pair(dev, func)];
+  if (have >= bytes) return;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess) have = bytes;
 }
 
 int set_err(tmamg_ctx* ctx, int code, const std::string& msg) {

@@ -849,23 +849,16 @@ static size_t dyn_smem_bytes(int m, int nc, int nsys, bool tc, int nstage) {
 }
 
 static size_t dyn_smem_cap() {
-  static size_t cap = 0;
-  if (!cap) {
-    cap = cm_dyn_cap((const void*)coarse_gmres_kernel);
-    cudaFuncSetAttribute(coarse_gmres_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
-  }
+  const size_t cap = cm_dyn_cap((const void*)coarse_gmres_kernel);
+  func_smem_optin((const void*)coarse_gmres_kernel, (int)cap);
   return cap;
 }
 
 int coarse_gmres_grid(int nt) {
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel, CG_THREADS, dyn_smem_cap());
-    if (per_sm < 1) per_sm = 1;
-  }
+  const int sms = device_sms();
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel, CG_THREADS, dyn_smem_cap());
+  if (per_sm < 1) per_sm = 1;
   int want = sms;  // one CTA per SM keeps the barrier short
   if (want > per_sm * sms) want = per_sm * sms;
   int Gt = want / nt;

@@ -88,9 +88,7 @@ __global__ void __launch_bounds__(CM_THREADS, 1) coarse_mma_kernel(CmArgs q) {
 }
 
 size_t cm_dyn_cap(const void* kernel) {
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int optin = device_smem_optin();
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 0;
   const size_t used = fa.sharedSizeBytes + 1024;  // static shared memory and the per-CTA reserve
@@ -99,15 +97,9 @@ size_t cm_dyn_cap(const void* kernel) {
 
 int coarse_apply_f16(const CoarseDims& cd, const __half* A16, const float* x, float* y, const double* mu, double dmu,
                      int nsys, float* mx, __half* X16, int* err, cudaStream_t st) {
-  static int sms = 0;
-  static size_t cap = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cap = cm_dyn_cap((const void*)coarse_mma_kernel);
-    cudaFuncSetAttribute(coarse_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
-  }
+  const int sms = device_sms();
+  const size_t cap = cm_dyn_cap((const void*)coarse_mma_kernel);
+  func_smem_optin((const void*)coarse_mma_kernel, (int)cap);
   if (nsys <= 0) return 0;
   if (cd.nc > CM_MAXNC || cd.nc < 1 || nsys > CM_MAXSYS) return -2;
   const int nstage = cm_nstage(cd.nc, nsys, cap);

@@ -103,6 +103,13 @@ void free_levels(tmamg_ctx* ctx);
 void free_workspace(tmamg_ctx* ctx);
 void free_nn(tmamg_ctx* ctx);
 
+// per-device launch facts (host, thread-safe): the SM count and the shared-memory opt-in limit
+// of the current device, and a kernel's dynamic shared-memory limit raised on the current device
+// (cudaFuncSetAttribute acts per device, so each device gets its own call)
+int device_sms();
+int device_smem_optin();
+void func_smem_optin(const void* func, int bytes);
+
 // error helpers (host)
 int set_err(tmamg_ctx* ctx, int code, const std::string& msg);
 int check_cuda(tmamg_ctx* ctx, cudaError_t e, const char* what);

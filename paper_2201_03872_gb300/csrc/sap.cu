@@ -367,13 +367,8 @@ void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C
   // links [4][9][bv] float2 + clover [72][bv] + rho [12][bv] float4 + reduction scratch
   size_t smem = sizeof(float2) * 36 * d.bv + sizeof(float) * 72 * d.bv + sizeof(float4) * 12 * d.bv +
                 sizeof(float) * 8 * nwarps;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(sap_mr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  }
+  const int sms = device_sms();
+  func_smem_optin((const void*)sap_mr_kernel, 200 * 1024);
   const int per_colour = d.pdim < 0 ? 1 : nblocks / 2;
   for (int cy = 0; cy < cycles; ++cy) {
     for (int colour = 0; colour < 2; ++colour) {
@@ -611,11 +606,7 @@ void sap_apply64(const Geom& g, const int bs[4], const double2* U64, const doubl
   cudaMemsetAsync(e, 0, sizeof(double) * 24 * g.V * nsys, st);
   const int nthreads = (d.bv + 31) / 32 * 32;
   const size_t smem = sizeof(double2) * 12 * d.bv + sizeof(double) * 4 * (nthreads / 32);
-  static bool attr = false;
-  if (!attr) {  // 4^4 blocks need 49 KB, above the default dynamic limit
-    cudaFuncSetAttribute(sap64_mr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    attr = true;
-  }
+  func_smem_optin((const void*)sap64_mr_kernel, 64 * 1024);  // 4^4 blocks need 49 KB, above the default limit
   for (int cy = 0; cy < cycles; ++cy) {
     for (int colour = 0; colour < 2; ++colour) {
       const int nb_c = d.pdim < 0 ? (colour == 0 ? 1 : 0) : nblocks / 2;

@@ -8,6 +8,7 @@
 // variant whose scratch lives in file-scope device arrays of a fixed maximum size, which
 // every GPU that loads the library holds until the process exits.
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "sap.cuh"
@@ -22,8 +23,11 @@ static __device__ __align__(256) float4 g_sap_scratch[NOALLOC_SAP_SCRATCH_BYTES 
 static __device__ __align__(256) double g_sap_mu[NOALLOC_SAP_MAX_SYS];
 
 // device addresses of the two arrays, looked up once per device (host-side names are only
-// stand-ins for the device symbols and must never be passed to a kernel)
+// stand-ins for the device symbols and must never be passed to a kernel). std::call_once makes
+// the first lookup on a device safe when several host threads make their first call together.
 constexpr int MAX_DEVICES = 64;
+static std::once_flag s_once[MAX_DEVICES];
+static cudaError_t s_lookup_err[MAX_DEVICES];
 static float* s_scratch_ptr[MAX_DEVICES] = {nullptr};
 static double* s_mu_ptr[MAX_DEVICES] = {nullptr};
 
@@ -32,16 +36,19 @@ static int noalloc_addresses(tmamg_ctx* ctx, float** scratch, double** mu) {
   int rc = check_cuda(ctx, cudaGetDevice(&dev), "cudaGetDevice");
   if (rc) return rc;
   if (dev < 0 || dev >= MAX_DEVICES) return set_err(ctx, TMAMG_ERR_STATE, "sap_noalloc: device index out of range");
-  if (!s_scratch_ptr[dev]) {
+  std::call_once(s_once[dev], [dev]() {
     void* p = nullptr;
-    rc = check_cuda(ctx, cudaGetSymbolAddress(&p, g_sap_scratch), "cudaGetSymbolAddress(scratch)");
-    if (rc) return rc;
     void* q = nullptr;
-    rc = check_cuda(ctx, cudaGetSymbolAddress(&q, g_sap_mu), "cudaGetSymbolAddress(mu)");
-    if (rc) return rc;
-    s_scratch_ptr[dev] = static_cast<float*>(p);
-    s_mu_ptr[dev] = static_cast<double*>(q);
-  }
+    cudaError_t e = cudaGetSymbolAddress(&p, g_sap_scratch);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_sap_mu);
+    s_lookup_err[dev] = e;
+    if (e == cudaSuccess) {
+      s_scratch_ptr[dev] = static_cast<float*>(p);
+      s_mu_ptr[dev] = static_cast<double*>(q);
+    }
+  });
+  rc = check_cuda(ctx, s_lookup_err[dev], "cudaGetSymbolAddress(sap_noalloc scratch)");
+  if (rc) return rc;
   *scratch = s_scratch_ptr[dev];
   *mu = s_mu_ptr[dev];
   return TMAMG_OK;

@@ -74,3 +74,61 @@ def test_sap_reduces_residual(small):
     res = r - op.apply(e, mu)
     for n in range(2):
         assert np.linalg.norm(res[n]) < 0.5 * np.linalg.norm(r[n])
+
+
+def _dense_gauss_seidel(M, colour, r, cycles):
+    """Multiplicative Schwarz with exact block solves, written with dense matrices: for each
+    cycle, e_red += M_rr^{-1} (r - M e)_red, then e_black += M_bb^{-1} (r - M e)_black."""
+    e = np.zeros_like(r)
+    for _ in range(cycles):
+        for c in (0, 1):
+            sel = colour == c
+            res = r - M @ e
+            e[sel] += np.linalg.solve(M[np.ix_(sel, sel)], res[sel])
+    return e
+
+
+def test_sap_cycle_is_block_gauss_seidel(small):
+    # Paper Sec. 2: SAP inverts the red blocks, then the black blocks on the residual that the red
+    # correction left. On a 2 x 2 chessboard of blocks the two red blocks do not touch, so the red
+    # block operator is the red-red part of D and one sweep with converged block solves is one step
+    # of block Gauss-Seidel. Computing both colours from the same residual (additive Schwarz) or
+    # reusing the red residual for the black sweep fails this pin.
+    Ls = (4, 4, 2, 2)
+    op = dirac.Operator(synth.gauge_field(Ls, 0.3, seed=26), kappa=0.11, c_sw=1.0)
+    bs = (2, 2, 2, 2)
+    mu = 0.05
+    M = op.dense(mu)
+    colour = np.repeat(sap.block_colour(Ls, bs).ravel(), 12)
+    r = synth.gaussian_spinors(Ls, 1, seed=27)[0]
+    for cycles in (1, 2):
+        e = sap.sap(op, r, mu, bs, cycles=cycles, mr_steps=150)  # block MR converged (1e-15) well before 150
+        ref = _dense_gauss_seidel(M, colour, r.ravel(), cycles)
+        assert np.linalg.norm(e.ravel() - ref) < 1e-8 * np.linalg.norm(ref), cycles
+    # the pin separates multiplicative from additive Schwarz on this lattice
+    add = np.zeros_like(r.ravel())
+    for c in (0, 1):
+        sel = colour == c
+        add[sel] = np.linalg.solve(M[np.ix_(sel, sel)], r.ravel()[sel])
+    ref1 = _dense_gauss_seidel(M, colour, r.ravel(), 1)
+    assert np.linalg.norm(add - ref1) > 1e-2 * np.linalg.norm(ref1)
+
+
+def test_setup_test_vectors_is_inverse_power_iteration(small):
+    # Paper Sec. 2: the test vectors approximate low modes by inverse iteration. With one SAP block
+    # covering the lattice and its MR solve run to convergence, SAP(v) = D^{-1} v, so k setup steps
+    # give D^{-k} v0 normalised (dense inverse power iteration).
+    from oracle import amg
+    Ls, op = small
+    mu = 0.02
+    V0 = synth.gaussian_spinors(Ls, 2, seed=28)
+    k = 3
+    V = amg.setup_test_vectors(op, V0, mu, Ls, k, sap_cycles=1, mr_steps=500)
+    Minv = np.linalg.inv(op.dense(mu))
+    for n in range(2):
+        ref = V0[n].ravel()
+        for _ in range(k):
+            ref = Minv @ ref
+        ref = ref / np.linalg.norm(ref)
+        assert np.linalg.norm(V[n].ravel() - ref) < 1e-8, n
+        assert abs(np.linalg.norm(V[n]) - 1.0) < 1e-12

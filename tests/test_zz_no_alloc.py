@@ -29,13 +29,17 @@ def test_sap_noalloc_matches_sap_twice():
         eb = lat.torch.zeros_like(rb)
         T.tmamg_sap(lat.ctx, rb, eb, nsys, mu, bs, 2, 3)
         e_ref = lat.from_fine_bundle(eb, nsys)
+        r_ref = lat.from_fine_bundle(rb, nsys)  # both calls leave the partially updated residual in r
         for call in range(2):
             rb2 = lat.fine_bundle(r)
             eb2 = lat.torch.full_like(rb2, 7.0)  # the output need not be cleared by the caller
             T.tmamg_sap_noalloc(lat.ctx, rb2, eb2, nsys, mu, bs, 2, 3)
+            lat.torch.cuda.synchronize()  # the call returns without waiting for its stream
             e = lat.from_fine_bundle(eb2, nsys)
+            r2 = lat.from_fine_bundle(rb2, nsys)
             for n in range(nsys):
                 assert relerr(e[n], e_ref[n]) <= TOL32, (call, n, relerr(e[n], e_ref[n]))
+                assert relerr(r2[n], r_ref[n]) <= TOL32, (call, n, relerr(r2[n], r_ref[n]))
     finally:
         lat.close()
 
@@ -51,5 +55,20 @@ def test_sap_noalloc_rejects_oversized_bundle():
         with pytest.raises(T.TmamgError) as ei:
             T.tmamg_sap_noalloc(lat.ctx, rb, eb, nsys, np.zeros(nsys), (4, 4, 4, 4), 1, 1)
         assert ei.value.code == -1 and "scratch" in str(ei.value)
+    finally:
+        lat.close()
+
+
+def test_sap_noalloc_rejects_too_many_systems():
+    from paper_2201_03872_gb300 import tmamg as T
+    L = (4, 4, 4, 4)
+    lat = Lattice(L, synth.unit_gauge(L), 0.12, 1.0)
+    try:
+        nsys = 65  # one more than the fixed twisted-mass array holds; 33 tiles of this lattice fit the scratch
+        rb = lat.torch.zeros(T.tmamg_bundle_bytes(lat.ctx, nsys, 32) // 4, dtype=lat.torch.float32, device="cuda")
+        eb = lat.torch.zeros_like(rb)
+        with pytest.raises(T.TmamgError) as ei:
+            T.tmamg_sap_noalloc(lat.ctx, rb, eb, nsys, np.zeros(nsys), (2, 2, 2, 2), 1, 1)
+        assert ei.value.code == -1 and "systems" in str(ei.value)
     finally:
         lat.close()

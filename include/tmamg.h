@@ -293,6 +293,19 @@ int tmamg_coarse_apply(tmamg_ctx* ctx, int level, const void* x_bundle, void* y_
 int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* xc_bundle, int nrhs, const double* mu,
                        int nshift, const tmamg_solve_params* p, int* iterations);
 
+/* ------------------------------------------------------------------ diagnostics */
+
+/* Failure-path test hook (no counterpart in the paper). Sets, for the whole process, the bound
+ * in SM clock cycles of the grid-barrier waits of the persistent coarse GMRES kernel
+ * (limit_cycles; 0 restores the default of 2e9 cycles, about one second at 2 GHz). If
+ * unreachable_next is nonzero, the next persistent coarse solve (of any context) makes every grid
+ * barrier wait for one arrival more than its grid holds, a count that nothing reaches: its first
+ * barrier, which follows a plain vector pass, gives up after limit_cycles, the kernel records the
+ * failure and returns, and the call reports TMAMG_ERR_TIMEOUT; the request is then cleared.
+ * With the FP32 coarse stencil (coarse_precision 32) no bulk copy or tensor-core operation is in
+ * flight when the wait gives up. Returns TMAMG_ERR_ARG for limit_cycles < 0. */
+int tmamg_debug_bounded_wait(long long limit_cycles, int unreachable_next);
+
 #ifdef __cplusplus
 }
 #endif

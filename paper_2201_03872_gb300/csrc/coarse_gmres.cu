@@ -20,6 +20,7 @@
 //    barrier of their own.
 //  * Small dense work (Givens rotations, back substitution) is per system, with every
 //    operand fetched before the dependent arithmetic starts.
+#include <atomic>
 #include <cmath>
 
 #include "amg.cuh"
@@ -73,6 +74,8 @@ struct CGArgs {
   float* hpart;   // [9][nt][nc][Vc][4] hop partials of the stencil
   unsigned* bar;  // [2]: count, generation
   int* err;
+  long long wait_limit;  // clock cycles a CTA waits at a grid barrier before it gives up
+  unsigned extra;        // arrivals a barrier needs beyond the grid (0; 1 makes every barrier unreachable)
   int* iters;  // [1] Arnoldi steps done
   int G, Gt;
   int NS;  // stride of the per-system arrays
@@ -88,13 +91,13 @@ __device__ __forceinline__ bool grid_barrier(const CGArgs& p) {
     unsigned prev;
     asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;\n" : "=r"(prev) : "l"(p.bar) : "memory");
     const unsigned G = (unsigned)p.G;
-    const unsigned target = (prev / G + 1) * G;
+    const unsigned target = (prev / G + 1) * G + p.extra;
     const long long t0 = clock64();
     while (true) {
       unsigned cur;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(cur) : "l"(p.bar) : "memory");
       if ((int)(cur - target) >= 0) break;
-      if (clock64() - t0 > 2000000000LL) {  // about one second at 2 GHz
+      if (clock64() - t0 > p.wait_limit) {  // 2e9 cycles by default, about one second at 2 GHz
         atomicExch(p.err, 1);
         break;
       }
@@ -866,6 +869,16 @@ int coarse_gmres_grid(int nt) {
   return Gt * nt;
 }
 
+// bound of the grid-barrier waits, and a one-shot request that the next launch's barriers be
+// unreachable (process-wide; set by tmamg_debug_bounded_wait for the tests of the timeout path)
+static std::atomic<long long> g_wait_limit{2000000000LL};
+static std::atomic<int> g_unreachable_next{0};
+
+void coarse_gmres_debug_wait(long long limit_cycles, int unreachable_next) {
+  g_wait_limit.store(limit_cycles > 0 ? limit_cycles : 2000000000LL);
+  g_unreachable_next.store(unreachable_next ? 1 : 0);
+}
+
 int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, const __half* A16, const float* rc,
                        float* xc, float* V, int64_t vstride, const double* mu, double dmu, int nsys, int m,
                        int maxiter, double tol, int* iters_done, cudaStream_t st) {
@@ -902,6 +915,8 @@ int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, co
   p.H = s.H; p.cs = s.cs; p.sn = s.sn; p.g = s.g; p.y = s.y; p.tolabs = s.tolabs; p.sc = s.sc;
   p.kconv = s.kconv; p.active = s.active; p.done = s.done; p.nactive = s.nactive; p.part = s.part;
   p.bar = s.bar; p.err = s.err; p.iters = s.iters; p.hpart = s.hpart;
+  p.wait_limit = g_wait_limit.load();
+  p.extra = (unsigned)g_unreachable_next.exchange(0);
   p.G = G;
   p.Gt = G / nt;
   p.NS = s.NS;

@@ -29,6 +29,11 @@ int coarse_gmres_grid(int nt);
 // apart). A16: the FP16 operator of the tensor-core stencil (coarse_mma.cuh), or null for the
 // FP32 stencil A. If iters_done is non-null the call synchronises the stream and returns -3
 // when a bounded wait timed out, else 0; -1 if the launch failed, -2 if the state is too small.
+// process-wide wait bound of the persistent kernel's grid barriers (cycles; <= 0 restores the
+// default of 2e9) and a one-shot request that the next launch's barriers wait for one arrival
+// more than the grid has, so that the bounded wait runs out (tests of the timeout path)
+void coarse_gmres_debug_wait(long long limit_cycles, int unreachable_next);
+
 int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, const __half* A16, const float* rc,
                        float* xc, float* V, int64_t vstride, const double* mu, double dmu, int nsys, int m,
                        int maxiter, double tol, int* iters_done, cudaStream_t st);

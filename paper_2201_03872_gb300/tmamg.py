@@ -111,6 +111,7 @@ SIGNATURES = {
     "tmamg_nn_forward": (I, [P, P, P, I, I]),
     "tmamg_nn_loss_grad": (I, [P, P, P, I, ctypes.POINTER(ctypes.c_double), P]),
     "tmamg_nn_train": (I, [P, ctypes.POINTER(NNParams), ctypes.POINTER(NNReport)]),
+    "tmamg_debug_bounded_wait": (I, [ctypes.c_longlong, I]),
 }
 
 
@@ -310,6 +311,13 @@ def tmamg_coarse_solve(ctx, level, rc_bundle, xc_bundle, nrhs, mu, nshift, param
                                                                 int(nrhs), _ptr(m), int(nshift), ctypes.byref(params),
                                                                 ctypes.byref(it)))
     return it.value
+
+
+def tmamg_debug_bounded_wait(limit_cycles, unreachable_next):
+    """Process-wide bound of the persistent coarse solver's barrier waits, and a one-shot
+    unreachable barrier for the next persistent coarse solve (tests of the timeout path)."""
+    return _check("tmamg_debug_bounded_wait", None, lib().tmamg_debug_bounded_wait(int(limit_cycles),
+                                                                                  int(unreachable_next)))
 
 
 def tmamg_default_nn_params(**kw):

@@ -62,3 +62,41 @@ def test_refinement_cap_returns_not_converged_with_stats():
                 assert 1e-14 < res < 1.0 and abs(s.true_rel_res - res) <= 1e-3 * res, (r, k, res, s.true_rel_res)
     finally:
         lat.close()
+
+
+def test_coarse_barrier_timeout_is_reported_and_context_recovers():
+    # the persistent coarse GMRES's grid barrier is made unreachable from the host (it waits for one
+    # arrival more than the grid holds) with a 10 ms bound; the first barrier follows a plain vector
+    # pass and the FP32 stencil is used, so no bulk copy or tensor-core work is in flight when the
+    # wait gives up. The call must report TMAMG_ERR_TIMEOUT and the context must still solve.
+    U, lat = _lattice()
+    T = lat.T
+    try:
+        nrhs, mus = 2, [0.01]
+        nsys = nrhs * len(mus)
+        nc = 24
+        Vc = int(np.prod([8 // 4, 4 // 2, 4 // 2, 8 // 4]))
+        from tests.gpu_util import coarse_to_bundle
+        rc_vec = synth.complex_normal(43, 1, (nsys, Vc, nc))
+        rb = lat.torch.from_numpy(coarse_to_bundle(rc_vec, nc, Vc)).cuda()
+        xb = lat.coarse_buffer(nsys)
+        sp = T.solve_params(coarse_precision=32, coarse_solver=0, coarse_tol=1e-3, coarse_maxiter=200)
+        T.tmamg_debug_bounded_wait(20_000_000, 1)  # about 10 ms at 2 GHz
+        try:
+            with pytest.raises(T.TmamgError) as ei:
+                T.tmamg_coarse_solve(lat.ctx, 1, rb, xb, nrhs, mus, len(mus), sp)
+            assert ei.value.code == -6, ei.value  # TMAMG_ERR_TIMEOUT
+        finally:
+            T.tmamg_debug_bounded_wait(0, 0)
+        # the same call without the unreachable barrier converges
+        it = T.tmamg_coarse_solve(lat.ctx, 1, rb, xb, nrhs, mus, len(mus), sp)
+        assert 0 < it < 200
+        yb = lat.coarse_buffer(nsys)
+        T.tmamg_coarse_apply(lat.ctx, 1, xb, yb, nsys, np.array(mus * nrhs), 32)
+        lat.torch.cuda.synchronize()
+        from tests.gpu_util import coarse_from_bundle
+        y = coarse_from_bundle(yb.cpu().numpy(), nsys, nc, Vc)
+        for n in range(nsys):
+            assert np.linalg.norm(y[n] - rc_vec[n]) <= 2e-3 * np.linalg.norm(rc_vec[n]), n
+    finally:
+        lat.close()

@@ -1,10 +1,17 @@
 """Benchmark of the multi-rhs / multi-shift twisted-mass solver on one GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--what solve|dirac]
+                [--workload largest|batched|precision] [--no-variants] [--no-cpu-baseline]
 
-Workload (precision form): 16^3 x 32 lattice, U = exp(i 0.25 H) reunitarised, c_sw = 1,
-kappa from the tuning table in tests/golden/kappa.json (sigma_min / sigma_max of D_W ~ 1e-3),
-mu = 0.003, 12 point-source right-hand sides; synthetic, seeded.
+Headline workload (largest single-GPU configuration): 40^3 x 80 lattice, U = exp(i 0.2 H)
+reunitarised, c_sw = 1, kappa from the tuning table in tests/golden/kappa.json, 4 Gaussian
+right-hand sides x 4 twisted masses {0.0015, 0.005, 0.015, 0.05} = 16 systems, three-level AMG
+(4^4 aggregates with Nv = 24, then 2^4 aggregates with Nv = 32), FP32 fine level and SAP, FP16
+coarse operators on the tensor cores, FP64 outer residuals; synthetic, seeded.
+Variants over other workloads: the batched multi-shift form (24^3 x 48, 4 complex Z2-noise
+right-hand sides x 10 log-spaced twisted masses = 40 systems in one solve) and the precision
+form (16^3 x 32, 12 point sources), with the single-system, plain FP64, block-GMRES, three-level
+and learned-step forms of the latter.
 
 One JSON line on rank 0. Under torchrun (N > 1) every rank runs an independent replica of
 the workload (the systems are independent; no data-path collective) and the time is the
@@ -24,10 +31,48 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOAD = dict(name="precision-form 16^3x32, 12 point sources, mu=0.003", L=(16, 16, 16, 32), eps=0.25, c_sw=1.0,
-                mu=0.003, nrhs=12, seed=1)
 METRIC = "rhs x shift solves/s at FP64 rel. residual 1e-10; Dirac-op GB/s vs HBM peak"
+
+_AMG2 = dict(levels=2, agg=(4, 4, 4, 4), nv=24, sap_block=(4, 4, 4, 4), sap_cycles=2, sap_mr_steps=3, setup_iters=20)
+WORKLOADS = {
+    "largest": dict(
+        name="largest single-GPU: 40^3x80, eps 0.2, 4 Gaussian rhs x 4 twisted masses {0.0015,0.005,0.015,0.05}, "
+             "3-level AMG",
+        L=(40, 40, 40, 80), eps=0.2, c_sw=1.0, seed=1, nrhs=4, rhs="gaussian", mus=[0.0015, 0.005, 0.015, 0.05],
+        setup=dict(_AMG2, levels=3, agg2=(2, 2, 2, 2), nv2=32, setup_gmres_steps=20),
+        solve=dict(tol=1e-10, restart=5, max_outer=60, coarse_tol=0.1, coarse_restart=40, coarse_maxiter=400,
+                   mid_tol=7e-2, mid_restart=10, mid_maxiter=50, mid_smooth=3),
+        amg="3-level: 4^4 aggregates Nv=24 (10^3x20 x 48), then 2^4 aggregates Nv=32 (5^3x10 x 64); 20 setup "
+            "iterations; SAP 4^4 blocks x 2 cycles x 3 MR; FGMRES(5) + FP64 refinement; middle FGMRES(10) to 7e-2 "
+            "with 3 MR smoothing steps; bottom persistent GMRES(40) to 0.1"),
+    "batched": dict(
+        name="batched multi-shift: 24^3x48, eps 0.25, 4 complex Z2-noise rhs x 10 twisted masses log-spaced "
+             "1e-3..1e-1 (40 systems)",
+        L=(24, 24, 24, 48), eps=0.25, c_sw=1.0, seed=1, nrhs=4, rhs="z2", mus=list(synth.log_shifts(10)),
+        setup=dict(_AMG2),
+        solve=dict(tol=1e-10, restart=10, max_outer=60, coarse_tol=0.1, coarse_restart=40, coarse_maxiter=400),
+        amg="2-level: 4^4 aggregates Nv=24 (6^3x12 x 48); 20 setup iterations; SAP 4^4 x 2 x 3 MR; FGMRES(10) + "
+            "FP64 refinement; persistent coarse GMRES(40) to 0.1"),
+    "precision": dict(
+        name="precision-form 16^3x32, 12 point sources, mu=0.003",
+        L=(16, 16, 16, 32), eps=0.25, c_sw=1.0, seed=1, nrhs=12, rhs="point", mus=[0.003],
+        setup=dict(_AMG2),
+        solve=dict(tol=1e-10, restart=20, max_outer=40, coarse_tol=0.1, coarse_restart=40, coarse_maxiter=400),
+        amg="2-level: 4^4 aggregates Nv=24 (4^3x8 x 48); 20 setup iterations; SAP 4^4 x 2 x 3 MR; FGMRES(20) + "
+            "FP64 refinement; persistent coarse GMRES(40) to 0.1"),
+}
+HEADLINE = "largest"
 DIRAC_WORKLOAD = "fine twisted-mass Wilson-clover stencil, 16^3x32, 12 systems (FP32 bundle)"
+
+
+def rhs_for(wl, rank=0):
+    """The workload's right-hand sides, complex128 [nrhs, Lt, Lz, Ly, Lx, 4, 3]."""
+    L, n = wl["L"], wl["nrhs"]
+    if wl["rhs"] == "point":
+        return synth.point_sources(L)[:n]
+    if wl["rhs"] == "z2":
+        return synth.z2_spinors(L, n, seed=11 + rank)
+    return synth.gaussian_spinors(L, n, seed=11 + rank)
 
 
 def kappa_for(L, eps, seed):
@@ -170,7 +215,7 @@ def run_dirac(args, world, rank, local):
     import torch
     from paper_2201_03872_gb300 import tmamg as T
 
-    wl = WORKLOAD
+    wl = WORKLOADS["precision"]
     L = wl["L"]
     V = int(np.prod(L))
     nsys = wl["nrhs"]
@@ -180,7 +225,7 @@ def run_dirac(args, world, rank, local):
     ctx = T.tmamg_create(L, -1, stream.cuda_stream)
     T.tmamg_load_gauge(ctx, U)
     T.tmamg_set_operator(ctx, kappa, wl["c_sw"])
-    mu = np.full(nsys, wl["mu"])
+    mu = np.full(nsys, wl["mus"][0])
     x = synth.gaussian_spinors(L, nsys, seed=7 + rank).astype(np.complex64)
     nb = T.tmamg_bundle_bytes(ctx, nsys, 32)
     xf = torch.from_numpy(x.view(np.float32).copy()).cuda()
@@ -246,14 +291,6 @@ def run_dirac(args, world, rank, local):
     return line
 
 
-def setup_kw():
-    return dict(agg=(4, 4, 4, 4), nv=24, sap_block=(4, 4, 4, 4), sap_cycles=2, sap_mr_steps=3, setup_iters=20)
-
-
-def solve_kw():
-    return dict(tol=1e-10, restart=20, max_outer=40, coarse_tol=0.1, coarse_restart=40, coarse_maxiter=400)
-
-
 def measure_dirac(T, ctx, nsys, mu, steps, stream):
     """CUDA-event time of the fine FP32 stencil on a bundle of nsys systems (same stream)."""
     import torch
@@ -269,38 +306,93 @@ def measure_dirac(T, ctx, nsys, mu, steps, stream):
         T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32)
         b.record(stream)
     torch.cuda.synchronize()
-    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    del xb, yb
+    torch.cuda.empty_cache()
+    return ms
+
+
+class Problem:
+    """A workload on the GPU: context with gauge field, operator and multigrid setup, and the
+    right-hand sides and solution buffers on the device."""
+
+    def __init__(self, wl, rank, stream, setup_overrides=None):
+        import torch
+        from paper_2201_03872_gb300 import tmamg as T
+        self.T, self.wl, self.stream = T, wl, stream
+        L = wl["L"]
+        self.L, self.V = L, int(np.prod(L))
+        self.nrhs, self.mus = wl["nrhs"], list(wl["mus"])
+        self.nsys = self.nrhs * len(self.mus)
+        self.kappa, self.ksrc = kappa_for(L, wl["eps"], wl["seed"])
+        t = time.time()
+        self.U = synth.gauge_field(L, wl["eps"], seed=wl["seed"] + rank)
+        self.b = rhs_for(wl, rank)
+        self.input_seconds = time.time() - t
+        self.ctx = T.tmamg_create(L, -1, stream.cuda_stream)
+        T.tmamg_load_gauge(self.ctx, self.U)
+        T.tmamg_set_operator(self.ctx, self.kappa, wl["c_sw"])
+        torch.cuda.synchronize()
+        t = time.time()
+        T.tmamg_setup(self.ctx, T.setup_params(**dict(wl["setup"], **(setup_overrides or {}))))
+        torch.cuda.synchronize()
+        self.setup_seconds = time.time() - t
+        self.bd = torch.from_numpy(self.b.view(np.float64).copy()).cuda()
+        self.xd = torch.zeros(self.nsys * self.V * 24, dtype=torch.float64, device="cuda")
+
+    def params(self, **kw):
+        return self.T.solve_params(**dict(self.wl["solve"], **kw))
+
+    def solve(self, sp, nrhs=None):
+        nr = self.nrhs if nrhs is None else nrhs
+        rc, stats = self.T.tmamg_solve(self.ctx, self.bd, nr, self.mus, len(self.mus), self.xd, 1, sp)
+        ok = rc == 0 and all(q.status == 0 and q.true_rel_res <= self.wl["solve"]["tol"] for q in stats)
+        return ok, stats
+
+    def close(self):
+        self.T.tmamg_destroy(self.ctx)
+        import torch
+        del self.bd, self.xd
+        torch.cuda.empty_cache()
+
+
+def stats_summary(stats):
+    s0 = stats[0]
+    return {"outer": max(q.outer_iters for q in stats), "fgmres": max(q.inner_iters for q in stats),
+            "coarse": s0.coarse_iters, "max_true_rel_res": max(q.true_rel_res for q in stats)}
+
+
+def timed_solves(pb, sp, steps, stream, nrhs=None):
+    """CUDA-event time of `steps` solves after one untimed solve; (ms per solve, converged, stats)."""
+    import torch
+    pb.solve(sp, nrhs)
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ok = True
+    stats = None
+    for _ in range(steps):
+        okk, stats = pb.solve(sp, nrhs)
+        ok &= okk
+    z.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(z) / steps, ok, stats
 
 
 def run_solve(args, world, rank, local):
     import torch
     from paper_2201_03872_gb300 import tmamg as T
 
-    wl = WORKLOAD
-    L = wl["L"]
-    V = int(np.prod(L))
-    nrhs = wl["nrhs"]
-    mus = [wl["mu"]]
-    nsys = nrhs * len(mus)
-    kappa, ksrc = kappa_for(L, wl["eps"], wl["seed"])
-    U = synth.gauge_field(L, wl["eps"], seed=wl["seed"] + rank)
+    wl = WORKLOADS[args.workload]
     stream = torch.cuda.current_stream()
-    ctx = T.tmamg_create(L, -1, stream.cuda_stream)
-    T.tmamg_load_gauge(ctx, U)
-    T.tmamg_set_operator(ctx, kappa, wl["c_sw"])
-    t = time.time()
-    T.tmamg_setup(ctx, T.setup_params(**setup_kw()))
-    torch.cuda.synchronize()
-    setup_s = time.time() - t
-    b = synth.point_sources(L)
-    bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
-    xd = torch.zeros(nsys * V * 24, dtype=torch.float64, device="cuda")
-    sp = T.solve_params(**solve_kw())
+    pb = Problem(wl, rank, stream)
+    nsys, V = pb.nsys, pb.V
+    sp = pb.params()
     ok = True
-    iters = None
+    stats = None
     with Clocks(local) as clk:
         for _ in range(args.warmup):
-            T.tmamg_solve(ctx, bd, nrhs, mus, len(mus), xd, 1, sp)
+            pb.solve(sp)
         torch.cuda.synchronize()
         barrier(world)
         launches0 = T.tmamg_kernel_launches()  # kernels launched before the timed region (ncu -s)
@@ -310,169 +402,221 @@ def run_solve(args, world, rank, local):
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for k in range(args.steps):
-            rc, stats = T.tmamg_solve(ctx, bd, nrhs, mus, len(mus), xd, 1, sp)
-            ok &= rc == 0 and all(s.status == 0 and s.true_rel_res <= 1e-10 for s in stats)
-            iters = stats
+            okk, stats = pb.solve(sp)
+            ok &= okk
         t1.record(stream)
         torch.cuda.synchronize()
         clk.mark(h0, time.time())
     launches = T.tmamg_kernel_launches() - launches0
     total_ms = max_over_ranks(t0.elapsed_time(t1), world)
     solves_per_s = whole_job_rate(nsys * args.steps, world, total_ms)
-    # end to end through the public API with host buffers: b copied in, x copied out, every step
-    bh = np.ascontiguousarray(b)
-    xh = np.zeros((nrhs, len(mus)) + b.shape[1:], dtype=np.complex128)
+    # end to end through the public API with host buffers (page-locked): every step copies b in
+    # and x out inside tmamg_solve
+    bh_t = torch.from_numpy(pb.b.view(np.float64).copy()).pin_memory()
+    xh_t = torch.zeros(nsys * V * 24, dtype=torch.float64).pin_memory()
+    bh, xh = bh_t.numpy(), xh_t.numpy()
     torch.cuda.synchronize()
     t = time.perf_counter()
+    e2e_ok = True
     for k in range(args.steps):
-        T.tmamg_solve(ctx, bh, nrhs, mus, len(mus), xh, 0, sp)
+        rc, st_ = T.tmamg_solve(pb.ctx, bh, pb.nrhs, pb.mus, len(pb.mus), xh, 0, sp)
+        e2e_ok &= rc == 0
     e2e_s = max_over_ranks(time.perf_counter() - t, world)
     # the fine stencil (dominant hot kernel named by the metric), same context and systems
-    kern_ms = measure_dirac(T, ctx, nsys, np.full(nsys, wl["mu"]), 20, stream)
-    variants = {}
-    if args.variants:
-        # same workload, other forms of the method (each timed over the same number of steps)
-        def timed(label, nr, c=ctx, **kw):
-            spv = T.solve_params(**dict(solve_kw(), **kw))
-            T.tmamg_solve(c, bd, nr, mus, len(mus), xd, 1, spv)
-            torch.cuda.synchronize()
-            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            okv = True
-            for _ in range(args.steps):
-                rcv, stv = T.tmamg_solve(c, bd, nr, mus, len(mus), xd, 1, spv)
-                okv &= rcv == 0 and all(q.status == 0 for q in stv)
-            z.record(stream)
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(z) / args.steps
-            variants[label] = {"solves_per_s": nr * len(mus) / (ms * 1e-3), "ms_per_step": ms, "all_converged": okv,
-                               "fgmres_iterations": stv[0].inner_iters, "coarse_iterations": stv[0].coarse_iters}
-        def guarded(label, fn):
-            # a variant that fails is recorded as such; the headline line is still printed
-            try:
-                fn()
-            except Exception as exc:  # noqa: BLE001
-                variants[label] = {"error": f"{type(exc).__name__}: {exc}"}
-
-        guarded("single_system", lambda: timed("single_system", 1))
-        # the plain comparator: one system, every vector, operator and reduction in FP64
-        guarded("plain_fp64_single_system", lambda: timed("plain_fp64_single_system", 1, precision=64))
-        guarded("block_gmres_coarse", lambda: timed("block_gmres_coarse", nrhs, coarse_solver=1))
-
-        def three_level():
-            # a second coarsening (2^4 aggregates of the 4^3 x 8 level-1 lattice, Nv = 32), the middle level
-            # solved by FGMRES(10) to 7e-2 with the level-2 correction and 3 MR steps as its preconditioner
-            ctx3 = T.tmamg_create(L, -1, stream.cuda_stream)
-            try:
-                T.tmamg_load_gauge(ctx3, U)
-                T.tmamg_set_operator(ctx3, kappa, wl["c_sw"])
-                t = time.time()
-                T.tmamg_setup(ctx3, T.setup_params(levels=3, agg2=(2, 2, 2, 2), nv2=32, **setup_kw()))
-                torch.cuda.synchronize()
-                setup3 = time.time() - t
-                timed("three_level", nrhs, c=ctx3)
-                variants["three_level"]["setup_seconds"] = setup3
-            finally:
-                T.tmamg_destroy(ctx3)
-
-        guarded("three_level", three_level)
-
-        def learned_step():
-            t = time.time()
-            rep = T.tmamg_nn_train(ctx, T.tmamg_default_nn_params(pairs=48, batch=12, epochs=30, lr=2e-3,
-                                                                  mu=wl["mu"], gate_systems=4))
-            torch.cuda.synchronize()
-            timed("learned_step", nrhs, use_nn=2)
-            variants["learned_step"].update({"train_seconds": time.time() - t, "loss_first": rep.loss_first,
-                                             "loss_last": rep.loss_last, "gate_iterations_plain": rep.iters_plain,
-                                             "gate_iterations_with_step": rep.iters_nn,
-                                             "gate_enabled": bool(rep.enabled)})
-
-        guarded("learned_step", learned_step)
-    T.tmamg_destroy(ctx)
+    kern_ms = measure_dirac(T, pb.ctx, nsys, np.array([pb.mus[n % len(pb.mus)] for n in range(nsys)]), 10, stream)
     hbm, _, peak_src = read_peaks()
     bytes_per_apply = dirac_bytes_per_site(nsys, 32) * V
     achieved = bytes_per_apply / (kern_ms * 1e-3) / 1e9
-    s0 = iters[0]
+    fb32 = T.tmamg_bundle_bytes(pb.ctx, nsys, 32)
+    fb64 = T.tmamg_bundle_bytes(pb.ctx, nsys, 64)
+    m = wl["solve"]["restart"]
+    vec_bytes = (2 * m + 1 + 3) * fb32 + 2 * fb64 + pb.nrhs * V * 12 * 16
     line = {
         "metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "lattice": "16^3x32", "systems_per_step": nsys, "kappa": kappa,
-                   "kappa_source": ksrc, "c_sw": wl["c_sw"], "mu": wl["mu"], "tol": 1e-10,
-                   "amg": "2-level, 4^4 aggregates, Nv=24, 20 setup iterations, SAP 4^4 blocks x 2 cycles x 3 MR, "
-                          "FGMRES(20) + FP64 refinement, persistent coarse GMRES(40) to 0.1",
-                   "setup_seconds": setup_s, "all_converged": bool(ok),
-                   "iterations": {"outer": s0.outer_iters, "fgmres": s0.inner_iters, "coarse": s0.coarse_iters},
-                   "l2": "working set > 129 MB L2 (solver vectors 3+ GB)"},
+        "vs_baseline": None, "dtype": "f32+f16+f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "lattice": "x".join(str(v) for v in pb.L), "systems_per_step": nsys,
+                   "nrhs": pb.nrhs, "twisted_masses": pb.mus, "kappa": pb.kappa, "kappa_source": pb.ksrc,
+                   "c_sw": wl["c_sw"], "tol": wl["solve"]["tol"], "amg": wl["amg"],
+                   "precision": "FP32 fine stencil, SAP, transfers and inner FGMRES; FP16 coarse operators on the "
+                                "tensor cores with FP32 accumulation; FP64 outer residuals",
+                   "setup_seconds": pb.setup_seconds, "all_converged": bool(ok and e2e_ok),
+                   "iterations": stats_summary(stats),
+                   "solver_vector_bytes": int(vec_bytes),
+                   "l2": "inputs larger than the 129 MB L2 (one FP32 bundle %.1f GB)" % (fb32 / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": dirac_traffic(), "peak_source": peak_src, "kernel": "dirac_kernel<float,2> (fine stencil)",
+                     "traffic": dirac_traffic() if args.workload == "precision" else None, "peak_source": peak_src,
+                     "kernel": "dirac_kernel<float,2> (fine stencil, %d systems)" % nsys,
                      "algorithmic_bytes_per_launch": bytes_per_apply, "launch_ms": kern_ms},
         "e2e": {"value": whole_job_rate(nsys * args.steps, world, e2e_s * 1e3), "unit": "solves/s",
-                "h2d_bytes_per_step": int(bh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)},
+                "h2d_bytes_per_step": int(pb.b.nbytes), "d2h_bytes_per_step": int(nsys * V * 24 * 8)},
         "gpu_launches": int(launches),
         "launches_before_timed": int(launches0),
         "clocks": clk.result,
     }
-    if variants:
-        line["variants"] = variants
+    pb.close()
+    del bh_t, xh_t
+    if args.variants:
+        line["variants"] = run_variants(args, rank, stream)
     return line
 
 
-def cpu_solve_baseline(iters_per_solve=21, steps=0, warmup=0):
-    """The FP64 numpy oracle on the same lattice: one fine-level AMG iteration (operator
-    applications, SAP smoother, restriction and prolongation with a random P) for one system,
-    timed on the host cores; solves/s = 1 / (time per iteration x iterations per solve), with
-    the FGMRES iteration count of the GPU solver on this workload (21, or the count measured in
-    the same run). Setup and the coarse solve are left out, so this over-estimates the CPU rate.
-    With steps > 0 (the reference arm) the iteration is timed once to express it in oracle operator
-    applications, then warmup + steps operator applications are timed one by one and the rate uses
-    their mean, so that every step is a bounded sample (one application, about a second)."""
+def run_variants(args, rank, stream):
+    """Other workloads and other forms of the method, each timed with CUDA events; a variant that
+    fails is recorded with its error and the headline line is still printed."""
+    import torch
+    from paper_2201_03872_gb300 import tmamg as T
+    out = {}
+    steps = max(1, min(args.steps, args.variant_steps))
+
+    def guarded(label, fn):
+        try:
+            fn()
+        except Exception as exc:  # noqa: BLE001
+            out[label] = {"error": f"{type(exc).__name__}: {exc}"}
+
+    def record(label, pb, ms, ok, stats, nrhs=None, **extra):
+        nr = pb.nrhs if nrhs is None else nrhs
+        n = nr * len(pb.mus)
+        out[label] = dict({"workload": pb.wl["name"], "systems_per_step": n, "solves_per_s": n / (ms * 1e-3),
+                           "ms_per_step": ms, "steps": steps, "all_converged": bool(ok),
+                           "iterations": stats_summary(stats)}, **extra)
+
+    def batched():
+        pb = Problem(WORKLOADS["batched"], rank, stream)
+        try:
+            ms, ok, st_ = timed_solves(pb, pb.params(), steps, stream)
+            record("batched_multishift_40_systems", pb, ms, ok, st_, setup_seconds=pb.setup_seconds)
+            ms, ok, st_ = timed_solves(pb, pb.params(coarse_solver=1), steps, stream)
+            record("batched_multishift_block_gmres_coarse", pb, ms, ok, st_)
+        finally:
+            pb.close()
+
+    def precision():
+        pb = Problem(WORKLOADS["precision"], rank, stream)
+        try:
+            ms, ok, st_ = timed_solves(pb, pb.params(), steps, stream)
+            record("precision_form", pb, ms, ok, st_, setup_seconds=pb.setup_seconds)
+            guarded("single_system", lambda: record("single_system", pb, *timed_solves(pb, pb.params(), steps,
+                                                                                      stream, 1), nrhs=1))
+            # the plain comparator: one system, every vector, operator and reduction in FP64
+            guarded("plain_fp64_single_system", lambda: record(
+                "plain_fp64_single_system", pb, *timed_solves(pb, pb.params(precision=64), steps, stream, 1), nrhs=1))
+            guarded("block_gmres_coarse", lambda: record(
+                "block_gmres_coarse", pb, *timed_solves(pb, pb.params(coarse_solver=1), steps, stream)))
+
+            def learned():
+                t = time.time()
+                rep = T.tmamg_nn_train(pb.ctx, T.tmamg_default_nn_params(pairs=48, batch=12, epochs=30, lr=2e-3,
+                                                                          mu=pb.mus[0], gate_systems=4))
+                torch.cuda.synchronize()
+                record("learned_step", pb, *timed_solves(pb, pb.params(use_nn=2), steps, stream),
+                       train_seconds=time.time() - t, loss_first=rep.loss_first, loss_last=rep.loss_last,
+                       gate_iterations_plain=rep.iters_plain, gate_iterations_with_step=rep.iters_nn,
+                       gate_enabled=bool(rep.enabled))
+
+            guarded("learned_step", learned)
+        finally:
+            pb.close()
+
+        def three():
+            pb3 = Problem(WORKLOADS["precision"], rank, stream,
+                          dict(levels=3, agg2=(2, 2, 2, 2), nv2=32, setup_gmres_steps=20))
+            try:
+                sp = pb3.params(mid_tol=7e-2, mid_restart=10, mid_maxiter=50, mid_smooth=3)
+                record("precision_form_three_level", pb3, *timed_solves(pb3, sp, steps, stream),
+                       setup_seconds=pb3.setup_seconds)
+            finally:
+                pb3.close()
+
+        guarded("precision_form_three_level", three)
+
+    guarded("batched_multishift_40_systems", batched)
+    guarded("precision_form", precision)
+    return out
+
+
+def cores_used(fn):
+    """Run fn and return (result, wall seconds, threads it kept busy = process CPU time / wall time)."""
+    c0, t0 = time.process_time(), time.perf_counter()
+    r = fn()
+    wall = time.perf_counter() - t0
+    return r, wall, max(1, round((time.process_time() - c0) / max(wall, 1e-9)))
+
+
+def oracle_amg_iteration(wl, Ls):
+    """Closure timing one fine-level AMG iteration of the FP64 numpy oracle for one system on lattice Ls
+    with the workload's gauge recipe: the FGMRES operator application, restriction and prolongation with a
+    random P (Nv = 24, 4^4 aggregates), the residual and the SAP smoother (4^4 blocks, 2 cycles, 3 MR)."""
     from oracle import dirac, sap as osap, amg
-    wl = WORKLOAD
-    L = wl["L"]
-    kappa, _ = kappa_for(L, wl["eps"], wl["seed"])
-    U = synth.gauge_field(L, wl["eps"], seed=wl["seed"])
+    kappa, _ = kappa_for(wl["L"], wl["eps"], wl["seed"])
+    U = synth.gauge_field(Ls, wl["eps"], seed=wl["seed"])
     op = dirac.Operator(U, kappa, wl["c_sw"])
-    x = synth.gaussian_spinors(L, 1, seed=7)[0]
+    x = synth.gaussian_spinors(Ls, 1, seed=7)[0]
     bop = osap.BlockOperator(op, (4, 4, 4, 4))
-    Vt = synth.gaussian_spinors(L, 24, seed=8)
-    P = amg.Prolongation(amg.FineLevel.to_chi(Vt), L, (4, 4, 4, 4))
-    t = time.perf_counter()
-    y = op.apply(x, wl["mu"])                       # the FGMRES operator application
-    rc = P.restrict(amg.FineLevel.to_chi(y))
-    e = amg.FineLevel.to_spin(P.prolong(rc))
-    r2 = y - op.apply(e, wl["mu"])                  # residual for the smoother
-    e = e + osap.sap(op, r2, wl["mu"], (4, 4, 4, 4), cycles=2, mr_steps=3, bop=bop)
-    dt = time.perf_counter() - t
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    Vt = synth.gaussian_spinors(Ls, 24, seed=8)
+    P = amg.Prolongation(amg.FineLevel.to_chi(Vt), Ls, (4, 4, 4, 4))
+    mu = wl["mus"][0]
+
+    def it():
+        y = op.apply(x, mu)
+        rc = P.restrict(amg.FineLevel.to_chi(y))
+        e = amg.FineLevel.to_spin(P.prolong(rc))
+        r2 = y - op.apply(e, mu)
+        return e + osap.sap(op, r2, mu, (4, 4, 4, 4), cycles=2, mr_steps=3, bop=bop)
+
+    return it, op, x, mu
+
+
+def sample_lattice(L):
+    """The numpy oracle's bounded sample: the workload's own lattice up to 16^3 x 32 sites (one AMG
+    iteration there takes the oracle about 12 s), else 16^3 x 32 with the same gauge recipe, the
+    per-site cost being the same on any volume."""
+    if int(np.prod(L)) > 16 ** 3 * 32:
+        return (16, 16, 16, 32)
+    return tuple(L)
+
+
+def cpu_solve_baseline(wl, iters_per_solve, nsys, steps=0, warmup=0):
+    """The FP64 numpy oracle as it stands, one system at a time: one fine-level AMG iteration on a
+    bounded sample lattice, timed on the host, scaled by the volume ratio to the workload's lattice and
+    multiplied by the GPU solver's FGMRES iteration count. Setup and coarse solves are left out, so this
+    over-estimates the CPU rate. With steps > 0 (the reference arm) the iteration is expressed in oracle
+    operator applications once, then warmup + steps applications are timed one by one."""
+    Ls = sample_lattice(wl["L"])
+    scale = float(np.prod(wl["L"])) / float(np.prod(Ls))
+    it, op, x, mu = oracle_amg_iteration(wl, Ls)
+    _, dt, cores = cores_used(it)
+    lat = "x".join(str(v) for v in Ls)
     if steps <= 0:
-        return {"value": 1.0 / (dt * iters_per_solve), "unit": "solves/s", "cores": cores, "kind": "oracle",
-                "sample": f"one fine-level AMG iteration of the numpy FP64 oracle on 16^3x32 ({dt:.1f} s), times "
-                          f"{iters_per_solve} iterations per solve; setup and coarse solves excluded"}
+        per_solve = dt * scale * iters_per_solve
+        return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                "sample": f"numpy FP64 oracle, extrapolated: one fine-level AMG iteration for one system on {lat} "
+                          f"({dt:.1f} s wall, about {cores} busy thread(s)) x volume ratio {scale:g} x "
+                          f"{iters_per_solve} FGMRES iterations per solve; setup and coarse solves excluded"}
     t = time.perf_counter()
-    op.apply(x, wl["mu"])
-    per_iter = dt / (time.perf_counter() - t)  # one AMG iteration in operator applications
+    op.apply(x, mu)
+    per_iter = dt / (time.perf_counter() - t)
     times = []
     for k in range(warmup + steps):
         t = time.perf_counter()
-        op.apply(x, wl["mu"])
+        op.apply(x, mu)
         if k >= warmup:
             times.append(time.perf_counter() - t)
     t_op = float(np.mean(times))
-    return {"value": 1.0 / (t_op * per_iter * iters_per_solve), "unit": "solves/s", "cores": cores,
+    return {"value": 1.0 / (t_op * per_iter * scale * iters_per_solve), "unit": "solves/s", "cores": cores,
             "kind": "oracle",
-            "sample": f"numpy FP64 oracle on 16^3x32, one system: {warmup} + {steps} timed operator applications "
-                      f"(mean {t_op:.2f} s) x {per_iter:.1f} applications per fine-level AMG iteration (one "
-                      f"iteration timed, {dt:.1f} s: operator, restriction and prolongation with a random P, SAP) "
-                      f"x {iters_per_solve} iterations per solve; setup and coarse solves excluded"}
+            "sample": f"numpy FP64 oracle, extrapolated: {warmup} + {steps} timed operator applications on {lat} "
+                      f"(mean {t_op:.2f} s) x {per_iter:.1f} applications per fine-level AMG iteration x volume "
+                      f"ratio {scale:g} x {iters_per_solve} iterations per solve; about {cores} busy thread(s); "
+                      f"setup and coarse solves excluded"}
 
 
 def cpu_dirac_baseline(steps=0, warmup=0):
-    """The FP64 oracle operator on the same lattice (4 systems), timed on the host cores: about 8 s
-    of applications, or (the reference arm) warmup + steps applications timed one by one."""
+    """The FP64 oracle operator on the precision-form lattice (4 systems), timed on the host cores:
+    about 8 s of applications, or (the reference arm) warmup + steps applications timed one by one."""
     from oracle import dirac
-    wl = WORKLOAD
+    wl = WORKLOADS["precision"]
     L = wl["L"]
     V = int(np.prod(L))
     kappa, _ = kappa_for(L, wl["eps"], wl["seed"])
@@ -480,16 +624,19 @@ def cpu_dirac_baseline(steps=0, warmup=0):
     op = dirac.Operator(U, kappa, wl["c_sw"])
     nsys = 4
     x = synth.gaussian_spinors(L, nsys, seed=7)
-    mu = np.full(nsys, wl["mu"])
+    mu = np.full(nsys, wl["mus"][0])
     op.apply(x[:1], mu[:1])
+    c0 = time.process_time()
     if steps > 0:
         times = []
+        t_all = time.perf_counter()
         for k in range(warmup + steps):
             t = time.perf_counter()
             op.apply(x, mu)
             if k >= warmup:
                 times.append(time.perf_counter() - t)
         dt, reps = float(np.mean(times)), steps
+        wall = time.perf_counter() - t_all
     else:
         t = time.perf_counter()
         reps = 0
@@ -498,37 +645,46 @@ def cpu_dirac_baseline(steps=0, warmup=0):
             reps += 1
             if time.perf_counter() - t > 8.0:
                 break
-        dt = (time.perf_counter() - t) / reps
+        wall = time.perf_counter() - t
+        dt = wall / reps
+    cores = max(1, round((time.process_time() - c0) / max(wall, 1e-9)))
     gbs = dirac_bytes_per_site(nsys, 32) * V / dt / 1e9
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"numpy FP64 oracle D(mu) on 16^3x32 with {nsys} systems, {reps} applications; "
-                      "bytes counted with the same FP32 algorithmic formula as the GPU line"}
+            "sample": f"numpy FP64 oracle D(mu) on 16^3x32 with {nsys} systems, {reps} applications, about {cores} "
+                      "busy thread(s); bytes counted with the same FP32 algorithmic formula as the GPU line"}
+
+
+# FGMRES iterations per solve of the GPU solver on each workload (the CPU extrapolation of the
+# reference arm uses them when it runs without a GPU measurement beside it)
+ITERS_PER_SOLVE = {"largest": 30, "batched": 25, "precision": 21}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--what", default="solve", choices=["solve", "dirac"])
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
+    ap.add_argument("--variant-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
-                    help="skip the single-system, block-GMRES and learned-step forms")
+                    help="skip the other workloads and forms of the method")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_init()
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = (cpu_solve_baseline(steps=args.steps, warmup=args.warmup) if args.what == "solve"
+        wl = WORKLOADS[args.workload]
+        cb = (cpu_solve_baseline(wl, ITERS_PER_SOLVE[args.workload], wl["nrhs"] * len(wl["mus"]), steps=args.steps,
+                                 warmup=args.warmup) if args.what == "solve"
               else cpu_dirac_baseline(steps=args.steps, warmup=args.warmup))
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"], "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD["name"] if args.what == "solve" else
-                           DIRAC_WORKLOAD},
+                "config": {"workload": wl["name"] if args.what == "solve" else DIRAC_WORKLOAD},
                 "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -545,8 +701,10 @@ def main():
     line = run_solve(args, world, rank, local) if args.what == "solve" else run_dirac(args, world, rank, local)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = (cpu_solve_baseline(line["config"]["iterations"]["fgmres"]) if args.what == "solve"
-                                    else cpu_dirac_baseline())
+            wl = WORKLOADS[args.workload]
+            line["cpu_baseline"] = (cpu_solve_baseline(wl, line["config"]["iterations"]["fgmres"],
+                                                       line["config"]["systems_per_step"])
+                                    if args.what == "solve" else cpu_dirac_baseline())
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -122,6 +122,10 @@ void launch_convert_gauge(const Geom& g, const double* Uin, double2* U64, float2
 template <typename real>
 void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu, int nsys,
                   cudaStream_t st);
+// r_n = b_{n / nshift} - D(mu_n) x_n on FP64 bundles (one system per tile), b holding one tile
+// per right-hand side: the outer residual of the solver without a separate product buffer
+void launch_residual64(const Geom& g, const double2* U, const double* C, const double* x, const double* b, int nshift,
+                       double* r, const double* mu, int nsys, cudaStream_t st);
 template <typename real>
 void launch_pack(const Geom& g, const real* field, real* bundle, int nsys, cudaStream_t st);
 template <typename real>

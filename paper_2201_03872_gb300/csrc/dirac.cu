@@ -236,7 +236,8 @@ template <typename real, int T, int BX>
 __global__ void __launch_bounds__(sizeof(real) == 4 ? 192 : 256, sizeof(real) == 4 ? 2 : 1) dirac_kernel(const typename LinkT<real>::t* __restrict__ U,
                                                     const real* __restrict__ C, const real* __restrict__ x,
                                                     real* __restrict__ y, const double* __restrict__ mu, int nsys,
-                                                    int ntile, int Lx, int Ly, int Lz, int Lt, real bc_t) {
+                                                    int ntile, int Lx, int Ly, int Lz, int Lt, real bc_t,
+                                                    const real* __restrict__ bsub, int nshift) {
   const int64_t V = (int64_t)Lx * Ly * Lz * Lt;
   const int64_t s = blockIdx.x * (int64_t)BX + threadIdx.x;
   const int tile = blockIdx.y * blockDim.y + threadIdx.y;
@@ -316,6 +317,20 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 192 : 256, sizeof(real) ==
     }
     local_term<real, T>(acc, xt + s * 2 * T, V, C, V, s, m);
     real* yo = y + tile * tstride + s * 2 * T;
+    if (bsub) {
+      // residual form y = b - D x, with b stored once per right-hand side (tile / nshift)
+      const real* bo = bsub + (int64_t)(tile / nshift) * tstride + s * 2 * T;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        CV<real, T> bv;
+        ldcv(bv, bo + (int64_t)k * V * 2 * T);
+#pragma unroll
+        for (int l = 0; l < T; ++l) {
+          acc.c[k].re[l] = bv.re[l] - acc.c[k].re[l];
+          acc.c[k].im[l] = bv.im[l] - acc.c[k].im[l];
+        }
+      }
+    }
 #pragma unroll
     for (int k = 0; k < 12; ++k) stcv(yo + (int64_t)k * V * 2 * T, acc.c[k]);
   }
@@ -341,7 +356,18 @@ void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, re
   dim3 block(BX, ty);
   dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nt / ty));
   dirac_kernel<real, T, BX><<<grid, block, 0, st>>>(reinterpret_cast<const typename LinkT<real>::t*>(U), C, x, y, mu,
-                                                    nsys, nt, g.L[0], g.L[1], g.L[2], g.L[3], (real)g.bc_t); TM_COUNT();
+                                                    nsys, nt, g.L[0], g.L[1], g.L[2], g.L[3], (real)g.bc_t, nullptr,
+                                                    1); TM_COUNT();
+}
+
+void launch_residual64(const Geom& g, const double2* U, const double* C, const double* x, const double* b, int nshift,
+                       double* r, const double* mu, int nsys, cudaStream_t st) {
+  constexpr int BX = 64;
+  const int ty = pick_ty(nsys, BX, 256);
+  dim3 block(BX, ty);
+  dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nsys / ty));
+  dirac_kernel<double, 1, BX><<<grid, block, 0, st>>>(U, C, x, r, mu, nsys, nsys, g.L[0], g.L[1], g.L[2], g.L[3],
+                                                      (double)g.bc_t, b, nshift); TM_COUNT();
 }
 
 template void launch_dirac<float>(const Geom&, const void*, const float*, const float*, float*, const double*, int,

@@ -344,7 +344,7 @@ int sap_check_blocks(const Geom& g, const int bs[4], std::string& why) {
 }
 
 void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C32, float* r, float* e, float* delta,
-               const double* mu, int nsys, int cycles, int steps, cudaStream_t st) {
+               const double* mu, int nsys, int cycles, int steps, cudaStream_t st, bool accumulate) {
   SapDims d;
   int nblocks = 1;
   for (int k = 0; k < 4; ++k) {
@@ -361,7 +361,7 @@ void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C
   constexpr int T = Tile<float>::T;
   int nt = ntiles(nsys, T);
   size_t M = (size_t)12 * g.V * 2 * T * nt;
-  cudaMemsetAsync(e, 0, M * sizeof(float), st);
+  if (!accumulate) cudaMemsetAsync(e, 0, M * sizeof(float), st);
   const int nthreads = (d.bv + 31) / 32 * 32;  // one thread per block site
   const int nwarps = nthreads / 32;
   // links [4][9][bv] float2 + clover [72][bv] + rho [12][bv] float4 + reduction scratch

@@ -31,8 +31,10 @@ struct Workspace {
   size_t fb32 = 0, fb64 = 0, cb32 = 0;  // bytes of one bundle
   float* V = nullptr;                   // m + 1 fine FP32 bundles
   float* Z = nullptr;                   // m
-  float *t1 = nullptr, *t2 = nullptr, *t3 = nullptr, *e32 = nullptr;
-  double *x64 = nullptr, *r64 = nullptr, *b64 = nullptr, *t64 = nullptr;
+  float *t1 = nullptr, *t2 = nullptr, *t3 = nullptr, *e32 = nullptr;  // t2: learned step only (made on use)
+  double *x64 = nullptr, *r64 = nullptr;
+  double* b64 = nullptr;  // right-hand sides, one FP64 tile each (grown on demand)
+  size_t b64_bytes = 0;
   float* Vc = nullptr;  // mc + 1 coarse bundles
   float *xc = nullptr, *rc = nullptr;
   GmresState top, coarse;
@@ -64,7 +66,7 @@ static bool has_middle(const tmamg_ctx* ctx) { return ctx->levels.size() == 2; }
 
 static void ws_free(Workspace* w) {
   if (!w) return;
-  void* ptrs[] = {w->V, w->Z, w->t1, w->t2, w->t3, w->e32, w->x64, w->r64, w->b64, w->t64, w->Vc, w->xc, w->rc,
+  void* ptrs[] = {w->V, w->Z, w->t1, w->t2, w->t3, w->e32, w->x64, w->r64, w->b64, w->Vc, w->xc, w->rc,
                   w->rel_top, w->rel_coarse, w->rn, w->bn, w->scale, w->beta0, w->tmpd, w->ones, w->mones, w->dot,
                   w->partial64, w->mask, w->flags, w->count, w->outer_it, w->inner_it, w->Vm, w->Zm, w->xm,
                   w->rm, w->sm1, w->sm2, w->rel_mid, w->beta0m, w->mra, w->mrd};
@@ -154,13 +156,10 @@ static int ensure_ws(tmamg_ctx* ctx, int nsys, const tmamg_solve_params& p) {
   A((void**)&w->V, w->fb32 * (mm + 1));
   A((void**)&w->Z, w->fb32 * mm);
   A((void**)&w->t1, w->fb32);
-  A((void**)&w->t2, w->fb32);
   A((void**)&w->t3, w->fb32);
   A((void**)&w->e32, w->fb32);
   A((void**)&w->x64, w->fb64);
   A((void**)&w->r64, w->fb64);
-  A((void**)&w->b64, w->fb64);
-  A((void**)&w->t64, w->fb64);
   A((void**)&w->Vc, w->cb32 * (mcc + 1));
   A((void**)&w->xc, w->cb32);
   A((void**)&w->rc, w->cb32);
@@ -213,6 +212,27 @@ static int ensure_ws(tmamg_ctx* ctx, int nsys, const tmamg_solve_params& p) {
   return check_cuda(ctx, cudaGetLastError(), "workspace init");
 }
 
+// the second FP32 scratch bundle of the workspace (used by the learned step only)
+static int ensure_t2(tmamg_ctx* ctx) {
+  Workspace* w = ctx->ws;
+  if (w->t2) return TMAMG_OK;
+  return check_cuda(ctx, cudaMalloc(&w->t2, w->fb32), "cudaMalloc(learned-step scratch)");
+}
+
+// the right-hand sides as FP64 bundles, one tile each (nrhs <= the workspace's system count)
+static int ensure_b64(tmamg_ctx* ctx, int nrhs) {
+  Workspace* w = ctx->ws;
+  const size_t need = (size_t)nrhs * 12 * ctx->g.V * 2 * sizeof(double);
+  if (need <= w->b64_bytes) return TMAMG_OK;
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(w->b64);
+  w->b64 = nullptr;
+  w->b64_bytes = 0;
+  int rc = check_cuda(ctx, cudaMalloc(&w->b64, need), "cudaMalloc(right-hand sides)");
+  if (!rc) w->b64_bytes = need;
+  return rc;
+}
+
 // ------------------------------------------------------------------ setup
 static AggDims agg_dims(const Geom& g, const int agg[4]) {
   AggDims a;
@@ -253,26 +273,43 @@ static CoarseDims coarse_dims(const CoarseLevel& l) {
   return c;
 }
 
-// host-side counter-based start vectors: splitmix64 -> uniform -> Box-Muller (complex Gaussian)
-static uint64_t splitmix64(uint64_t z) {
+// counter-based start vectors: splitmix64 -> uniform -> Box-Muller (complex Gaussian), generated
+// on the device (element i of stream (seed, stream) uses counters 2 i and 2 i + 1 of its key)
+__host__ __device__ inline uint64_t splitmix64(uint64_t z) {
   z += 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
 
-// n complex Gaussian numbers (interleaved re, im) of the stream (seed, stream)
+__global__ void gaussian_kernel(uint64_t key, int64_t n, float2* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t a = splitmix64(key + 2 * (uint64_t)i), b = splitmix64(key + 2 * (uint64_t)i + 1);
+  const double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+  const double u2 = ((b >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  const double r = sqrt(-log(u1));  // variance 1/2 per component
+  out[i] = make_float2((float)(r * cos(2 * M_PI * u2)), (float)(r * sin(2 * M_PI * u2)));
+}
+
+// the same numbers on the host (small draws: the learned step's start weights and gate right-hand sides)
 static void host_gaussian(uint64_t seed, uint64_t stream, size_t n, std::vector<float>& out) {
   out.resize(2 * n);  // n complex numbers
-  uint64_t key = splitmix64(seed ^ stream);
+  const uint64_t key = splitmix64(seed ^ stream);
   for (size_t i = 0; i < n; ++i) {
-    uint64_t a = splitmix64(key + 2 * i), b = splitmix64(key + 2 * i + 1);
-    double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740992.0);
-    double u2 = ((b >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-    double r = sqrt(-log(u1));  // variance 1/2 per component
+    const uint64_t a = splitmix64(key + 2 * i), b = splitmix64(key + 2 * i + 1);
+    const double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+    const double u2 = ((b >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double r = sqrt(-log(u1));
     out[2 * i] = (float)(r * cos(2 * M_PI * u2));
     out[2 * i + 1] = (float)(r * sin(2 * M_PI * u2));
   }
+}
+
+// n complex Gaussian numbers of the stream (seed, stream) into out (device)
+static void device_gaussian(uint64_t seed, uint64_t stream, int64_t n, float2* out, cudaStream_t st) {
+  const uint64_t key = splitmix64(seed ^ stream);
+  gaussian_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(key, n, out); TM_COUNT();
 }
 
 __global__ void inv_sqrt_kernel(const double2* dot, double2* sc, int n) {
@@ -358,12 +395,9 @@ static int setup_level2(tmamg_ctx* ctx, const tmamg_setup_params* p, const float
     return check_cuda(ctx, e, "level-2 setup scratch");
   }
   if (!vec2_dev) {
-    std::vector<float> host;
-    host_gaussian(p->seed, 0x5eed2ULL, (size_t)nv2 * L1.Vc * nc1, host);
-    e = cudaMalloc(&field, host.size() * sizeof(float));
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(field, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host copy goes out of scope
+    const int64_t n = (int64_t)nv2 * L1.Vc * nc1;
+    e = cudaMalloc(&field, sizeof(float2) * n);
+    if (e == cudaSuccess) device_gaussian(p->seed, 0x5eed2ULL, n, reinterpret_cast<float2*>(field), st);
     if (e != cudaSuccess) {
       cleanup();
       return check_cuda(ctx, e, "level-2 start vectors");
@@ -494,12 +528,10 @@ int do_setup(tmamg_ctx* ctx, const tmamg_setup_params* p, const float* vec_field
   }
   // start / test vectors as an FP32 bundle
   float* field = nullptr;
-  std::vector<float> host;
   if (!vec_field_dev) {
-    host_gaussian(p->seed, 0x5eedULL, (size_t)nv * g.V * 12, host);
-    e = cudaMalloc(&field, host.size() * sizeof(float));
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(field, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    const int64_t n = (int64_t)nv * g.V * 12;
+    e = cudaMalloc(&field, sizeof(float2) * n);
+    if (e == cudaSuccess) device_gaussian(p->seed, 0x5eedULL, n, reinterpret_cast<float2*>(field), st);
     if (e != cudaSuccess) {
       cudaFree(field);
       cleanup();
@@ -785,9 +817,9 @@ static void amg_cycle(SolveCtx& S, const float* v, float* z) {
   }
   launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, z, w->t1, S.mu, nsys, st);
   axpby<float>(w->ones, 2, v, w->mones, 2, w->t1, M, nsys, nullptr, st);  // t1 = v - D z
-  sap_apply(ctx->g, ctx->sp.sap_block, ctx->U32, ctx->C32, w->t1, w->t2, w->t3, S.mu, nsys, ctx->sp.sap_cycles,
-            ctx->sp.sap_mr_steps, st);
-  axpby<float>(w->ones, 2, w->t2, w->ones, 2, z, M, nsys, nullptr, st);  // z += SAP
+  // z += SAP(t1): the block solver adds its corrections to z directly
+  sap_apply(ctx->g, ctx->sp.sap_block, ctx->U32, ctx->C32, w->t1, z, w->t3, S.mu, nsys, ctx->sp.sap_cycles,
+            ctx->sp.sap_mr_steps, st, true);
   if (S.nn && ctx->nn && ctx->nn->trained) {
     // learned step on the residual left by the smoother: z += N(v - D z)
     NNState& nns = *ctx->nn;
@@ -812,6 +844,16 @@ __global__ void expand_b_kernel(const double* __restrict__ b, double* __restrict
   double* dst = b64 + t * 2;
   dst[0] = src[0];
   dst[1] = src[1];
+}
+
+// r (FP64 bundle of nsys = nrhs * nshift systems) = the right-hand-side tiles b (one per rhs):
+// system n takes tile n / nshift; per = complex entries per tile
+__global__ void expand_rhs_kernel(const double2* __restrict__ b, double2* __restrict__ r, int nshift, int nsys,
+                                  int64_t per) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nsys * per) return;
+  const int n = (int)(t / per);
+  r[t] = b[(int64_t)(n / nshift) * per + t % per];
 }
 
 // norms -> masks, scales and inner tolerances; flags: 1 = non-finite
@@ -1078,6 +1120,7 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   if (sp->coarse_solver == 1 && nrhs > 16)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: block GMRES takes at most 16 right-hand sides per shift");
   int rc = ensure_ws(ctx, nsys, *sp);
+  if (!rc) rc = ensure_b64(ctx, nrhs);
   if (rc) return rc;
   Workspace* w = ctx->ws;
   const int64_t V = g.V;
@@ -1087,23 +1130,21 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   for (int n = 0; n < nsys; ++n) musys[n] = mu[n % nshift];
   rc = upload_mu(ctx, musys.data(), nsys);
   if (rc) return rc;
-  // b -> FP64 bundle (T = 1)
+  // b -> FP64 bundle with one tile per right-hand side (host input staged through x64, which
+  // holds nsys >= nrhs fields and is cleared right after)
   const double* bsrc = b;
-  double* bstage = nullptr;
   if (!on_device) {
-    size_t bytes = sizeof(double) * 2 * 12 * V * nrhs;
-    rc = check_cuda(ctx, cudaMalloc(&bstage, bytes), "cudaMalloc(b staging)");
-    if (rc) return rc;
-    cudaMemcpyAsync(bstage, b, bytes, cudaMemcpyHostToDevice, st);
-    bsrc = bstage;
+    cudaMemcpyAsync(w->x64, b, sizeof(double) * 2 * M * nrhs, cudaMemcpyHostToDevice, st);
+    bsrc = w->x64;
   }
-  expand_b_kernel<<<(unsigned)(((int64_t)nsys * M + 255) / 256), 256, 0, st>>>(bsrc, w->b64, nshift, nsys, V); TM_COUNT();
+  launch_pack<double>(g, bsrc, w->b64, nrhs, st);
+  expand_rhs_kernel<<<(unsigned)(((int64_t)nsys * M + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const double2*>(w->b64), reinterpret_cast<double2*>(w->r64), nshift, nsys, M); TM_COUNT();
   cudaMemsetAsync(w->x64, 0, w->fb64, st);
-  cudaMemcpyAsync(w->r64, w->b64, w->fb64, cudaMemcpyDeviceToDevice, st);
   cudaMemsetAsync(w->flags, 0, sizeof(int) * nsys, st);
   cudaMemsetAsync(w->outer_it, 0, sizeof(int) * nsys, st);
   cudaMemsetAsync(w->inner_it, 0, sizeof(int) * nsys, st);
-  mdot<double>(w->b64, 0, 1, w->b64, M, nsys, w->dot, nsys, w->partial64, st);
+  mdot<double>(w->r64, 0, 1, w->r64, M, nsys, w->dot, nsys, w->partial64, st);
   sqrt_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->bn, nsys); TM_COUNT();
   SolveCtx S{ctx, sp, nsys, ctx->mu_dev, 0};
   S.nshift = nshift;
@@ -1111,6 +1152,8 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   if (S.nn && (!ctx->nn || !ctx->nn->trained)) return set_err(ctx, TMAMG_ERR_STATE, "solve: no trained network");
   if (S.nn) {
     if (ctx->nn->alloc(ctx->g.V, nsys)) return set_err(ctx, TMAMG_ERR_OOM, "solve: network buffers");
+    rc = ensure_t2(ctx);
+    if (rc) return rc;
   }
   LevelOps fine;
   fine.M = M;
@@ -1131,11 +1174,8 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
     gmres_cycle<float>(w->top, fine, nsys, sp->restart, w->V, vstride, w->Z, w->e32, w->mask, w->rel_top, 1, false, st);
     add_iters_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->top.kconv, w->mask, w->inner_it, nsys); TM_COUNT();
     f32_axpy_f64(w->rn, w->e32, w->x64, M, nsys, w->mask, st);
-    launch_dirac<double>(g, ctx->U64, ctx->C64, w->x64, w->t64, ctx->mu_dev, nsys, st);
-    axpby<double>(w->ones, 2, w->b64, w->mones, 2, w->t64, M, nsys, nullptr, st);
-    double* tmp = w->r64;
-    w->r64 = w->t64;
-    w->t64 = tmp;
+    // r = b - D x in FP64 in one pass (the stencil's residual form)
+    launch_residual64(g, ctx->U64, ctx->C64, w->x64, w->b64, nshift, w->r64, ctx->mu_dev, nsys, st);
   }
   rc = check_cuda(ctx, cudaGetLastError(), "solve kernels");
   // final true residual per system (r64 holds b - D x for the current x)
@@ -1150,19 +1190,12 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   cudaMemcpyAsync(hflags.data(), w->flags, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(hout.data(), w->outer_it, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(hin.data(), w->inner_it, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st);
-  // x bundle (T = 1) -> x field [nrhs][nshift][V][12]
-  double* xdst = x;
-  double* xstage = nullptr;
-  size_t xbytes = sizeof(double) * 2 * 12 * V * nsys;
-  if (!on_device) {
-    cudaMalloc(&xstage, xbytes);
-    xdst = xstage;
-  }
-  launch_unpack<double>(g, w->x64, xdst, nsys, st);
-  if (!on_device) cudaMemcpyAsync(x, xstage, xbytes, cudaMemcpyDeviceToHost, st);
+  // x bundle (T = 1) -> x field [nrhs][nshift][V][12]; a host destination is staged through
+  // r64 (the residual is no longer needed: the final norms are in rn)
+  const size_t xbytes = sizeof(double) * 2 * 12 * V * nsys;
+  launch_unpack<double>(g, w->x64, on_device ? x : w->r64, nsys, st);
+  if (!on_device) cudaMemcpyAsync(x, w->r64, xbytes, cudaMemcpyDeviceToHost, st);
   cudaError_t se = cudaStreamSynchronize(st);
-  cudaFree(bstage);
-  cudaFree(xstage);
   if (!rc) rc = check_cuda(ctx, se, "solve");
   if (!rc && S.launch_error) rc = set_err(ctx, TMAMG_ERR_CUDA, "solve: cooperative coarse-solver launch failed");
   for (const CoarseLevel& l : ctx->levels)
@@ -1378,12 +1411,11 @@ static int nn_upload(tmamg_ctx* ctx, const double* W) {
 
 // gaussian FP32 fine bundle of nsys systems from the library's counter-based generator
 static int random_bundle(tmamg_ctx* ctx, uint64_t seed, int nsys, float* bundle) {
-  std::vector<float> host;
-  host_gaussian(seed, 0x5eedULL, (size_t)nsys * ctx->g.V * 12, host);
+  const int64_t n = (int64_t)nsys * ctx->g.V * 12;
   float* field = nullptr;
-  int rc = check_cuda(ctx, cudaMalloc(&field, host.size() * sizeof(float)), "cudaMalloc(random field)");
+  int rc = check_cuda(ctx, cudaMalloc(&field, sizeof(float2) * n), "cudaMalloc(random field)");
   if (rc) return rc;
-  cudaMemcpyAsync(field, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+  device_gaussian(seed, 0x5eedULL, n, reinterpret_cast<float2*>(field), ctx->stream);
   launch_pack<float>(ctx->g, field, bundle, nsys, ctx->stream);
   rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "random bundle");
   cudaFree(field);
@@ -1503,6 +1535,8 @@ int tmamg_nn_loss_grad(tmamg_ctx* ctx, const void* r_bundle, const void* e_bundl
   int rc = ensure_ws(ctx, nsys, def);
   if (rc) return rc;
   if (ctx->nn->alloc(ctx->g.V, nsys)) return set_err(ctx, TMAMG_ERR_OOM, "nn_loss_grad: buffers");
+  rc = ensure_t2(ctx);
+  if (rc) return rc;
   Workspace* w = ctx->ws;
   NNGeom ng = nn_geom(ctx);
   nn_forward(*ctx->nn, ng, ctx->U32, (const float*)r_bundle, w->t1, nsys, false, ctx->stream);
@@ -1536,6 +1570,8 @@ int tmamg_nn_train(tmamg_ctx* ctx, const tmamg_nn_params* p, tmamg_nn_report* re
   int rc = ensure_ws(ctx, nsys, sp);
   if (rc) return rc;
   if (nns.alloc(ctx->g.V, nsys)) return set_err(ctx, TMAMG_ERR_OOM, "nn_train: buffers");
+  rc = ensure_t2(ctx);
+  if (rc) return rc;
   Workspace* w = ctx->ws;
   std::vector<double> mus(nsys, p->mu);
   rc = upload_mu(ctx, mus.data(), nsys);

@@ -62,11 +62,50 @@ def normal(seed: int, stream: int, n: int) -> np.ndarray:
     return z[:n]
 
 
+def _uniform_at(base: np.uint64, idx: np.ndarray) -> np.ndarray:
+    """The uniform() values at counter offsets idx of a stream."""
+    with np.errstate(over="ignore"):
+        ctr = idx.astype(np.uint64) + base
+    bits = _splitmix64(ctr) >> np.uint64(11)
+    return (bits.astype(np.float64) + 1.0) * (1.0 / 9007199254740992.0)
+
+
+def _complex_normal_range(seed: int, stream: int, n: int, k0: int, k1: int, var: float) -> np.ndarray:
+    """Elements [k0, k1) of complex_normal(seed, stream, (n,), var), computed alone. In
+    normal(seed, stream, 2 n) the Box-Muller pair j takes its radius from uniform index j and its
+    angle from index n + j, and gives z[j] = r cos(th), z[n + j] = r sin(th); complex element k is
+    z[k] + i z[n + k]. Same arithmetic as the whole-array form, so any split gives the same numbers."""
+    base = _stream_base(seed, stream)
+    k = np.arange(k0, k1, dtype=np.int64)
+    u_r = _uniform_at(base, k)
+    u_t = _uniform_at(base, k + n)
+    r = np.sqrt(-2.0 * np.log(u_r))
+    th = 2.0 * np.pi * u_t
+    sc = np.sqrt(var / 2.0)
+    return (r * np.cos(th)) * sc + 1j * ((r * np.sin(th)) * sc)
+
+
+def _parallel_rows(n: int, fn, chunk: int = 1 << 20):
+    """Apply fn(k0, k1) over [0, n) in chunks on a thread pool (numpy releases the GIL in its
+    loops), returning the concatenation in order."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    bounds = [(a, min(a + chunk, n)) for a in range(0, n, chunk)]
+    if len(bounds) <= 1:
+        return fn(0, n)
+    workers = max(1, min(len(bounds), os.cpu_count() or 1, 32))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        parts = list(ex.map(lambda b: fn(*b), bounds))
+    return np.concatenate(parts)
+
+
 def complex_normal(seed: int, stream: int, shape, var: float = 1.0) -> np.ndarray:
     """Complex Gaussian with E|z|^2 = var (real and imaginary parts each var/2)."""
     n = int(np.prod(shape))
-    z = normal(seed, stream, 2 * n) * np.sqrt(var / 2.0)
-    return (z[:n] + 1j * z[n:]).reshape(shape)
+    if n <= (1 << 20):
+        z = normal(seed, stream, 2 * n) * np.sqrt(var / 2.0)
+        return (z[:n] + 1j * z[n:]).reshape(shape)
+    return _parallel_rows(n, lambda a, b: _complex_normal_range(seed, stream, n, a, b, var)).reshape(shape)
 
 
 def lattice_shape(L):
@@ -74,23 +113,45 @@ def lattice_shape(L):
     return (Lt, Lz, Ly, Lx)
 
 
-def gauge_field(L, eps: float, seed: int = 1) -> np.ndarray:
-    """Random SU(3) links U = exp(i eps H), reunitarised.
-
-    H = (A + A^dagger)/2 - tr/3 with A complex Gaussian entries (Re, Im each of
-    variance 1/2); the exponential is taken through the eigendecomposition of H.
-    Returns complex128 [Lt, Lz, Ly, Lx, 4, 3, 3].
-    """
-    shp = lattice_shape(L) + (4,)
-    nlink = int(np.prod(shp))
-    A = complex_normal(seed, 101, (nlink, 3, 3), var=1.0)
+def _links(seed: int, eps: float, nlink: int, a: int, b: int) -> np.ndarray:
+    """Links [a, b) of the recipe below: their Gaussian matrices are elements [9 a, 9 b) of the
+    stream, so every split of the links gives the same field."""
+    A = _complex_normal_range(seed, 101, 9 * nlink, 9 * a, 9 * b, 1.0).reshape(b - a, 3, 3)
     H = 0.5 * (A + np.conj(np.swapaxes(A, -1, -2)))
     tr = np.trace(H, axis1=-2, axis2=-1).real / 3.0
     H = H - tr[:, None, None] * np.eye(3)
     lam, Q = np.linalg.eigh(H)
     ph = np.exp(1j * eps * lam)
-    U = np.einsum("nab,nb,ncb->nac", Q, ph, np.conj(Q))
-    U = reunitarise(U)
+    return reunitarise((Q * ph[:, None, :]) @ np.conj(np.swapaxes(Q, -1, -2)))
+
+
+def gauge_field(L, eps: float, seed: int = 1, chunk: int = 1 << 17, processes: int | None = None) -> np.ndarray:
+    """Random SU(3) links U = exp(i eps H), reunitarised.
+
+    H = (A + A^dagger)/2 - tr/3 with A complex Gaussian entries (Re, Im each of
+    variance 1/2); the exponential is taken through the eigendecomposition of H.
+    Returns complex128 [Lt, Lz, Ly, Lx, 4, 3, 3].
+
+    Large fields are made in chunks of `chunk` links on a pool of spawned processes (by default
+    one per core when there are more than 16 chunks); the result does not depend on the split.
+    """
+    import os
+    shp = lattice_shape(L) + (4,)
+    nlink = int(np.prod(shp))
+    bounds = [(a, min(a + chunk, nlink)) for a in range(0, nlink, chunk)]
+    if processes is None:
+        processes = (os.cpu_count() or 1) if len(bounds) > 16 else 1
+    if processes <= 1 or len(bounds) == 1:
+        U = np.concatenate([_links(seed, eps, nlink, a, b) for a, b in bounds])
+    else:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        U = np.empty((nlink, 3, 3), dtype=np.complex128)
+        with ProcessPoolExecutor(max_workers=min(processes, len(bounds)),
+                                 mp_context=mp.get_context("spawn")) as ex:
+            futs = [(a, b, ex.submit(_links, seed, eps, nlink, a, b)) for a, b in bounds]
+            for a, b, f in futs:
+                U[a:b] = f.result()
     return U.reshape(shp + (3, 3))
 
 

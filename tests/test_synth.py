@@ -44,3 +44,16 @@ def test_z2_noise_and_point_sources():
     assert np.allclose(b.reshape(12, -1).sum(axis=1), 1.0)
     mus = synth.log_shifts(10)
     assert np.isclose(mus[0], 1e-3) and np.isclose(mus[-1], 1e-1)
+
+
+def test_split_generation_gives_the_same_numbers():
+    # large inputs are generated in chunks (threads for Gaussian vectors, spawned processes for
+    # links); every split must reproduce the whole-array recipe exactly
+    import numpy as np
+    n = (1 << 20) + 777
+    z = synth.normal(5, 9, 2 * n) * np.sqrt(0.5)
+    assert np.array_equal(synth.complex_normal(5, 9, (n,)), z[:n] + 1j * z[n:])
+    L = (4, 4, 4, 8)
+    whole = synth.gauge_field(L, 0.3, seed=2, chunk=1 << 20, processes=1)
+    split = synth.gauge_field(L, 0.3, seed=2, chunk=500, processes=2)
+    assert np.array_equal(whole, split)

@@ -291,6 +291,41 @@ def run_dirac(args, world, rank, local):
     return line
 
 
+def run_sap(args, world, rank, local):
+    """The SAP smoother alone on the precision-form lattice and systems (diagnostic mode: one colour
+    sweep pair per cycle, 4^4 blocks, 2 cycles, 3 MR steps), for profiling the block solver."""
+    import torch
+    from paper_2201_03872_gb300 import tmamg as T
+    wl = WORKLOADS["precision"]
+    L = wl["L"]
+    nsys = wl["nrhs"]
+    kappa, _ = kappa_for(L, wl["eps"], wl["seed"])
+    stream = torch.cuda.current_stream()
+    ctx = T.tmamg_create(L, -1, stream.cuda_stream)
+    T.tmamg_load_gauge(ctx, synth.gauge_field(L, wl["eps"], seed=wl["seed"] + rank))
+    T.tmamg_set_operator(ctx, kappa, wl["c_sw"])
+    nb = T.tmamg_bundle_bytes(ctx, nsys, 32)
+    r0 = torch.randn(nb // 4, dtype=torch.float32, device="cuda")
+    r = torch.empty_like(r0)
+    e = torch.empty_like(r0)
+    mu = np.full(nsys, wl["mus"][0])
+    blk = wl["setup"]["sap_block"]
+    for _ in range(args.warmup):
+        r.copy_(r0)
+        T.tmamg_sap(ctx, r, e, nsys, mu, blk, 2, 3)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        r.copy_(r0)
+        T.tmamg_sap(ctx, r, e, nsys, mu, blk, 2, 3)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t) * 1e3 / args.steps
+    T.tmamg_destroy(ctx)
+    return {"metric": "SAP smoother applications/s (diagnostic)", "value": 1e3 / ms, "unit": "applications/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "data": "synthetic", "config": {"workload": "SAP 4^4 blocks x 2 cycles x 3 MR on 16^3x32, 12 systems"}}
+
+
 def measure_dirac(T, ctx, nsys, mu, steps, stream):
     """CUDA-event time of the fine FP32 stencil on a bundle of nsys systems (same stream)."""
     import torch
@@ -379,6 +414,65 @@ def timed_solves(pb, sp, steps, stream, nrhs=None):
     return a.elapsed_time(z) / steps, ok, stats
 
 
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
+FP64_PEAK_TFLOPS = 1.25                                   # GB300 nominal FP64 (non-tensor)
+DIRAC_FLOP_PER_SITE_SYSTEM = 1896                         # hops 1320 + clover 2 x 252 + twist/diag 48 + combine 24
+
+
+def kernel_profile(pb, sp, stream):
+    """One more solve with the library's per-kernel event timing on: {kernel: (launches, ms)} and the
+    solve's own CUDA-event time."""
+    import torch
+    T = pb.T
+    T.tmamg_profile_enable(1)
+    try:
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ok, stats = pb.solve(sp)
+        z.record(stream)
+        torch.cuda.synchronize()
+        rec = T.tmamg_profile_report()
+    finally:
+        T.tmamg_profile_enable(0)
+    return rec, a.elapsed_time(z), stats
+
+
+def kernel_rooflines(pb, rec, total_ms, stats):
+    """Per-kernel time share of one profiled solve and, where an algorithmic count is defined, the
+    achieved rate against its peak (HBM copy bandwidth, FP32 or FP64 ALU rate)."""
+    hbm, _, peak_src = read_peaks()
+    V, N = pb.V, pb.nsys
+    st = pb.wl["setup"]
+    nv = st["nv"]
+    asz = int(np.prod(st["agg"]))
+    steps = pb.wl["setup"].get("sap_mr_steps", 3)
+    out = {}
+    for name, (cnt, ms) in sorted(rec.items(), key=lambda kv: -kv[1][1]):
+        e = {"launches": cnt, "ms": ms, "share": ms / total_ms, "ms_per_launch": ms / max(cnt, 1)}
+        per = ms / max(cnt, 1) * 1e-3
+        if name == "dirac_f32":
+            b = dirac_bytes_per_site(N, 32) * V
+            e.update(bound="hbm", algorithmic_bytes_per_launch=b, achieved=b / per / 1e9, peak=hbm, unit="GB/s")
+        elif name == "residual_f64":
+            f = DIRAC_FLOP_PER_SITE_SYSTEM * V * N
+            e.update(bound="alu", algorithmic_flops_per_launch=f, achieved=f / per / 1e12, peak=FP64_PEAK_TFLOPS,
+                     unit="TFLOP/s", peak_source="nominal GB300 FP64")
+        elif name in ("restrict", "prolong"):
+            # P (FP32 complex, 12 Nv per site) plus the fine vectors (FP32, 96 B per site and system)
+            b = V * (12 * nv * 8 + 96 * N)
+            e.update(bound="hbm", algorithmic_bytes_per_launch=b, achieved=b / per / 1e9, peak=hbm, unit="GB/s")
+        elif name == "sap_mr":
+            # one colour sweep: half the sites, `steps` block-operator applications per system
+            f = DIRAC_FLOP_PER_SITE_SYSTEM * (V // 2) * N * steps
+            e.update(bound="alu", algorithmic_flops_per_launch=f, achieved=f / per / 1e12,
+                     peak=FP32_ALU_PEAK_TFLOPS, unit="TFLOP/s", peak_source="152 SMs x 128 FP32 lanes x 2 x 2070 MHz")
+        if "achieved" in e:
+            e["frac"] = e["achieved"] / e["peak"]
+            e.setdefault("peak_source", peak_src)
+        out[name] = e
+    return out
+
+
 def run_solve(args, world, rank, local):
     import torch
     from paper_2201_03872_gb300 import tmamg as T
@@ -422,7 +516,10 @@ def run_solve(args, world, rank, local):
         rc, st_ = T.tmamg_solve(pb.ctx, bh, pb.nrhs, pb.mus, len(pb.mus), xh, 0, sp)
         e2e_ok &= rc == 0
     e2e_s = max_over_ranks(time.perf_counter() - t, world)
-    # the fine stencil (dominant hot kernel named by the metric), same context and systems
+    # per-kernel shares of one more (profiled) solve, and the fine stencil (the operator the metric
+    # names) timed alone on the same context and systems
+    rec, prof_ms, prof_stats = kernel_profile(pb, sp, stream)
+    kernels = kernel_rooflines(pb, rec, prof_ms, prof_stats)
     kern_ms = measure_dirac(T, pb.ctx, nsys, np.array([pb.mus[n % len(pb.mus)] for n in range(nsys)]), 10, stream)
     hbm, _, peak_src = read_peaks()
     bytes_per_apply = dirac_bytes_per_site(nsys, 32) * V
@@ -444,10 +541,12 @@ def run_solve(args, world, rank, local):
                    "iterations": stats_summary(stats),
                    "solver_vector_bytes": int(vec_bytes),
                    "l2": "inputs larger than the 129 MB L2 (one FP32 bundle %.1f GB)" % (fb32 / 1e9)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+        "roofline": dominant_roofline(kernels),
+        "dirac_op": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": dirac_traffic() if args.workload == "precision" else None, "peak_source": peak_src,
-                     "kernel": "dirac_kernel<float,2> (fine stencil, %d systems)" % nsys,
+                     "kernel": "dirac_kernel<float,2> (fine stencil, %d systems, timed alone)" % nsys,
                      "algorithmic_bytes_per_launch": bytes_per_apply, "launch_ms": kern_ms},
+        "kernels": {"profiled_solve_ms": prof_ms, "by_kernel": kernels},
         "e2e": {"value": whole_job_rate(nsys * args.steps, world, e2e_s * 1e3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(pb.b.nbytes), "d2h_bytes_per_step": int(nsys * V * 24 * 8)},
         "gpu_launches": int(launches),
@@ -459,6 +558,24 @@ def run_solve(args, world, rank, local):
     if args.variants:
         line["variants"] = run_variants(args, rank, stream)
     return line
+
+
+def dominant_roofline(kernels):
+    """The roofline entry of the kernel with the largest time share that has an algorithmic count."""
+    best = None
+    for name, e in kernels.items():
+        if "achieved" in e and (best is None or e["share"] > kernels[best]["share"]):
+            best = name
+    if best is None:
+        return None
+    e = kernels[best]
+    r = {k: e[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_source")}
+    r.update(kernel=best, share_of_solve=e["share"], launches_in_solve=e["launches"], launch_ms=e["ms_per_launch"],
+             traffic=None)
+    for k in ("algorithmic_bytes_per_launch", "algorithmic_flops_per_launch"):
+        if k in e:
+            r[k] = e[k]
+    return r
 
 
 def run_variants(args, rank, stream):
@@ -665,7 +782,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--what", default="solve", choices=["solve", "dirac"])
+    ap.add_argument("--what", default="solve", choices=["solve", "dirac", "sap"])
     ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
     ap.add_argument("--variant-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -698,9 +815,10 @@ def main():
         torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
-    line = run_solve(args, world, rank, local) if args.what == "solve" else run_dirac(args, world, rank, local)
+    run = {"solve": run_solve, "dirac": run_dirac, "sap": run_sap}[args.what]
+    line = run(args, world, rank, local)
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline and world == 1 and args.what != "sap":
             wl = WORKLOADS[args.workload]
             line["cpu_baseline"] = (cpu_solve_baseline(wl, line["config"]["iterations"]["fgmres"],
                                                        line["config"]["systems_per_step"])

@@ -295,6 +295,18 @@ int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* x
 
 /* ------------------------------------------------------------------ diagnostics */
 
+/* Per-kernel timing (process-wide, off by default; no counterpart in the paper). With on != 0
+ * the main launch sites of the library (fine stencil and FP64 residual, SAP block solver and
+ * face update, restriction, prolongation, coarse stencils, persistent coarse GMRES, the BLAS-1
+ * kernels) record a pair of CUDA events on their stream around each launch; every call clears
+ * what was recorded. Always returns TMAMG_OK. */
+int tmamg_profile_enable(int on);
+
+/* Writes the record as NUL-terminated JSON text {"name": [launches, total_ms], ...} into buf,
+ * after waiting for the recorded events. Returns the text length, or TMAMG_ERR_ARG if buf is
+ * NULL or len is shorter than the text plus its terminator. */
+int tmamg_profile_report(char* buf, size_t len);
+
 /* Failure-path test hook (no counterpart in the paper). Sets, for the whole process, the bound
  * in SM clock cycles of the grid-barrier waits of the persistent coarse GMRES kernel
  * (limit_cycles; 0 restores the default of 2e9 cycles, about one second at 2 GHz). If

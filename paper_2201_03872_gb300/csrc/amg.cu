@@ -12,6 +12,7 @@
 // Coarse stencil: float2 A[9][Vc][nc (column j)][nc (row i)], hop index 0 = self,
 // 1 + 2 nu = +nu, 2 + 2 nu = -nu.
 #include "amg.cuh"
+#include "profile.cuh"
 #include "stencil.cuh"
 
 namespace tmamg {
@@ -245,6 +246,7 @@ void restrict_vec(const AggDims& g, const float2* P, const float* r, float* xc, 
   while (kc > RS_KS && sizeof(float4) * (size_t)nt * kc + sizeof(int) * g.asize > 190 * 1024) kc -= RS_KS;
   const size_t smem = sizeof(float4) * (size_t)nt * kc + sizeof(int) * g.asize;
   func_smem_optin((const void*)restrict_kernel, 200 * 1024);
+  TM_PROF(st, d == 6 ? "restrict" : "restrict_coarse");
   restrict_kernel<<<(unsigned)(g.Vc * 2), RS_THREADS, smem, st>>>(P, r, xc, g, nv, d, nt, kc);
   TM_COUNT();
 }
@@ -324,6 +326,7 @@ __global__ void __launch_bounds__(RP_THREADS) prolong_kernel(const float2* __res
 
 void prolong_vec(const AggDims& g, const float2* P, const float* xc, float* e, int nv, int d, int nsys, int accumulate,
                  cudaStream_t st) {
+  TM_PROF(st, d == 6 ? "prolong" : "prolong_coarse");
   const int nt = ntiles(nsys, T2);
   prolong_kernel<<<(unsigned)(g.Vc * 2), RP_THREADS, sizeof(int) * g.asize, st>>>(P, xc, e, g, nv, d, nt, accumulate);
   TM_COUNT();
@@ -380,6 +383,7 @@ __global__ void coarse_apply_kernel(const float2* __restrict__ A, const float* _
 
 void coarse_apply(const CoarseDims& cd, const float2* A, const float* x, float* y, const double* mu, double dmu,
                   int nsys, cudaStream_t st) {
+  TM_PROF(st, "coarse_apply_f32");
   int nt = ntiles(nsys, T2);
   int64_t total = cd.Vc * cd.nc;
   coarse_apply_kernel<<<dim3((unsigned)((total + 127) / 128), nt), 128, 0, st>>>(A, x, y, mu, dmu, nsys, cd); TM_COUNT();

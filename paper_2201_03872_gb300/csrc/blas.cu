@@ -6,6 +6,7 @@
 // (the paper attributes most of the block-solver overhead to global reductions, Sec. 4;
 // on one GPU they are on-device two-pass sums with no host involvement).
 #include "blas.cuh"
+#include "profile.cuh"
 
 namespace tmamg {
 
@@ -125,6 +126,7 @@ static int red_blocks(int64_t M, int ntile) {
 template <typename real>
 void mdot(const real* V, int64_t vstride, int k, const real* w, int64_t M, int nsys, double2* out, int64_t ostride,
           double2* partial, cudaStream_t st) {
+  TM_PROF(st, "mdot");
   constexpr int T = Tile<real>::T;
   int nt = ntiles(nsys, T);
   int nblk = red_blocks(M, nt);
@@ -214,6 +216,7 @@ static dim3 upd_grid(int64_t M, int nt, int bs) {
 template <typename real>
 void maxpy(const real* V, int64_t vstride, int k, const double2* c, int64_t cstride, double sign, real* y, int64_t M,
            int nsys, const int* mask, cudaStream_t st) {
+  TM_PROF(st, "maxpy");
   constexpr int T = Tile<real>::T;
   int nt = ntiles(nsys, T);
   if (k <= MAXPY_K)
@@ -270,6 +273,7 @@ __global__ void axpby_kernel(const double2* __restrict__ a, const real* __restri
 template <typename real>
 void axpby(const double2* a, int amode, const real* x, const double2* b, int bmode, real* y, int64_t M, int nsys,
            const int* mask, cudaStream_t st) {
+  TM_PROF(st, "axpby");
   constexpr int T = Tile<real>::T;
   int nt = ntiles(nsys, T);
   axpby_kernel<real, T><<<upd_grid(M, nt, 256), 256, 0, st>>>(a, x, b, y, M, nsys, mask, amode, bmode); TM_COUNT();
@@ -300,6 +304,7 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ x64, const double* 
 }
 
 void f64_to_f32(const double* x64, const double* s, float* x32, int64_t M, int nsys, cudaStream_t st) {
+  TM_PROF(st, "f64_to_f32");
   int nt = ntiles(nsys, 2);
   f64_to_f32_kernel<<<dim3((unsigned)((M + 255) / 256), nt), 256, 0, st>>>(x64, s, x32, M, nsys); TM_COUNT();
 }
@@ -324,6 +329,7 @@ __global__ void f32_axpy_f64_kernel(const double* __restrict__ s, const float* _
 
 void f32_axpy_f64(const double* s, const float* x32, double* x64, int64_t M, int nsys, const int* mask,
                   cudaStream_t st) {
+  TM_PROF(st, "f32_axpy_f64");
   f32_axpy_f64_kernel<<<dim3((unsigned)((M + 255) / 256), nsys), 256, 0, st>>>(s, x32, x64, M, nsys, mask); TM_COUNT();
 }
 

@@ -24,6 +24,7 @@
 #include <cmath>
 
 #include "amg.cuh"
+#include "profile.cuh"
 #include "coarse_gmres.cuh"
 #include "coarse_mma.cuh"
 
@@ -923,6 +924,7 @@ int coarse_gmres_solve(CoarseGmres& s, const CoarseDims& cd, const float2* A, co
   cudaMemsetAsync(s.bar, 0, sizeof(unsigned) * 2, st);
   cudaMemsetAsync(s.err, 0, sizeof(int), st);
   void* args[] = {&p};
+  TM_PROF(st, "coarse_gmres");
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)coarse_gmres_kernel, dim3(G), dim3(CG_THREADS), args,
                                               dyn, st);
   TM_COUNT();

@@ -1,6 +1,7 @@
 // Coarse stencil on the tensor cores: operator packing, per-system range scan and the
 // stand-alone launch of the stencil phase (coarse_mma.cuh holds the phase itself).
 #include "coarse_mma.cuh"
+#include "profile.cuh"
 
 namespace tmamg {
 
@@ -97,6 +98,7 @@ size_t cm_dyn_cap(const void* kernel) {
 
 int coarse_apply_f16(const CoarseDims& cd, const __half* A16, const float* x, float* y, const double* mu, double dmu,
                      int nsys, float* mx, __half* X16, int* err, cudaStream_t st) {
+  TM_PROF(st, "coarse_apply_f16");
   const int sms = device_sms();
   const size_t cap = cm_dyn_cap((const void*)coarse_mma_kernel);
   func_smem_optin((const void*)coarse_mma_kernel, (int)cap);

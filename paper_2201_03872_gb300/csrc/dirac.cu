@@ -13,6 +13,7 @@
 // projection in the chiral basis halves the SU(3) work: each hop multiplies
 // two colour vectors.
 #include "stencil.cuh"
+#include "profile.cuh"
 
 namespace tmamg {
 
@@ -351,6 +352,7 @@ void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, re
   // FP32: 32 sites x up to 6 tiles per CTA, so a site's links and clover are read once per CTA
   constexpr int BX = sizeof(real) == 4 ? 32 : 64;
   constexpr int MAXT = sizeof(real) == 4 ? 192 : 256;
+  TM_PROF(st, sizeof(real) == 4 ? "dirac_f32" : "dirac_f64");
   int nt = ntiles(nsys, T);
   int ty = pick_ty(nt, BX, MAXT);
   dim3 block(BX, ty);
@@ -362,6 +364,7 @@ void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, re
 
 void launch_residual64(const Geom& g, const double2* U, const double* C, const double* x, const double* b, int nshift,
                        double* r, const double* mu, int nsys, cudaStream_t st) {
+  TM_PROF(st, "residual_f64");
   constexpr int BX = 64;
   const int ty = pick_ty(nsys, BX, 256);
   dim3 block(BX, ty);

@@ -13,6 +13,7 @@
 // residual on the other colour changes only through hops that cross a block face: a
 // second kernel subtracts those hops, so SAP needs no full-lattice operator application.
 #include "sap.cuh"
+#include "profile.cuh"
 #include "stencil.cuh"
 
 namespace tmamg {
@@ -376,11 +377,13 @@ void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C
       const int nitems = nb_c * nt;
       if (nitems > 0) {
         const int grid = nitems < sms ? nitems : sms;
+        TM_PROF(st, "sap_mr");
         sap_mr_kernel<<<grid, nthreads, smem, st>>>(U32, C32, r, delta, e, mu, nsys, d, colour, steps, nitems, nt);
         TM_COUNT();
       }
       bool last = (cy == cycles - 1) && colour == 1;
       if (!last) {
+        TM_PROF(st, "sap_face");
         sap_face_kernel<float, T><<<dim3((unsigned)((g.V + 255) / 256), nt), 256, 0, st>>>(U32, delta, r, d,
                                                                                           1 - colour, nt); TM_COUNT();
       }

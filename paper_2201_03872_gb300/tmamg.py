@@ -112,6 +112,8 @@ SIGNATURES = {
     "tmamg_nn_loss_grad": (I, [P, P, P, I, ctypes.POINTER(ctypes.c_double), P]),
     "tmamg_nn_train": (I, [P, ctypes.POINTER(NNParams), ctypes.POINTER(NNReport)]),
     "tmamg_debug_bounded_wait": (I, [ctypes.c_longlong, I]),
+    "tmamg_profile_enable": (I, [I]),
+    "tmamg_profile_report": (I, [ctypes.c_char_p, ctypes.c_size_t]),
 }
 
 
@@ -311,6 +313,22 @@ def tmamg_coarse_solve(ctx, level, rc_bundle, xc_bundle, nrhs, mu, nshift, param
                                                                 int(nrhs), _ptr(m), int(nshift), ctypes.byref(params),
                                                                 ctypes.byref(it)))
     return it.value
+
+
+def tmamg_profile_enable(on):
+    """Per-kernel CUDA-event timing of the library's launches (process-wide); clears the record."""
+    return lib().tmamg_profile_enable(int(bool(on)))
+
+
+def tmamg_profile_report():
+    """{kernel: (launches, total_ms)} of the launches recorded since tmamg_profile_enable."""
+    import json
+    n = 1 << 16
+    buf = ctypes.create_string_buffer(n)
+    rc = lib().tmamg_profile_report(buf, n)
+    if rc < 0:
+        raise TmamgError("tmamg_profile_report", rc, "record longer than the buffer")
+    return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
 
 
 def tmamg_debug_bounded_wait(limit_cycles, unreachable_next):

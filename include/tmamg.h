@@ -98,6 +98,9 @@ typedef struct {
   int mid_restart;     /* <= 64 */
   int mid_maxiter;
   int mid_smooth;      /* 0 = no level-1 smoothing */
+  int inner_cycles;    /* FP32 FGMRES(restart) cycles per FP64 refinement cycle (>= 1): after each cycle the
+                          systems that missed the inner goal restart from their FP32 residual, so the FP64
+                          residual (the expensive product on GB300) is formed only once per inner_cycles cycles */
 } tmamg_solve_params;
 
 typedef struct {

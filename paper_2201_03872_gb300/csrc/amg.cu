@@ -145,12 +145,11 @@ void build_P(const AggDims& g, const float* Vb, float2* P, int nv, int d, cudaSt
 // k; per k it loads three entries of P and reads three staged 16-byte entries, and does nine
 // packed complex multiply-adds (both systems of a tile at once). The 16 slice sums of an output
 // are added by shuffles in a fixed order.
-constexpr int RS_KS = 16;       // k slices (lanes of a half warp)
-constexpr int RS_SLOTS = 16;    // output blocks processed at once per CTA
-constexpr int RS_THREADS = RS_KS * RS_SLOTS;
-constexpr int RS_KC = 128;      // k values staged per chunk (fewer when many tiles)
+constexpr int RS_KS = 16;         // k slices (lanes of a half warp)
+constexpr int RS_MAX_SLOTS = 32;  // output blocks processed at once per CTA (blockDim.x / RS_KS)
+constexpr int RS_KC = 128;        // k values staged per chunk (fewer when many tiles)
 
-__global__ void __launch_bounds__(RS_THREADS) restrict_kernel(const float2* __restrict__ P,
+__global__ void __launch_bounds__(RS_KS * RS_MAX_SLOTS) restrict_kernel(const float2* __restrict__ P,
                                                               const float* __restrict__ r, float* __restrict__ xc,
                                                               AggDims g, int nv, int d, int nt, int kc) {
   extern __shared__ float4 rsm[];                            // [nt][kc] staged entries
@@ -164,9 +163,10 @@ __global__ void __launch_bounds__(RS_THREADS) restrict_kernel(const float2* __re
     sidx[q] = (int)site_index(c, g.L);
   }
   const int ks = threadIdx.x % RS_KS, slot = threadIdx.x / RS_KS;
+  const int nslots = blockDim.x / RS_KS;
   const int JG = (nv + 2) / 3, TG = (nt + 2) / 3;
   const float2* Pa = P + ((a * 2 + chi) * nv) * (int64_t)K;
-  for (int og0 = 0; og0 < JG * TG; og0 += RS_SLOTS) {
+  for (int og0 = 0; og0 < JG * TG; og0 += nslots) {
     const int og = og0 + slot;
     const bool live = og < JG * TG;
     const int jg = live ? og / TG : 0, tg = live ? og % TG : 0;
@@ -247,7 +247,12 @@ void restrict_vec(const AggDims& g, const float2* P, const float* r, float* xc, 
   const size_t smem = sizeof(float4) * (size_t)nt * kc + sizeof(int) * g.asize;
   func_smem_optin((const void*)restrict_kernel, 200 * 1024);
   TM_PROF(st, d == 6 ? "restrict" : "restrict_coarse");
-  restrict_kernel<<<(unsigned)(g.Vc * 2), RS_THREADS, smem, st>>>(P, r, xc, g, nv, d, nt, kc);
+  // every output block of the aggregate in one pass over P and the staged vector chunks when they
+  // fit one CTA (rounds of RS_MAX_SLOTS blocks otherwise)
+  const int nblk = ((nv + 2) / 3) * ((nt + 2) / 3);
+  const int rounds = (nblk + RS_MAX_SLOTS - 1) / RS_MAX_SLOTS;
+  const int slots = (nblk + rounds - 1) / rounds;
+  restrict_kernel<<<(unsigned)(g.Vc * 2), RS_KS * slots, smem, st>>>(P, r, xc, g, nv, d, nt, kc);
   TM_COUNT();
 }
 

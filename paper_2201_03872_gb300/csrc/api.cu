@@ -140,6 +140,7 @@ void tmamg_default_solve_params(tmamg_solve_params* p) {
   p->mid_restart = 10;
   p->mid_maxiter = 50;
   p->mid_smooth = 3;
+  p->inner_cycles = 1;
 }
 
 int tmamg_create(const int L[4], int bc_t, void* cuda_stream, tmamg_ctx** out) {

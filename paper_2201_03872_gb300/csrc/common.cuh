@@ -122,6 +122,9 @@ void launch_convert_gauge(const Geom& g, const double* Uin, double2* U64, float2
 template <typename real>
 void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu, int nsys,
                   cudaStream_t st);
+// r = b - D(mu) x on FP32 bundles in one pass (b with the same tiles as x)
+void launch_residual32(const Geom& g, const float2* U, const float* C, const float* x, const float* b, float* r,
+                       const double* mu, int nsys, cudaStream_t st);
 // r_n = b_{n / nshift} - D(mu_n) x_n on FP64 bundles (one system per tile), b holding one tile
 // per right-hand side: the outer residual of the solver without a separate product buffer
 void launch_residual64(const Geom& g, const double2* U, const double* C, const double* x, const double* b, int nshift,

@@ -233,12 +233,15 @@ void launch_build_clover(const Geom& g, const double2* U64, double kappa, double
 }
 
 // FP32: 192-thread CTAs, two per SM, up to 170 registers (no spills); FP64: 256 threads, one per SM
-template <typename real, int T, int BX>
+// RES: residual form y = b - D x (b = bsub, tile tile / nshift), else y = D x (bsub unused)
+template <typename real, int T, int BX, bool RES>
 __global__ void __launch_bounds__(sizeof(real) == 4 ? 192 : 256, sizeof(real) == 4 ? 2 : 1) dirac_kernel(const typename LinkT<real>::t* __restrict__ U,
                                                     const real* __restrict__ C, const real* __restrict__ x,
-                                                    real* __restrict__ y, const double* __restrict__ mu, int nsys,
+                                                    real* y, const double* __restrict__ mu, int nsys,
                                                     int ntile, int Lx, int Ly, int Lz, int Lt, real bc_t,
-                                                    const real* __restrict__ bsub, int nshift) {
+                                                    const real* bsub, int nshift) {
+  // y is not restrict-qualified: the residual form may run in place (bsub == y), every thread
+  // reading b at its own site before it writes y there; x never overlaps y
   const int64_t V = (int64_t)Lx * Ly * Lz * Lt;
   const int64_t s = blockIdx.x * (int64_t)BX + threadIdx.x;
   const int tile = blockIdx.y * blockDim.y + threadIdx.y;
@@ -287,6 +290,16 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 192 : 256, sizeof(real) ==
     const float2 m2 = make_float2(n0 < nsys ? (float)mu[n0] : 0.f, n0 + 1 < nsys ? (float)mu[n0 + 1] : 0.f);
     local2(acc, xt + s * 4, V, C, V, s, m2);
     real* yo = y + tile * tstride + s * 4;
+    if constexpr (RES) {
+      // residual form y = b - D x (b tile tile / nshift)
+      const real* bo = bsub + (int64_t)(tile / nshift) * tstride + s * 4;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const CV2 bv = ld2(bo + (int64_t)k * V * 4);
+        acc.c[k].re = sub2(bv.re, acc.c[k].re);
+        acc.c[k].im = sub2(bv.im, acc.c[k].im);
+      }
+    }
 #pragma unroll
     for (int k = 0; k < 12; ++k) st2(yo + (int64_t)k * V * 4, acc.c[k]);
   } else {
@@ -318,7 +331,7 @@ __global__ void __launch_bounds__(sizeof(real) == 4 ? 192 : 256, sizeof(real) ==
     }
     local_term<real, T>(acc, xt + s * 2 * T, V, C, V, s, m);
     real* yo = y + tile * tstride + s * 2 * T;
-    if (bsub) {
+    if constexpr (RES) {
       // residual form y = b - D x, with b stored once per right-hand side (tile / nshift)
       const real* bo = bsub + (int64_t)(tile / nshift) * tstride + s * 2 * T;
 #pragma unroll
@@ -357,9 +370,21 @@ void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, re
   int ty = pick_ty(nt, BX, MAXT);
   dim3 block(BX, ty);
   dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nt / ty));
-  dirac_kernel<real, T, BX><<<grid, block, 0, st>>>(reinterpret_cast<const typename LinkT<real>::t*>(U), C, x, y, mu,
+  dirac_kernel<real, T, BX, false><<<grid, block, 0, st>>>(reinterpret_cast<const typename LinkT<real>::t*>(U), C, x, y, mu,
                                                     nsys, nt, g.L[0], g.L[1], g.L[2], g.L[3], (real)g.bc_t, nullptr,
                                                     1); TM_COUNT();
+}
+
+void launch_residual32(const Geom& g, const float2* U, const float* C, const float* x, const float* b, float* r,
+                       const double* mu, int nsys, cudaStream_t st) {
+  TM_PROF(st, "residual_f32");
+  constexpr int BX = 32;
+  const int nt = ntiles(nsys, 2);
+  const int ty = pick_ty(nt, BX, 192);
+  dim3 block(BX, ty);
+  dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nt / ty));
+  dirac_kernel<float, 2, BX, true><<<grid, block, 0, st>>>(U, C, x, r, mu, nsys, nt, g.L[0], g.L[1], g.L[2], g.L[3],
+                                                     (float)g.bc_t, b, 1); TM_COUNT();
 }
 
 void launch_residual64(const Geom& g, const double2* U, const double* C, const double* x, const double* b, int nshift,
@@ -369,7 +394,7 @@ void launch_residual64(const Geom& g, const double2* U, const double* C, const d
   const int ty = pick_ty(nsys, BX, 256);
   dim3 block(BX, ty);
   dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nsys / ty));
-  dirac_kernel<double, 1, BX><<<grid, block, 0, st>>>(U, C, x, r, mu, nsys, nsys, g.L[0], g.L[1], g.L[2], g.L[3],
+  dirac_kernel<double, 1, BX, true><<<grid, block, 0, st>>>(U, C, x, r, mu, nsys, nsys, g.L[0], g.L[1], g.L[2], g.L[3],
                                                       (double)g.bc_t, b, nshift); TM_COUNT();
 }
 

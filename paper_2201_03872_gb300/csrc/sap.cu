@@ -48,22 +48,26 @@ __device__ __forceinline__ int local_index(const int* lc, const SapDims& d) {
   return ((lc[3] * d.bs[2] + lc[2]) * d.bs[1] + lc[1]) * d.bs[0] + lc[0];
 }
 
-template <int T>
-__device__ __forceinline__ void block_reduce(float* v, int n, float* red) {
-  // sums v[0..n) over the CTA; every thread gets the totals (n <= 8); blockDim.x is a
-  // multiple of 32, so every warp is full
+template <int N>
+__device__ __forceinline__ void block_reduce(float (&v)[N], float* red) {
+  // sums v[0..N) over the CTA; every thread gets the totals (N <= 8); blockDim.x is a
+  // multiple of 32, so every warp is full. Fixed-size and fully unrolled, so v stays in registers.
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = (blockDim.x + 31) >> 5;
-  for (int i = 0; i < n; ++i) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
     float x = v[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     v[i] = x;
   }
-  if (lane == 0)
-    for (int i = 0; i < n; ++i) red[warp * 8 + i] = v[i];
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) red[warp * 8 + i] = v[i];
+  }
   __syncthreads();
-  for (int i = 0; i < n; ++i) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
     float s = 0;
     for (int w = 0; w < nw; ++w) s += red[w * 8 + i];
     v[i] = s;
@@ -85,19 +89,29 @@ constexpr int SAP_THREADS = 256;
 
 __device__ __forceinline__ int colour_block(const SapDims& d, int colour, int k) {
   if (d.pdim < 0) return k;  // one block covers the lattice (colour 0 only)
-  const int p = d.pdim, half = d.nb[p] / 2;
+  // the k-th block of this colour: dimension p = pdim takes 2 j + parity, the others the digits of
+  // k / half; written with selects on p so that no array is indexed at run time (that would put
+  // the arrays in local memory)
+  const int p = d.pdim;
+  const int half = (p == 0 ? d.nb[0] : p == 1 ? d.nb[1] : p == 2 ? d.nb[2] : d.nb[3]) / 2;
   const int j = k % half;
   int rest = k / half;
   int c[4];
   int par = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (q == p) continue;
+    if (q == p) {
+      c[q] = 0;
+      continue;
+    }
     c[q] = rest % d.nb[q];
     rest /= d.nb[q];
     par += c[q];
   }
-  c[p] = 2 * j + ((colour + par) & 1);
+  const int cp = 2 * j + ((colour + par) & 1);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q == p) c[q] = cp;
   return ((c[3] * d.nb[2] + c[2]) * d.nb[1] + c[1]) * d.nb[0] + c[0];
 }
 
@@ -220,7 +234,7 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
         v[0] = qq.x; v[1] = qr.x; v[2] = qi.x;
         v[3] = qq.y; v[4] = qr.y; v[5] = qi.y;
       }
-      block_reduce<T>(v, 6, red);  // contains the barrier: every q is computed, rho may change
+      block_reduce(v, red);  // contains the barrier: every q is computed, rho may change
       const float2 ar = make_float2(v[0] > 0.f ? v[1] / v[0] : 0.f, v[3] > 0.f ? v[4] / v[3] : 0.f);
       const float2 ai = make_float2(v[0] > 0.f ? v[2] / v[0] : 0.f, v[3] > 0.f ? v[5] / v[3] : 0.f);
       const float2 nai = make_float2(-ai.x, -ai.y);

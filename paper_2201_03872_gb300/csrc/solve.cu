@@ -55,6 +55,7 @@ struct Workspace {
   double2 *ones = nullptr, *mones = nullptr, *dot = nullptr, *partial64 = nullptr;
   size_t partial64_cap = 0;
   int *mask = nullptr, *flags = nullptr, *count = nullptr;
+  int* mask2 = nullptr;  // systems still iterating inside the FP32 inner cycles of one refinement cycle
   int* h_count = nullptr;
   int *outer_it = nullptr, *inner_it = nullptr;
   std::vector<void*> extra;
@@ -68,7 +69,7 @@ static void ws_free(Workspace* w) {
   if (!w) return;
   void* ptrs[] = {w->V, w->Z, w->t1, w->t2, w->t3, w->e32, w->x64, w->r64, w->b64, w->Vc, w->xc, w->rc,
                   w->rel_top, w->rel_coarse, w->rn, w->bn, w->scale, w->beta0, w->tmpd, w->ones, w->mones, w->dot,
-                  w->partial64, w->mask, w->flags, w->count, w->outer_it, w->inner_it, w->Vm, w->Zm, w->xm,
+                  w->partial64, w->mask, w->mask2, w->flags, w->count, w->outer_it, w->inner_it, w->Vm, w->Zm, w->xm,
                   w->rm, w->sm1, w->sm2, w->rel_mid, w->beta0m, w->mra, w->mrd};
   for (void* p : ptrs) cudaFree(p);
   for (void* p : w->extra) cudaFree(p);
@@ -178,6 +179,7 @@ static int ensure_ws(tmamg_ctx* ctx, int nsys, const tmamg_solve_params& p) {
   w->partial64_cap = partial_elems(12 * V, ns, 1, 1);
   A((void**)&w->partial64, sizeof(double2) * w->partial64_cap);
   A((void**)&w->mask, sizeof(int) * ns);
+  A((void**)&w->mask2, sizeof(int) * ns);
   A((void**)&w->flags, sizeof(int) * ns);
   A((void**)&w->count, sizeof(int));
   A((void**)&w->outer_it, sizeof(int) * ns);
@@ -815,8 +817,7 @@ static void amg_cycle(SolveCtx& S, const float* v, float* z) {
     coarse_solve(S, w->rc, w->xc);
     prolong_vec(ad, L1.P, w->xc, z, nv, 6, nsys, 0, st);
   }
-  launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, z, w->t1, S.mu, nsys, st);
-  axpby<float>(w->ones, 2, v, w->mones, 2, w->t1, M, nsys, nullptr, st);  // t1 = v - D z
+  launch_residual32(ctx->g, ctx->U32, ctx->C32, z, v, w->t1, S.mu, nsys, st);  // t1 = v - D z
   // z += SAP(t1): the block solver adds its corrections to z directly
   sap_apply(ctx->g, ctx->sp.sap_block, ctx->U32, ctx->C32, w->t1, z, w->t3, S.mu, nsys, ctx->sp.sap_cycles,
             ctx->sp.sap_mr_steps, st, true);
@@ -881,6 +882,30 @@ __global__ void outer_check_kernel(const double2* __restrict__ dot, const double
 __global__ void sqrt_kernel(const double2* dot, double* out, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = sqrt(fmax(dot[i].x, 0.0));
+}
+
+// after an FP32 inner cycle: the systems whose FGMRES residual is still above the cycle's goal
+// keep iterating (mask2), counted in *count
+__global__ void inner_check_kernel(const double* __restrict__ resid, const double* __restrict__ tolabs, int* mask2,
+                                   int* count, int nsys) {
+  const int n = threadIdx.x;
+  int on = 0;
+  if (n < nsys) {
+    on = mask2[n] && resid[n] > tolabs[n];
+    mask2[n] = on;
+  }
+  const int c = __syncthreads_count(on);
+  if (n == 0) *count = c;
+}
+
+// goal of the next inner cycle relative to its start residual (norms from dot): the absolute goal
+// rel0 (in units of the refinement cycle's normalised residual) over the new start norm
+__global__ void inner_rel_kernel(const double2* __restrict__ dot, const double* __restrict__ rel0, double* rel,
+                                 int nsys) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nsys) return;
+  const double b = sqrt(fmax(dot[n].x, 0.0));
+  rel[n] = b > 0 ? fmin(rel0[n] / b, 1.0) : 1.0;
 }
 
 __global__ void add_iters_kernel(const int* kconv, const int* mask, int* it, int n) {
@@ -1102,7 +1127,7 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   const int nsys = nrhs * nshift;
   if (nsys > 256) return set_err(ctx, TMAMG_ERR_ARG, "solve: at most 256 systems per call");
   if (sp->restart < 1 || sp->restart > 64 || sp->coarse_restart < 1 || sp->coarse_restart > 128 ||
-      sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1)
+      sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1 || sp->inner_cycles < 1)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: bad parameters");
   if (has_middle(ctx) &&
       (sp->mid_restart < 1 || sp->mid_restart > 64 || sp->mid_maxiter < 1 || !(sp->mid_tol > 0) || sp->mid_smooth < 0))
@@ -1171,8 +1196,23 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
     if (*w->h_count == 0 || outer == sp->max_outer) break;
     f64_to_f32(w->r64, w->scale, w->V, M, nsys, st);
     cudaMemsetAsync(w->e32, 0, w->fb32, st);
-    gmres_cycle<float>(w->top, fine, nsys, sp->restart, w->V, vstride, w->Z, w->e32, w->mask, w->rel_top, 1, false, st);
-    add_iters_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->top.kconv, w->mask, w->inner_it, nsys); TM_COUNT();
+    cudaMemcpyAsync(w->mask2, w->mask, sizeof(int) * nsys, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(w->tmpd, w->rel_top, sizeof(double) * nsys, cudaMemcpyDeviceToDevice, st);
+    for (int ic = 0; ic < sp->inner_cycles; ++ic) {
+      gmres_cycle<float>(w->top, fine, nsys, sp->restart, w->V, vstride, w->Z, w->e32, w->mask2, w->rel_top, 1, false,
+                         st);
+      add_iters_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->top.kconv, w->mask2, w->inner_it, nsys); TM_COUNT();
+      if (ic + 1 == sp->inner_cycles) break;
+      inner_check_kernel<<<1, 1024, 0, st>>>(w->top.resid, w->top.tolabs, w->mask2, w->count, nsys); TM_COUNT();
+      cudaMemcpyAsync(w->h_count, w->count, sizeof(int), cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      if (*w->h_count == 0) break;
+      // restart from the FP32 residual of the inner problem: V0 = r / |r| - D e32
+      f64_to_f32(w->r64, w->scale, w->V, M, nsys, st);
+      launch_residual32(g, ctx->U32, ctx->C32, w->e32, w->V, w->V, ctx->mu_dev, nsys, st);
+      mdot<float>(w->V, 0, 1, w->V, M, nsys, w->dot, nsys, w->top.partial, st);
+      inner_rel_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->tmpd, w->rel_top, nsys); TM_COUNT();
+    }
     f32_axpy_f64(w->rn, w->e32, w->x64, M, nsys, w->mask, st);
     // r = b - D x in FP64 in one pass (the stencil's residual form)
     launch_residual64(g, ctx->U64, ctx->C64, w->x64, w->b64, nshift, w->r64, ctx->mu_dev, nsys, st);

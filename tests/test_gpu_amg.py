@@ -246,3 +246,26 @@ def test_solve_precision_lattice_persistent_vs_launches():
             res = np.linalg.norm(b[1] - op.apply(x[1, 0], 0.003)) / np.linalg.norm(b[1])
             assert res <= 1e-10
     assert abs(out[0] - out[2]) <= max(3, 0.3 * out[2])
+
+
+def test_inner_fp32_cycles_cut_fp64_refinements():
+    # FP32 FGMRES(4) restarted from its FP32 residual inside each FP64 refinement cycle: every system
+    # still reaches the FP64 goal (checked by the oracle operator) with fewer FP64 residuals
+    L = (8, 4, 4, 8)
+    U = synth.gauge_field(L, 0.3, seed=3)
+    kappa = 0.126
+    b = synth.gaussian_spinors(L, 2, seed=6)
+    mus = [0.001, 0.05]
+    op = dirac.Operator(U, kappa, 1.0)
+    outer = {}
+    for ic in (1, 4):
+        rc, stats, x = _solve(L, U, kappa, 1.0, b, mus,
+                              dict(agg=(4, 2, 2, 4), nv=12, sap_block=(2, 2, 2, 2), setup_iters=4),
+                              dict(restart=4, tol=1e-10, inner_cycles=ic))
+        assert rc == 0, [(s.status, s.true_rel_res) for s in stats]
+        for r in range(2):
+            for k, mu in enumerate(mus):
+                res = np.linalg.norm(b[r] - op.apply(x[r, k], mu)) / np.linalg.norm(b[r])
+                assert res <= 1e-10, (ic, r, k, res)
+        outer[ic] = max(s.outer_iters for s in stats)
+    assert outer[4] < outer[1], outer

@@ -146,10 +146,11 @@ void build_P(const AggDims& g, const float* Vb, float2* P, int nv, int d, cudaSt
 // packed complex multiply-adds (both systems of a tile at once). The 16 slice sums of an output
 // are added by shuffles in a fixed order.
 constexpr int RS_KS = 16;         // k slices (lanes of a half warp)
-constexpr int RS_MAX_SLOTS = 32;  // output blocks processed at once per CTA (blockDim.x / RS_KS)
+constexpr int RS_MAX_SLOTS = 24;  // output blocks processed at once per CTA (blockDim.x / RS_KS)
 constexpr int RS_KC = 128;        // k values staged per chunk (fewer when many tiles)
 
-__global__ void __launch_bounds__(RS_KS * RS_MAX_SLOTS) restrict_kernel(const float2* __restrict__ P,
+// two CTAs per SM (80 registers, no spills): one stages its vector chunk while the other computes
+__global__ void __launch_bounds__(RS_KS * RS_MAX_SLOTS, 2) restrict_kernel(const float2* __restrict__ P,
                                                               const float* __restrict__ r, float* __restrict__ xc,
                                                               AggDims g, int nv, int d, int nt, int kc) {
   extern __shared__ float4 rsm[];                            // [nt][kc] staged entries
@@ -243,7 +244,7 @@ void restrict_vec(const AggDims& g, const float2* P, const float* r, float* xc, 
                   cudaStream_t st) {
   const int nt = ntiles(nsys, T2);
   int kc = RS_KC;
-  while (kc > RS_KS && sizeof(float4) * (size_t)nt * kc + sizeof(int) * g.asize > 190 * 1024) kc -= RS_KS;
+  while (kc > RS_KS && sizeof(float4) * (size_t)nt * kc + sizeof(int) * g.asize > 100 * 1024) kc -= RS_KS;  // two CTAs per SM
   const size_t smem = sizeof(float4) * (size_t)nt * kc + sizeof(int) * g.asize;
   func_smem_optin((const void*)restrict_kernel, 200 * 1024);
   TM_PROF(st, d == 6 ? "restrict" : "restrict_coarse");

@@ -38,6 +38,7 @@ constexpr int CM_SLACK = 2048;    // bytes past the last stage the M = 128 descr
 constexpr int CM_MAXNC = 64;      // rows of D read back by the two epilogue warps
 constexpr int CM_MAXSTG = 16;     // stages in the shared-memory ring
 constexpr int CM_EPI0 = 4;        // first epilogue warp (warps 4 and 5 read TMEM lanes 0..63)
+constexpr int CM_TAB = 256;       // systems whose epilogue factors are tabulated in shared memory per call
 
 __host__ __device__ inline int cm_ncp(int nc) { return (nc + 7) / 8 * 8; }
 __host__ __device__ inline int64_t cm_hop_bytes(int nc) {
@@ -70,6 +71,11 @@ struct CmShared {
   unsigned long long tfull[CM_ACCS], tempty[CM_ACCS];    // accumulator ready / drained
   unsigned tmem;
   int fail;
+  // per-system epilogue factors of the current call (systems n < CM_TAB): output scale so[n] and
+  // twist dmu mu_n si[n], in FP32, so that the epilogue does no FP64 arithmetic (FP64 runs at a
+  // small fraction of the FP32 rate on this GPU)
+  float so[CM_TAB];
+  float tw[CM_TAB];
 };
 
 // role-local pipeline position, carried from one stencil call to the next by the thread
@@ -309,6 +315,12 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
   // shared memory last written through the generic proxy (other phases) is next written by
   // the bulk copies and read by the tensor cores (async proxy)
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  for (int n = tid; n < q.nsys && n < CM_TAB; n += blockDim.x) {
+    float si, so;
+    cm_sys_scale(q.scale, q.mode, n, si, so);
+    cs.so[n] = so;
+    cs.tw[n] = (float)(q.dmu * q.mu[n]) * si;
+  }
   __syncthreads();
   const uint32_t s0 = cm_smem(dsm);
 
@@ -370,9 +382,12 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
           }
           cm_fence_after();
           const uint32_t ab = s0 + st * ST, bb = ab + HA;
+          // k-step descriptors: the start-address field (address / 16, 14 bits) of the stage's
+          // descriptor advanced by the k offset (every address stays below 2^18 bytes: no carry)
+          const uint64_t ad0 = cm_desc(ab, MG * 128, 128), bd0 = cm_desc(bb, NG * 128, 128);
           for (int k = 0; k < KS; ++k) {
-            const uint64_t ad = cm_desc(ab + 2 * k * MG * 128, MG * 128, 128);
-            const uint64_t bd = cm_desc(bb + 2 * k * NG * 128, NG * 128, 128);
+            const uint64_t ad = ad0 + (uint64_t)((2 * k * MG * 128) >> 4);
+            const uint64_t bd = bd0 + (uint64_t)((2 * k * NG * 128) >> 4);
             const uint32_t accum = (h | k) != 0;
             asm volatile(
                 "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -440,11 +455,21 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
             const int t = c * TP + tp;
             if (tp < TP && t < nt) {
               const int n0 = 2 * t;
-              float si0, so0, si1 = 0.f, so1 = 0.f;
-              cm_sys_scale(q.scale, q.mode, n0, si0, so0);
-              if (n0 + 1 < q.nsys) cm_sys_scale(q.scale, q.mode, n0 + 1, si1, so1);
-              const float tw0 = g5 * (float)(q.dmu * q.mu[n0]) * si0;
-              const float tw1 = n0 + 1 < q.nsys ? g5 * (float)(q.dmu * q.mu[n0 + 1]) * si1 : 0.f;
+              float so0, so1 = 0.f, tw0, tw1 = 0.f;
+              if (n0 + 1 < CM_TAB) {
+                so0 = cs.so[n0];
+                tw0 = g5 * cs.tw[n0];
+                if (n0 + 1 < q.nsys) {
+                  so1 = cs.so[n0 + 1];
+                  tw1 = g5 * cs.tw[n0 + 1];
+                }
+              } else {  // systems past the table: the factors computed here
+                float si0, si1 = 0.f;
+                cm_sys_scale(q.scale, q.mode, n0, si0, so0);
+                if (n0 + 1 < q.nsys) cm_sys_scale(q.scale, q.mode, n0 + 1, si1, so1);
+                tw0 = g5 * (float)(q.dmu * q.mu[n0]) * si0;
+                tw1 = n0 + 1 < q.nsys ? g5 * (float)(q.dmu * q.mu[n0 + 1]) * si1 : 0.f;
+              }
               float4 o;
               o.x = so0 * (__uint_as_float(r[4 * tp]) - tw0 * xv[tp].z);
               o.y = so1 * (__uint_as_float(r[4 * tp + 1]) - tw1 * xv[tp].w);

@@ -280,21 +280,23 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
 template <typename real, int T>
 __global__ void __launch_bounds__(256) sap_face_kernel(const float2* __restrict__ U, const real* __restrict__ delta,
                                                        real* __restrict__ r, SapDims d, int other, int ntile) {
+  // threads over the sites of the blocks of colour `other` only (block k of that colour, site q
+  // in the block), so that no lane of a warp idles on a site of the wrong colour
   const int64_t V = (int64_t)d.L[0] * d.L[1] * d.L[2] * d.L[3];
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int tile = blockIdx.y;
-  if (s >= V || tile >= ntile) return;
-  int c[4];
-  site_coords(s, d.L, c);
-  int col = 0;
+  const int nbc = d.pdim < 0 ? 0 : (int)(V / d.bv / 2);
+  if (idx >= (int64_t)nbc * d.bv || tile >= ntile) return;
+  const int k = (int)(idx / d.bv), q = (int)(idx % d.bv);
+  int bc[4], lc[4], c[4];
+  block_site(d, colour_block(d, other, k), q, bc, lc, c);
+  const int64_t s = site_index(c, d.L);
   bool fwd[4], bwd[4];
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
-    col += c[nu] / d.bs[nu];
-    fwd[nu] = d.nb[nu] > 1 && (c[nu] % d.bs[nu]) == d.bs[nu] - 1;
-    bwd[nu] = d.nb[nu] > 1 && (c[nu] % d.bs[nu]) == 0;
+    fwd[nu] = d.nb[nu] > 1 && lc[nu] == d.bs[nu] - 1;
+    bwd[nu] = d.nb[nu] > 1 && lc[nu] == 0;
   }
-  if ((col & 1) != other) return;
   if (!(fwd[0] || fwd[1] || fwd[2] || fwd[3] || bwd[0] || bwd[1] || bwd[2] || bwd[3])) return;
   const int64_t tstride = (int64_t)12 * V * 2 * T;
   const real* dt = delta + tile * tstride;
@@ -396,10 +398,11 @@ void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C
         TM_COUNT();
       }
       bool last = (cy == cycles - 1) && colour == 1;
-      if (!last) {
+      if (!last && d.pdim >= 0) {
         TM_PROF(st, "sap_face");
-        sap_face_kernel<float, T><<<dim3((unsigned)((g.V + 255) / 256), nt), 256, 0, st>>>(U32, delta, r, d,
-                                                                                          1 - colour, nt); TM_COUNT();
+        const int64_t nsite = (int64_t)(nblocks / 2) * d.bv;  // sites of the blocks of the other colour
+        sap_face_kernel<float, T><<<dim3((unsigned)((nsite + 255) / 256), nt), 256, 0, st>>>(U32, delta, r, d,
+                                                                                            1 - colour, nt); TM_COUNT();
       }
     }
   }

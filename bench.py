@@ -554,6 +554,7 @@ def run_solve(args, world, rank, local):
         "gpu_launches": int(launches),
         "launches_before_timed": int(launches0),
         "clocks": clk.result,
+        "autotune": T.tmamg_autotune_report(),
     }
     pb.close()
     del bh_t, xh_t

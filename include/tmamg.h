@@ -298,6 +298,19 @@ int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* x
 
 /* ------------------------------------------------------------------ diagnostics */
 
+/* Launch-shape autotuning (process-wide, on by default). Kernel families with several launch
+ * variants that compute identical results (the fine stencil and its residual forms: CTA shape and
+ * register budget) time every variant on the first call for a lattice volume and system count,
+ * with CUDA events on that call's stream, and use the fastest from then on (per device). The first
+ * call of each shape therefore synchronises its stream once. on = 0 uses the default variant
+ * everywhere. Every call clears the recorded choices. Always returns TMAMG_OK. */
+int tmamg_autotune(int on);
+
+/* Writes the choices as NUL-terminated JSON text {"family/devD/key": {"choice": v, "ms": [per
+ * variant]}, ...} (key = volume * 4096 + systems). Returns the text length, or TMAMG_ERR_ARG if buf
+ * is NULL or len is shorter than the text plus its terminator. */
+int tmamg_autotune_report(char* buf, size_t len);
+
 /* Per-kernel timing (process-wide, off by default; no counterpart in the paper). With on != 0
  * the main launch sites of the library (fine stencil and FP64 residual, SAP block solver and
  * face update, restriction, prolongation, coarse stencils, persistent coarse GMRES, the BLAS-1

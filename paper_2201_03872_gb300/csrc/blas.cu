@@ -46,7 +46,11 @@ struct Acc {
 };
 
 // ----------------------------------------------------------------------- multi-dot
-// partial[(tile * nblk + blk) * k + i][lane] = sum over the CTA's slice of conj(V_i) w
+// partial[(tile * nblk + blk) * k + i][lane] = sum over the CTA's slice of conj(V_i) w.
+// The basis vectors are taken MD_KC at a time: each entry of w is loaded once per group and
+// multiplied with the group's vectors, so one call reads w ceil(k / MD_KC) times instead of k.
+constexpr int MD_KC = 8;
+
 template <typename real, int T>
 __global__ void __launch_bounds__(RED_THREADS) mdot_partial_kernel(const real* __restrict__ Vb, int64_t vstride, int k,
                                                                    const real* __restrict__ w, int64_t M,
@@ -54,45 +58,54 @@ __global__ void __launch_bounds__(RED_THREADS) mdot_partial_kernel(const real* _
   const int tile = blockIdx.y;
   const int nblk = gridDim.x;
   const int64_t toff = (int64_t)tile * M * 2 * T;
-  __shared__ double2 red[RED_THREADS / 32][T];
-  for (int i = 0; i < k; ++i) {
-    const real* v = Vb + i * vstride + toff;
-    const real* ww = w + toff;
-    real sr[T], si[T];
+  __shared__ double2 red[RED_THREADS / 32][MD_KC][T];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const real* ww = w + toff;
+  for (int i0 = 0; i0 < k; i0 += MD_KC) {
+    const int kn = k - i0 < MD_KC ? k - i0 : MD_KC;
+    real sr[MD_KC][T], si[MD_KC][T];
 #pragma unroll
-    for (int l = 0; l < T; ++l) { sr[l] = 0; si[l] = 0; }
+    for (int u = 0; u < MD_KC; ++u)
+#pragma unroll
+      for (int l = 0; l < T; ++l) { sr[u][l] = 0; si[u][l] = 0; }
     for (int64_t m = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; m < M; m += (int64_t)nblk * RED_THREADS) {
-      Ent<real, T> a = lde<real, T>(v + m * 2 * T);
-      Ent<real, T> b = lde<real, T>(ww + m * 2 * T);
+      const Ent<real, T> b = lde<real, T>(ww + m * 2 * T);
 #pragma unroll
-      for (int l = 0; l < T; ++l) {
-        sr[l] += a.re[l] * b.re[l] + a.im[l] * b.im[l];
-        si[l] += a.re[l] * b.im[l] - a.im[l] * b.re[l];
+      for (int u = 0; u < MD_KC; ++u) {
+        if (u < kn) {
+          const Ent<real, T> a = lde<real, T>(Vb + (int64_t)(i0 + u) * vstride + toff + m * 2 * T);
+#pragma unroll
+          for (int l = 0; l < T; ++l) {
+            sr[u][l] += a.re[l] * b.re[l] + a.im[l] * b.im[l];
+            si[u][l] += a.re[l] * b.im[l] - a.im[l] * b.re[l];
+          }
+        }
       }
     }
-    double dr[T], di[T];
 #pragma unroll
-    for (int l = 0; l < T; ++l) {
-      dr[l] = sr[l];
-      di[l] = si[l];
+    for (int u = 0; u < MD_KC; ++u) {
+      if (u < kn) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        dr[l] += __shfl_xor_sync(0xffffffffu, dr[l], o);
-        di[l] += __shfl_xor_sync(0xffffffffu, di[l], o);
+        for (int l = 0; l < T; ++l) {
+          double dr = sr[u][l], di = si[u][l];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            dr += __shfl_xor_sync(0xffffffffu, dr, o);
+            di += __shfl_xor_sync(0xffffffffu, di, o);
+          }
+          if (lane == 0) red[warp][u][l] = make_double2(dr, di);
+        }
       }
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0)
-#pragma unroll
-      for (int l = 0; l < T; ++l) red[warp][l] = make_double2(dr[l], di[l]);
     __syncthreads();
-    if (threadIdx.x < T) {
+    if (threadIdx.x < kn * T) {
+      const int u = threadIdx.x / T, l = threadIdx.x % T;
       double2 s = make_double2(0, 0);
       for (int q = 0; q < RED_THREADS / 32; ++q) {
-        s.x += red[q][threadIdx.x].x;
-        s.y += red[q][threadIdx.x].y;
+        s.x += red[q][u][l].x;
+        s.y += red[q][u][l].y;
       }
-      partial[(((int64_t)tile * nblk + blockIdx.x) * k + i) * T + threadIdx.x] = s;
+      partial[(((int64_t)tile * nblk + blockIdx.x) * k + i0 + u) * T + l] = s;
     }
     __syncthreads();
   }

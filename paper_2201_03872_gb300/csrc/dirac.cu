@@ -12,6 +12,7 @@
 // Sec. 3: the matrix data is loaded once for all right-hand sides). Spin
 // projection in the chiral basis halves the SU(3) work: each hop multiplies
 // two colour vectors.
+#include "autotune.cuh"
 #include "stencil.cuh"
 #include "profile.cuh"
 
@@ -233,9 +234,11 @@ void launch_build_clover(const Geom& g, const double2* U64, double kappa, double
 }
 
 // FP32: 192-thread CTAs, two per SM, up to 170 registers (no spills); FP64: 256 threads, one per SM
-// RES: residual form y = b - D x (b = bsub, tile tile / nshift), else y = D x (bsub unused)
-template <typename real, int T, int BX, bool RES>
-__global__ void __launch_bounds__(sizeof(real) == 4 ? 192 : 256, sizeof(real) == 4 ? 2 : 1) dirac_kernel(const typename LinkT<real>::t* __restrict__ U,
+// RES: residual form y = b - D x (b = bsub, tile tile / nshift), else y = D x (bsub unused).
+// MAXT, MINB: the launch variant's largest CTA and the CTAs per SM it is compiled for (which sets the
+// register budget); every variant does the same per-thread arithmetic.
+template <typename real, int T, int BX, bool RES, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) dirac_kernel(const typename LinkT<real>::t* __restrict__ U,
                                                     const real* __restrict__ C, const real* __restrict__ x,
                                                     real* y, const double* __restrict__ mu, int nsys,
                                                     int ntile, int Lx, int Ly, int Lz, int Lt, real bc_t,
@@ -358,44 +361,84 @@ static inline int pick_ty(int nt, int bx, int maxthreads) {
   return best;
 }
 
+// launch variants: (sites per CTA row, largest CTA, CTAs per SM). FP32: 168 registers at 12 warps
+// per SM, or 128 registers (a few bytes of spills) at 16 warps per SM; FP64: 254 registers at 8
+// warps, or 168 registers (about 100 bytes of spills) at 12 warps.
+template <typename real, bool RES, int BX, int MAXT, int MINB>
+static void launch_variant(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu,
+                           int nsys, const real* b, int nshift, cudaStream_t st) {
+  constexpr int T = Tile<real>::T;
+  const int nt = ntiles(nsys, T);
+  const int ty = pick_ty(nt, BX, MAXT);
+  dim3 block(BX, ty);
+  dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nt / ty));
+  dirac_kernel<real, T, BX, RES, MAXT, MINB><<<grid, block, 0, st>>>(
+      reinterpret_cast<const typename LinkT<real>::t*>(U), C, x, y, mu, nsys, nt, g.L[0], g.L[1], g.L[2], g.L[3],
+      (real)g.bc_t, b, nshift); TM_COUNT();
+}
+
+template <typename real, bool RES>
+static void launch_variant_k(int v, const Geom& g, const void* U, const real* C, const real* x, real* y,
+                             const double* mu, int nsys, const real* b, int nshift, cudaStream_t st) {
+  if constexpr (sizeof(real) == 4) {
+    switch (v) {
+      case 1: launch_variant<real, RES, 32, 256, 2>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
+      case 2: launch_variant<real, RES, 64, 256, 2>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
+      case 3: launch_variant<real, RES, 32, 128, 4>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
+      default: launch_variant<real, RES, 32, 192, 2>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
+    }
+  } else {
+    switch (v) {
+      case 1: launch_variant<real, RES, 64, 192, 2>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
+      case 2: launch_variant<real, RES, 32, 192, 2>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
+      default: launch_variant<real, RES, 64, 256, 1>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
+    }
+  }
+}
+
+template <typename real>
+static constexpr int n_variants() {
+  return sizeof(real) == 4 ? 4 : 3;
+}
+
+// the tuned variant of a family for this lattice and system count; tuning (which runs every variant
+// on this call's data) only when `may_tune`, i.e. when the launch is repeatable
+template <typename real, bool RES>
+static void launch_tuned(const char* family, bool may_tune, const Geom& g, const void* U, const real* C, const real* x,
+                         real* y, const double* mu, int nsys, const real* b, int nshift, cudaStream_t st) {
+  const int64_t key = g.V * 4096 + nsys;
+  int v = 0;
+  if (autotune_on()) {
+    v = tune_lookup(family, key);
+    if (v < 0)
+      v = may_tune ? tune_run(family, key, n_variants<real>(),
+                              [&](int k) { launch_variant_k<real, RES>(k, g, U, C, x, y, mu, nsys, b, nshift, st); },
+                              st)
+                   : 0;
+  }
+  launch_variant_k<real, RES>(v, g, U, C, x, y, mu, nsys, b, nshift, st);
+}
+
 template <typename real>
 void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu, int nsys,
                   cudaStream_t st) {
-  constexpr int T = Tile<real>::T;
-  // FP32: 32 sites x up to 6 tiles per CTA, so a site's links and clover are read once per CTA
-  constexpr int BX = sizeof(real) == 4 ? 32 : 64;
-  constexpr int MAXT = sizeof(real) == 4 ? 192 : 256;
   TM_PROF(st, sizeof(real) == 4 ? "dirac_f32" : "dirac_f64");
-  int nt = ntiles(nsys, T);
-  int ty = pick_ty(nt, BX, MAXT);
-  dim3 block(BX, ty);
-  dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nt / ty));
-  dirac_kernel<real, T, BX, false><<<grid, block, 0, st>>>(reinterpret_cast<const typename LinkT<real>::t*>(U), C, x, y, mu,
-                                                    nsys, nt, g.L[0], g.L[1], g.L[2], g.L[3], (real)g.bc_t, nullptr,
-                                                    1); TM_COUNT();
+  launch_tuned<real, false>(sizeof(real) == 4 ? "dirac_f32" : "dirac_f64", true, g, U, C, x, y, mu, nsys, nullptr, 1,
+                            st);
 }
 
 void launch_residual32(const Geom& g, const float2* U, const float* C, const float* x, const float* b, float* r,
                        const double* mu, int nsys, cudaStream_t st) {
   TM_PROF(st, "residual_f32");
-  constexpr int BX = 32;
-  const int nt = ntiles(nsys, 2);
-  const int ty = pick_ty(nt, BX, 192);
-  dim3 block(BX, ty);
-  dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nt / ty));
-  dirac_kernel<float, 2, BX, true><<<grid, block, 0, st>>>(U, C, x, r, mu, nsys, nt, g.L[0], g.L[1], g.L[2], g.L[3],
-                                                     (float)g.bc_t, b, 1); TM_COUNT();
+  // tuned only out of place (in place, b == r, the launch is not repeatable)
+  launch_tuned<float, true>("residual_f32", b != r, g, reinterpret_cast<const void*>(U), C, x, r, mu, nsys, b, 1, st);
 }
 
 void launch_residual64(const Geom& g, const double2* U, const double* C, const double* x, const double* b, int nshift,
                        double* r, const double* mu, int nsys, cudaStream_t st) {
   TM_PROF(st, "residual_f64");
-  constexpr int BX = 64;
-  const int ty = pick_ty(nsys, BX, 256);
-  dim3 block(BX, ty);
-  dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nsys / ty));
-  dirac_kernel<double, 1, BX, true><<<grid, block, 0, st>>>(U, C, x, r, mu, nsys, nsys, g.L[0], g.L[1], g.L[2], g.L[3],
-                                                      (double)g.bc_t, b, nshift); TM_COUNT();
+  launch_tuned<double, true>("residual_f64", b != r, g, reinterpret_cast<const void*>(U), C, x, r, mu, nsys, b, nshift,
+                             st);
 }
 
 template void launch_dirac<float>(const Geom&, const void*, const float*, const float*, float*, const double*, int,

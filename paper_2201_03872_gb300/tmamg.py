@@ -113,6 +113,8 @@ SIGNATURES = {
     "tmamg_nn_train": (I, [P, ctypes.POINTER(NNParams), ctypes.POINTER(NNReport)]),
     "tmamg_debug_bounded_wait": (I, [ctypes.c_longlong, I]),
     "tmamg_profile_enable": (I, [I]),
+    "tmamg_autotune": (I, [I]),
+    "tmamg_autotune_report": (I, [ctypes.c_char_p, ctypes.c_size_t]),
     "tmamg_profile_report": (I, [ctypes.c_char_p, ctypes.c_size_t]),
 }
 
@@ -313,6 +315,22 @@ def tmamg_coarse_solve(ctx, level, rc_bundle, xc_bundle, nrhs, mu, nshift, param
                                                                 int(nrhs), _ptr(m), int(nshift), ctypes.byref(params),
                                                                 ctypes.byref(it)))
     return it.value
+
+
+def tmamg_autotune(on):
+    """Launch-shape autotuning on (default) or off (process-wide); clears the recorded choices."""
+    return lib().tmamg_autotune(int(bool(on)))
+
+
+def tmamg_autotune_report():
+    """{family/device/key: {"choice": v, "ms": [...]}} of the tuned launch shapes."""
+    import json
+    n = 1 << 16
+    buf = ctypes.create_string_buffer(n)
+    rc = lib().tmamg_autotune_report(buf, n)
+    if rc < 0:
+        raise TmamgError("tmamg_autotune_report", rc, "record longer than the buffer")
+    return json.loads(buf.value.decode())
 
 
 def tmamg_profile_enable(on):

@@ -48,11 +48,10 @@ struct Acc {
 // ----------------------------------------------------------------------- multi-dot
 // partial[(tile * nblk + blk) * k + i][lane] = sum over the CTA's slice of conj(V_i) w.
 // The basis vectors are taken MD_KC at a time: each entry of w is loaded once per group and
-// multiplied with the group's vectors, so one call reads w ceil(k / MD_KC) times instead of k.
-constexpr int MD_KC = 8;
-
-template <typename real, int T>
-__global__ void __launch_bounds__(RED_THREADS) mdot_partial_kernel(const real* __restrict__ Vb, int64_t vstride, int k,
+// multiplied with the group's vectors, so one call reads w ceil(k / MD_KC) times instead of k
+// (MD_KC = 1 for single dots and norms, 4 otherwise; four CTAs per SM either way).
+template <typename real, int T, int MD_KC>
+__global__ void __launch_bounds__(RED_THREADS, 4) mdot_partial_kernel(const real* __restrict__ Vb, int64_t vstride, int k,
                                                                    const real* __restrict__ w, int64_t M,
                                                                    double2* __restrict__ partial) {
   const int tile = blockIdx.y;
@@ -143,7 +142,11 @@ void mdot(const real* V, int64_t vstride, int k, const real* w, int64_t M, int n
   constexpr int T = Tile<real>::T;
   int nt = ntiles(nsys, T);
   int nblk = red_blocks(M, nt);
-  mdot_partial_kernel<real, T><<<dim3(nblk, nt), RED_THREADS, 0, st>>>(V, vstride, k, w, M, partial); TM_COUNT();
+  if (k == 1)
+    mdot_partial_kernel<real, T, 1><<<dim3(nblk, nt), RED_THREADS, 0, st>>>(V, vstride, k, w, M, partial);
+  else
+    mdot_partial_kernel<real, T, 4><<<dim3(nblk, nt), RED_THREADS, 0, st>>>(V, vstride, k, w, M, partial);
+  TM_COUNT();
   int tot = nsys * k;
   mdot_final_kernel<T><<<(tot + 127) / 128, 128, 0, st>>>(partial, nblk, k, nsys, out, ostride, 1.0); TM_COUNT();
 }

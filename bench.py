@@ -97,9 +97,9 @@ def dirac_bytes_per_site(nsys, prec):
 # DRAM bytes (read + write) of one fine-stencil launch at 16^3x32 x 12 systems, from an ncu
 # capture of that kernel; valid only for the kernel sources it was taken on (SHA-1 of dirac.cu
 # and stencil.cuh), else reported as null
-DIRAC_TRAFFIC = {"bytes": 237069824 + 120919040,
-                 "sha1": {"dirac.cu": "24e92d0ad15242de099dc0789bc8e321b64cb249",
-                          "stencil.cuh": "bdc68ee2e32fd9112f7efc57c95df0422ce387ff"}}
+DIRAC_TRAFFIC = {"bytes": 237310464 + 121262080,
+                 "sha1": {"dirac.cu": "871752da5cf290ad9f1436f55402167b7898c48a",
+                          "stencil.cuh": "05b2e5366b623651c2f5dfec54e20b5ae49291c7"}}
 
 
 def dirac_traffic():
@@ -651,8 +651,24 @@ def run_variants(args, rank, stream):
 
         guarded("precision_form_three_level", three)
 
+    def largest_fp64():
+        # the plain comparator on the headline lattice: one system, two levels (the FP64 solver's form),
+        # every vector, operator and reduction in FP64; one timed solve
+        wl = dict(WORKLOADS["largest"], nrhs=1, mus=[WORKLOADS["largest"]["mus"][0]],
+                  setup=dict(WORKLOADS["largest"]["setup"], levels=2),
+                  solve=dict(tol=1e-10, restart=10, max_outer=60, coarse_tol=0.1, coarse_restart=40,
+                             coarse_maxiter=400))
+        pb = Problem(wl, rank, stream)
+        try:
+            ms, ok, st_ = timed_solves(pb, pb.params(precision=64), 1, stream)
+            record("largest_plain_fp64_single_system", pb, ms, ok, st_, setup_seconds=pb.setup_seconds, steps=1,
+                   note="40^3x80, one Gaussian rhs at mu=0.0015, two-level FP64 AMG, FGMRES(10)")
+        finally:
+            pb.close()
+
     guarded("batched_multishift_40_systems", batched)
     guarded("precision_form", precision)
+    guarded("largest_plain_fp64_single_system", largest_fp64)
     return out
 
 

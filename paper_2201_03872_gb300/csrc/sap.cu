@@ -75,6 +75,15 @@ __device__ __forceinline__ void block_reduce(float (&v)[N], float* red) {
   __syncthreads();
 }
 
+__device__ __forceinline__ void sap_cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void sap_cp_async_wait() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Persistent block solver: CTA b takes a contiguous range of the work items (block of this
 // colour, tile), item = k * ntile + tile, so consecutive items mostly share a block. The
 // block's links and clover are staged in shared memory once per block and serve every tile
@@ -139,6 +148,20 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
   int64_t s = 0;
   int nf[4], nbk[4];
   float pf[4], pb[4];
+  // the residual of an item is fetched into rho by asynchronous copies (each thread its own site's
+  // twelve entries), for the next item while the current one writes its results back
+  auto fetch_rho = [&](int item_) {
+    const int k_ = item_ / ntile, t_ = item_ % ntile;
+    int bc_[4], lc_[4], c_[4];
+    block_site(d, colour_block(d, colour, k_), act ? tid : 0, bc_, lc_, c_);
+    const int64_t s_ = site_index(c_, d.L);
+    const float* rt_ = r + t_ * tstride;
+    if (act) {
+#pragma unroll
+      for (int k2 = 0; k2 < 12; ++k2) sap_cp_async16(&rho[k2 * bv + tid], rt_ + ((int64_t)k2 * V + s_) * 2 * T);
+    }
+  };
+  if (i0 < i1) fetch_rho(i0);
   for (int item = i0; item < i1; ++item) {
     const int k = item / ntile, tile = item % ntile;
     const int b = colour_block(d, colour, k);
@@ -189,8 +212,8 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
     for (int k2 = 0; k2 < 12; ++k2) {
       eb[k2].re = make_float2(0.f, 0.f);
       eb[k2].im = make_float2(0.f, 0.f);
-      if (act) rho[k2 * bv + tid] = *reinterpret_cast<const float4*>(rt + ((int64_t)k2 * V + s) * 2 * T);
     }
+    sap_cp_async_wait();  // this thread's residual entries are in rho (the barrier below publishes them)
     const int n0 = tile * T;
     const float2 m2 = make_float2(n0 < nsys ? (float)mu[n0] : 0.f, n0 + 1 < nsys ? (float)mu[n0 + 1] : 0.f);
     const float* rb = reinterpret_cast<const float*>(rho);
@@ -260,17 +283,23 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
     if (act) {
       float* dt = delta + tile * tstride;
       float* et = e + tile * tstride;
+      // every load of e first (twelve in flight), then the stores
+      CV2 e0[12];
+#pragma unroll
+      for (int k2 = 0; k2 < 12; ++k2) e0[k2] = ld2(et + ((int64_t)k2 * V + s) * 2 * T);
 #pragma unroll
       for (int k2 = 0; k2 < 12; ++k2) {
         const int64_t o = ((int64_t)k2 * V + s) * 2 * T;
         st2(dt + o, eb[k2]);
-        CV2 e0 = ld2(et + o);
-        e0.re = add2(e0.re, eb[k2].re);
-        e0.im = add2(e0.im, eb[k2].im);
-        st2(et + o, e0);
+        e0[k2].re = add2(e0[k2].re, eb[k2].re);
+        e0[k2].im = add2(e0[k2].im, eb[k2].im);
+        st2(et + o, e0[k2]);
         *reinterpret_cast<float4*>(rt + o) = rho[k2 * bv + tid];
       }
     }
+    // rho is private per thread from the last barrier on (neighbour reads ended before it): the
+    // next item's residual may be fetched into this thread's entries now
+    if (item + 1 < i1) fetch_rho(item + 1);
   }
 }
 

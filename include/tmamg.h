@@ -146,6 +146,15 @@ int tmamg_unpack(tmamg_ctx* ctx, const void* x_bundle, void* x_field, int nsys, 
  * nsys twisted masses. prec: 32 or 64. x and y must not overlap. */
 int tmamg_dirac(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int nsys, const double* mu, int prec);
 
+/* The non-degenerate twisted-mass doublet (paper Sec. 1, the generalisation of the method to a
+ * flavour doublet): D_ND(mu, eps) = D_W (x) 1 + i mu gamma5 (x) tau3 - eps 1 (x) tau1, acting on a
+ * pair (u, d) of fields as (D(mu) u - eps d, D(-mu) d - eps u), with D(mu) the degenerate
+ * operator above. Doublet q occupies systems 2q (u) and 2q + 1 (d) of the bundles: at prec 32
+ * one tile of two systems per doublet, at prec 64 the tiles 2q and 2q + 1. mu, eps: host arrays
+ * [npair]. x and y (device bundles of 2 npair systems) must not overlap. */
+int tmamg_dirac_doublet(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int npair, const double* mu,
+                        const double* eps, int prec);
+
 /* Convenience: y = D(mu_n) x_n on user fields (device pointers), packing through
  * internal scratch bundles. */
 int tmamg_apply(tmamg_ctx* ctx, const void* x_field, void* y_field, int nsys, const double* mu, int prec);
@@ -182,6 +191,19 @@ int tmamg_setup_from_vectors(tmamg_ctx* ctx, const tmamg_setup_params* p, const 
  * Synchronises the stream. */
 int tmamg_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int nshift, double* x, int on_device,
                 const tmamg_solve_params* p, tmamg_system_stats* stats);
+
+/* Solve D_ND(mu_k, eps_k) (x_u, x_d)_{r,k} = (b_u, b_d)_r for the non-degenerate doublet (see
+ * tmamg_dirac_doublet) with the same multigrid hierarchy: every level applies the doublet form
+ * (the coarse operator of D_ND is D_c(mu) (x) 1 - eps 1 (x) tau1 on P (x) 1, with the coarse
+ * twisted mass taking the sign of the flavour), and the Krylov scalars of each doublet are shared
+ * by its two flavours. b: complex double [nrhs][2][V][4][3] (flavour u, then d); mu, eps: host
+ * arrays [nshift]; x: complex double [nrhs][nshift][2][V][4][3]. stats: host array
+ * [nrhs * nshift] (one entry per doublet, norms over both flavours) or NULL. Requires the
+ * mixed-precision solver (p->precision 32) with the per-launch coarse GMRES (coarse_solver 0 is
+ * taken as 2; 1 and the learned step are rejected). Returns as tmamg_solve; at most 128
+ * doublets (rhs x shift) per call. Synchronises the stream. */
+int tmamg_solve_doublet(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, const double* eps, int nshift,
+                        double* x, int on_device, const tmamg_solve_params* p, tmamg_system_stats* stats);
 
 /* ------------------------------------------------------------------ learned preconditioner step */
 /* A gauge-covariant network of three linear parallel-transport layers (4 -> 8 -> 8 -> 4

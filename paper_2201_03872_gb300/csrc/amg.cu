@@ -341,7 +341,8 @@ void prolong_vec(const AggDims& g, const float2* P, const float* xc, float* e, i
 // ------------------------------------------------------------------ coarse stencil application
 // y[tile][i][a] = sum_h sum_j A[h][a][j][i] x[tile][j][a + h] + i dmu mu_n g5c(i) x[tile][i][a]
 __global__ void coarse_apply_kernel(const float2* __restrict__ A, const float* __restrict__ x, float* __restrict__ y,
-                                    const double* __restrict__ mu, double dmu, int nsys, CoarseDims cd) {
+                                    const double* __restrict__ mu, double dmu, int nsys, CoarseDims cd,
+                                    const double* __restrict__ eps) {
   const int nc = cd.nc;
   const int64_t Vc = cd.Vc;
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -384,15 +385,23 @@ __global__ void coarse_apply_kernel(const float2* __restrict__ A, const float* _
   acc.y -= m1 * xs.w;
   acc.z += m0 * xs.x;
   acc.w += m1 * xs.y;
+  if (eps) {  // doublet form: - eps times the other flavour (the tile's other lane)
+    const float ep = (float)eps[tile];
+    acc.x -= ep * xs.y;
+    acc.y -= ep * xs.x;
+    acc.z -= ep * xs.w;
+    acc.w -= ep * xs.z;
+  }
   *reinterpret_cast<float4*>(y + ((int64_t)(tile * nc + i) * Vc + a) * 2 * T2) = acc;
 }
 
 void coarse_apply(const CoarseDims& cd, const float2* A, const float* x, float* y, const double* mu, double dmu,
-                  int nsys, cudaStream_t st) {
+                  int nsys, cudaStream_t st, const double* eps) {
   TM_PROF(st, "coarse_apply_f32");
   int nt = ntiles(nsys, T2);
   int64_t total = cd.Vc * cd.nc;
-  coarse_apply_kernel<<<dim3((unsigned)((total + 127) / 128), nt), 128, 0, st>>>(A, x, y, mu, dmu, nsys, cd); TM_COUNT();
+  coarse_apply_kernel<<<dim3((unsigned)((total + 127) / 128), nt), 128, 0, st>>>(A, x, y, mu, dmu, nsys, cd, eps);
+  TM_COUNT();
 }
 
 // ------------------------------------------------------------------ Galerkin coarse operator

@@ -30,7 +30,7 @@ void prolong_vec(const AggDims& g, const float2* P, const float* xc, float* e, i
                  cudaStream_t st);
 // y = D_c(dmu * mu_n) x on coarse bundles
 void coarse_apply(const CoarseDims& cd, const float2* A, const float* x, float* y, const double* mu, double dmu,
-                  int nsys, cudaStream_t st);
+                  int nsys, cudaStream_t st, const double* eps = nullptr);
 // A = P^+ D P for a fine parent; W, Y: fine bundles of 2 nv systems; R: coarse bundle of 2 nv systems
 void build_coarse_operator_fine(const AggDims& g, const float2* U32, const float* C32, const float2* P, float2* A,
                                 int nv, int bc_t, float* W, float* Y, float* R, cudaStream_t st);

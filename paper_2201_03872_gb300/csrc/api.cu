@@ -5,6 +5,7 @@
 #include <mutex>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -179,6 +180,7 @@ int tmamg_destroy(tmamg_ctx* ctx) {
   cudaFree(ctx->C64);
   cudaFree(ctx->C32);
   cudaFree(ctx->mu_dev);
+  cudaFree(ctx->eps_dev);
   for (int i = 0; i < 2; ++i) cudaFree(ctx->scratch[i]);
   delete ctx;
   return TMAMG_OK;
@@ -277,6 +279,42 @@ int tmamg_dirac(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int nsys, 
   else
     return set_err(ctx, TMAMG_ERR_ARG, "dirac: prec must be 32 or 64");
   return check_cuda(ctx, cudaGetLastError(), "dirac launch");
+}
+
+int tmamg_dirac_doublet(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int npair, const double* mu,
+                        const double* eps, int prec) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!x_bundle || !y_bundle || !mu || !eps || npair <= 0 || (prec != 32 && prec != 64))
+    return set_err(ctx, TMAMG_ERR_ARG, "dirac_doublet: bad argument");
+  if (x_bundle == y_bundle) return set_err(ctx, TMAMG_ERR_ARG, "dirac_doublet: x and y must not overlap");
+  if (!ctx->have_op) return set_err(ctx, TMAMG_ERR_STATE, "dirac_doublet: operator not set");
+  const int nsys = 2 * npair;
+  std::vector<double> ms(nsys);
+  for (int q = 0; q < npair; ++q) {
+    ms[2 * q] = mu[q];
+    ms[2 * q + 1] = -mu[q];
+  }
+  int rc = upload_mu(ctx, ms.data(), nsys);
+  if (rc) return rc;
+  if (npair > ctx->eps_cap) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->eps_dev);
+    ctx->eps_dev = nullptr;
+    ctx->eps_cap = 0;
+    rc = check_cuda(ctx, cudaMalloc(&ctx->eps_dev, sizeof(double) * npair), "cudaMalloc(eps)");
+    if (rc) return rc;
+    ctx->eps_cap = npair;
+  }
+  rc = check_cuda(ctx, cudaMemcpyAsync(ctx->eps_dev, eps, sizeof(double) * npair, cudaMemcpyHostToDevice,
+                                       ctx->stream), "upload eps");
+  if (rc) return rc;
+  if (prec == 32)
+    launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, (const float*)x_bundle, (float*)y_bundle, ctx->mu_dev, nsys,
+                        ctx->stream, ctx->eps_dev);
+  else
+    launch_dirac<double>(ctx->g, ctx->U64, ctx->C64, (const double*)x_bundle, (double*)y_bundle, ctx->mu_dev, nsys,
+                         ctx->stream, ctx->eps_dev);
+  return check_cuda(ctx, cudaGetLastError(), "dirac_doublet launch");
 }
 
 int tmamg_apply(tmamg_ctx* ctx, const void* x_field, void* y_field, int nsys, const double* mu, int prec) {

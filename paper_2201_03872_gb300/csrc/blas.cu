@@ -127,6 +127,20 @@ __global__ void mdot_final_kernel(const double2* __restrict__ partial, int nblk,
   out[i * ostride + n] = make_double2(s.x * scale, s.y * scale);
 }
 
+static thread_local bool t_pair_fold = false;
+void set_pair_fold(bool on) { t_pair_fold = on; }
+
+// out[i * ostride + 2p] = out[i * ostride + 2p + 1] = their sum, p < npair, i < k
+__global__ void pair_fold_kernel(double2* out, int64_t ostride, int k, int npair) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k * npair) return;
+  const int i = t / npair, p = t % npair;
+  double2* o = out + (int64_t)i * ostride + 2 * p;
+  const double2 s = make_double2(o[0].x + o[1].x, o[0].y + o[1].y);
+  o[0] = s;
+  o[1] = s;
+}
+
 static int red_blocks(int64_t M, int ntile) {
   // about 4 CTAs per SM in total, at least one per tile
   int64_t want = (152 * 4 + ntile - 1) / ntile;
@@ -149,6 +163,10 @@ void mdot(const real* V, int64_t vstride, int k, const real* w, int64_t M, int n
   TM_COUNT();
   int tot = nsys * k;
   mdot_final_kernel<T><<<(tot + 127) / 128, 128, 0, st>>>(partial, nblk, k, nsys, out, ostride, 1.0); TM_COUNT();
+  if (t_pair_fold) {
+    const int np = nsys / 2;
+    pair_fold_kernel<<<(k * np + 127) / 128, 128, 0, st>>>(out, ostride, k, np); TM_COUNT();
+  }
 }
 
 size_t partial_elems(int64_t M, int nsys, int kmax, int T) {

@@ -12,6 +12,16 @@ void mdot(const real* V, int64_t vstride, int k, const real* w, int64_t M, int n
           double2* partial, cudaStream_t st);
 size_t partial_elems(int64_t M, int nsys, int kmax, int T);
 
+// Doublet solves: while set (on the calling host thread), every mdot adds the results of systems
+// 2p and 2p + 1 and gives the sum to both, so that a Krylov method running on per-system scalars
+// treats each doublet (its two flavours) as one system: both lanes then see identical norms, dots,
+// rotations and update coefficients.
+void set_pair_fold(bool on);
+struct PairFold {
+  explicit PairFold(bool on) { set_pair_fold(on); }
+  ~PairFold() { set_pair_fold(false); }
+};
+
 // y[n] += sign * sum_i c[i * cstride + n] V_i[n]; masked systems unchanged
 template <typename real>
 void maxpy(const real* V, int64_t vstride, int k, const double2* c, int64_t cstride, double sign, real* y, int64_t M,

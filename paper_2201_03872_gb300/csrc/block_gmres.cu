@@ -15,7 +15,6 @@
 
 #include "amg.cuh"
 #include "block_gmres.cuh"
-#include "profile.cuh"
 
 namespace tmamg {
 
@@ -31,6 +30,58 @@ __device__ __forceinline__ double2 bcj(double2 a) { return make_double2(a.x, -a.
 __device__ __forceinline__ float2 bget(const float* v, int64_t M, int n, int64_t e) {
   const float* q = v + (((int64_t)(n >> 1) * M + e) * 4);
   return make_float2(q[n & 1], q[2 + (n & 1)]);
+}
+
+// ---------------------------------------------------------------- block Gram: out[i][a][b] = <V_i[a], W[b]>
+// for i < k and a, b in the same block (a % nshift == b % nshift); partials per CTA, then a
+// fixed-order sum. One CTA handles a range of entries for every (i, pair).
+__global__ void __launch_bounds__(BG_THREADS) bgram_partial_kernel(const float* __restrict__ V, int64_t vstride, int k,
+                                                                   const float* __restrict__ W, int64_t M, int nsys,
+                                                                   int nshift, double2* __restrict__ part) {
+  // one warp per (i, pair) at a time, lanes over the CTA's entries (coalesced), FP32 lane sums
+  // added by a fixed-order warp reduction and kept in FP64
+  const int npair = nsys * (nsys / nshift);  // (a, b-index within a's block)
+  const int s = nsys / nshift;
+  const int64_t per = (M + gridDim.x - 1) / gridDim.x;
+  const int64_t e_lo = blockIdx.x * per;
+  const int64_t e_hi = e_lo + per < M ? e_lo + per : M;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = warp; q < k * npair; q += nw) {
+    const int i = q / npair, pr = q % npair;
+    const int a = pr / s, bi = pr % s;
+    const int b = (a % nshift) + bi * nshift;
+    const float* vi = V + (int64_t)i * vstride;
+    double sr = 0, si = 0;
+    for (int64_t e0 = e_lo; e0 < e_hi; e0 += 32 * 64) {  // FP32 runs of at most 64 entries per lane
+      float fr = 0, fi = 0;
+      const int64_t e1 = e0 + 32 * 64 < e_hi ? e0 + 32 * 64 : e_hi;
+      for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const float2 x = bget(vi, M, a, e), y = bget(W, M, b, e);
+        fr += x.x * y.x + x.y * y.y;
+        fi += x.x * y.y - x.y * y.x;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        fr += __shfl_xor_sync(0xffffffffu, fr, o);
+        fi += __shfl_xor_sync(0xffffffffu, fi, o);
+      }
+      sr += fr;
+      si += fi;
+    }
+    if (lane == 0) part[((int64_t)blockIdx.x * k + i) * npair + pr] = make_double2(sr, si);
+  }
+}
+
+__global__ void bgram_final_kernel(const double2* __restrict__ part, int nblk, int k, int npair, double2* out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= k * npair) return;
+  double2 s = make_double2(0, 0);
+  for (int b = 0; b < nblk; ++b) {
+    const double2 v = part[(int64_t)b * k * npair + q];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  out[q] = s;  // out[(i * nsys + a) * s + bi]
 }
 
 // ---------------------------------------------------------------- W[b] += sign sum_i sum_a V_i[a] C[i][a][bi]
@@ -121,6 +172,45 @@ __device__ void chol_inv(const double2* G, int s, double2* R, double2* Ri) {
     }
   }
   __syncwarp();
+}
+
+// gram layout from bgram: out[(i * nsys + a) * s + bi]; for block kb: G[ai][bi] with a = kb + ai nshift
+__global__ void bg_cholqr_kernel(const double2* __restrict__ gram, int nsys, int nshift, double2* coef,
+                                 double2* Racc, int first) {
+  __shared__ double2 G[BG_MAXS * BG_MAXS], R[BG_MAXS * BG_MAXS], Ri[BG_MAXS * BG_MAXS], T[BG_MAXS * BG_MAXS];
+  const int kb = blockIdx.x;
+  const int s = nsys / nshift;
+  const int lane = threadIdx.x;
+  for (int q = lane; q < s * s; q += 32) {
+    const int ai = q / s, bi = q % s;
+    const int a = kb + ai * nshift;
+    G[q] = gram[(int64_t)a * s + bi];
+  }
+  __syncwarp();
+  chol_inv(G, s, R, Ri);
+  // coefficients for W <- W Ri : coef[(0 * nsys + a) * s + bi] = Ri[ai][bi]
+  for (int q = lane; q < s * s; q += 32) {
+    const int ai = q / s, bi = q % s;
+    coef[((int64_t)(kb + ai * nshift)) * s + bi] = Ri[q];
+  }
+  // Racc (per block, s x s) <- R Racc  (or R on the first pass)
+  double2* Ra = Racc + (int64_t)kb * s * s;
+  for (int q = lane; q < s * s; q += 32) T[q] = first ? R[q] : Ra[q];
+  __syncwarp();
+  if (!first) {
+    for (int q = lane; q < s * s; q += 32) {
+      const int i = q / s, c = q % s;
+      double2 v = make_double2(0, 0);
+      for (int p = 0; p < s; ++p) {
+        const double2 t = bcm(R[i * s + p], T[p * s + c]);
+        v.x += t.x;
+        v.y += t.y;
+      }
+      Ra[q] = v;
+    }
+  } else {
+    for (int q = lane; q < s * s; q += 32) Ra[q] = T[q];
+  }
 }
 
 // State per block (FP64, global): Hb [(m+1) s][m s] (row-major, ld = m s), Gb [(m+1) s][s],
@@ -320,189 +410,6 @@ __global__ void bg_steps_kernel(const int* __restrict__ active, int* steps, int 
   if (k < nblock && active[k]) steps[k] = j + 1;
 }
 
-// ---------------------------------------------------------------- one reduction per block step
-// Block classical Gram-Schmidt with the Cholesky Gram taken from the same reduction: with
-// H_i = V_i^+ W (i < k) and G = W^+ W, the block left after the projection, U = W - sum V_i H_i,
-// has U^+ U = G - sum_i H_i^+ H_i (the V_i are orthonormal), so U = V_k R with R the Cholesky
-// factor of that matrix, and V_k = U R^{-1} = W R^{-1} - sum_i V_i (H_i R^{-1}). One grid-wide
-// reduction and one vector pass per block step instead of a Gram, an update and two CholQR passes
-// (the paper, Sec. 4: most of the block solver's overhead is global reductions).
-
-// partial[((blk * nshift + g) * (k + 1) + i) * s * s + ar * s + br] over the CTA's entries:
-// i < k: <V_i[a], W[b]>, i = k: <W[a], W[b]>, systems a = g + ar nshift, b = g + br nshift of
-// group g = blockIdx.y. Pairs in 4 x 4 chunks (blockIdx.z = chunk pair).
-__global__ void __launch_bounds__(BG_THREADS) bg_gram_kernel(const float* __restrict__ V, int64_t vstride, int k,
-                                                             const float* __restrict__ W, int64_t M, int nsys,
-                                                             int nshift, double2* __restrict__ part) {
-  const int s = nsys / nshift;
-  const int g = blockIdx.y;
-  const int nch = (s + 3) / 4;
-  const int ca = blockIdx.z / nch, cb = blockIdx.z % nch;
-  const int nblk = gridDim.x;
-  const int64_t per = (M + nblk - 1) / nblk;
-  const int64_t e_lo = blockIdx.x * per;
-  const int64_t e_hi = e_lo + per < M ? e_lo + per : M;
-  __shared__ double2 red[BG_THREADS / 32][16];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = 0; i <= k; ++i) {
-    const float* X = i < k ? V + (int64_t)i * vstride : W;
-    float ar[4][4], ai[4][4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) { ar[p][q] = 0.f; ai[p][q] = 0.f; }
-    for (int64_t e = e_lo + threadIdx.x; e < e_hi; e += blockDim.x) {
-      float2 x[4], y[4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const int ra = ca * 4 + p, rb = cb * 4 + p;
-        x[p] = ra < s ? bget(X, M, g + ra * nshift, e) : make_float2(0.f, 0.f);
-        y[p] = rb < s ? bget(W, M, g + rb * nshift, e) : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {  // conj(x_p) y_q
-          ar[p][q] += x[p].x * y[q].x + x[p].y * y[q].y;
-          ai[p][q] += x[p].x * y[q].y - x[p].y * y[q].x;
-        }
-    }
-    // fixed-order reduction: warp shuffles, then the warps in order
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        double dr = ar[p][q], di = ai[p][q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          dr += __shfl_xor_sync(0xffffffffu, dr, o);
-          di += __shfl_xor_sync(0xffffffffu, di, o);
-        }
-        if (lane == 0) red[warp][p * 4 + q] = make_double2(dr, di);
-      }
-    __syncthreads();
-    if (threadIdx.x < 16) {
-      const int p = threadIdx.x / 4, q = threadIdx.x % 4;
-      const int ra = ca * 4 + p, rb = cb * 4 + q;
-      double2 t = make_double2(0, 0);
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        t.x += red[w][threadIdx.x].x;
-        t.y += red[w][threadIdx.x].y;
-      }
-      if (ra < s && rb < s)
-        part[(((int64_t)blockIdx.x * nshift + g) * (k + 1) + i) * s * s + ra * s + rb] = t;
-    }
-    __syncthreads();
-  }
-}
-
-// out[(g (k + 1) + i) s s + pair] = sum over the CTAs in index order
-__global__ void bg_gram_final_kernel(const double2* __restrict__ part, int nblk, int nper, double2* __restrict__ out) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nper) return;
-  double2 t = make_double2(0, 0);
-  for (int b = 0; b < nblk; ++b) {
-    const double2 v = part[(int64_t)b * nper + q];
-    t.x += v.x;
-    t.y += v.y;
-  }
-  out[q] = t;
-}
-
-// Per group (one warp): R = chol(G - sum_i H_i^+ H_i), the update coefficients
-// coef[(g (k + 1) + i) s s + c s + b] = -(H_i R^{-1})[c][b] (i < k) and R^{-1}[c][b] (i = k), the block
-// Gram in the Hessenberg kernel's layout gram[(i nsys + a) s + br] = H_i[ar][br] and Racc[g] = R.
-__global__ void bg_lowsync_kernel(const double2* __restrict__ out, int k, int nsys, int nshift, double2* coef,
-                                  double2* gram, double2* Racc) {
-  __shared__ double2 G[BG_MAXS * BG_MAXS], R[BG_MAXS * BG_MAXS], Ri[BG_MAXS * BG_MAXS];
-  const int g = blockIdx.x;
-  const int s = nsys / nshift;
-  const int lane = threadIdx.x;
-  const double2* o = out + (int64_t)g * (k + 1) * s * s;
-  // G - sum_i H_i^+ H_i, entry (p, q) = G[p][q] - sum_i sum_c conj(H_i[c][p]) H_i[c][q]
-  for (int q2 = lane; q2 < s * s; q2 += 32) {
-    const int p = q2 / s, q = q2 % s;
-    double2 v = o[(int64_t)k * s * s + q2];
-    for (int i = 0; i < k; ++i)
-      for (int c = 0; c < s; ++c) {
-        const double2 t = bcm(bcj(o[(int64_t)i * s * s + c * s + p]), o[(int64_t)i * s * s + c * s + q]);
-        v.x -= t.x;
-        v.y -= t.y;
-      }
-    G[q2] = v;
-  }
-  __syncwarp();
-  chol_inv(G, s, R, Ri);
-  double2* cf = coef + (int64_t)g * (k + 1) * s * s;
-  for (int q2 = lane; q2 < s * s; q2 += 32) {
-    const int c = q2 / s, b = q2 % s;
-    cf[(int64_t)k * s * s + q2] = Ri[q2];
-    for (int i = 0; i < k; ++i) {
-      double2 v = make_double2(0, 0);
-      for (int d = 0; d < s; ++d) {
-        const double2 t = bcm(o[(int64_t)i * s * s + c * s + d], Ri[d * s + b]);
-        v.x -= t.x;
-        v.y -= t.y;
-      }
-      cf[(int64_t)i * s * s + q2] = v;
-      gram[((int64_t)i * nsys + g + c * nshift) * s + b] = o[(int64_t)i * s * s + q2];
-    }
-    Racc[(int64_t)g * s * s + q2] = R[q2];
-  }
-}
-
-// V_new[b] = sum_c W[c] coef_k[c][b] + sum_{i < k} sum_c V_i[c] coef_i[c][b] for the systems b of group
-// g (c and b over the group): one thread per (entry, group), thread index = entry * nshift + g, so
-// the two groups that share a 16-byte entry of a tile read it in the same warp; coefficients (FP32)
-// in shared memory [g][i][c][b]
-__global__ void __launch_bounds__(BG_THREADS) bg_update_kernel(const float* __restrict__ V, int64_t vstride, int k,
-                                                               const float* __restrict__ W,
-                                                               const double2* __restrict__ coef, int64_t M, int nsys,
-                                                               int nshift, float* __restrict__ Vout) {
-  extern __shared__ float2 cf[];  // [nshift][k + 1][s][s]
-  const int s = nsys / nshift;
-  const int ncoef = nshift * (k + 1) * s * s;
-  for (int q = threadIdx.x; q < ncoef; q += blockDim.x) {
-    const double2 c = coef[q];
-    cf[q] = make_float2((float)c.x, (float)c.y);
-  }
-  __syncthreads();
-  const int64_t total = M * nshift;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = idx / nshift;
-    const int g = (int)(idx % nshift);
-    float2 acc[BG_MAXS];
-#pragma unroll
-    for (int br = 0; br < BG_MAXS; ++br) acc[br] = make_float2(0.f, 0.f);
-    for (int i = 0; i <= k; ++i) {
-      const float* X = i < k ? V + (int64_t)i * vstride : W;
-      const float2* ci = cf + (int64_t)(g * (k + 1) + i) * s * s;
-      for (int cr = 0; cr < s; ++cr) {
-        const float2 x = bget(X, M, g + cr * nshift, e);
-        const float2* cc = ci + cr * s;
-#pragma unroll
-        for (int br = 0; br < BG_MAXS; ++br) {
-          if (br < s) {
-            const float2 w = cc[br];
-            acc[br].x += x.x * w.x - x.y * w.y;
-            acc[br].y += x.x * w.y + x.y * w.x;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int br = 0; br < BG_MAXS; ++br) {
-      if (br < s) {
-        const int b = g + br * nshift;
-        float* q = Vout + (((int64_t)(b >> 1) * M + e) * 4);
-        q[b & 1] = acc[br].x;
-        q[2 + (b & 1)] = acc[br].y;
-      }
-    }
-  }
-}
-
 int BlockGmres::alloc(int m_, int nsys_, int nshift_, int64_t M_) {
   if (m_ <= m && nsys_ == nsys && nshift_ == nshift && M_ <= M) return 0;
   release();
@@ -519,10 +426,10 @@ int BlockGmres::alloc(int m_, int nsys_, int nshift_, int64_t M_) {
   auto A = [&](void** q, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(q, bytes);
   };
-  A((void**)&gram, sizeof(double2) * (size_t)(m + 2) * nsys * s);
-  A((void**)&part, sizeof(double2) * (size_t)nblk * (m + 2) * nsys * s);
-  A((void**)&coef, sizeof(double2) * (size_t)(m + 2) * nsys * s);
-  A((void**)&hgram, sizeof(double2) * (size_t)(m + 2) * nsys * s);
+  A((void**)&gram, sizeof(double2) * (size_t)(m + 1) * nsys * s);
+  A((void**)&part, sizeof(double2) * (size_t)nblk * (m + 1) * nsys * s);
+  A((void**)&coef, sizeof(double2) * (size_t)(m + 1) * nsys * s);
+  A((void**)&hgram, sizeof(double2) * (size_t)(m + 1) * nsys * s);
   A((void**)&Racc, sizeof(double2) * (size_t)nb * s * s);
   A((void**)&S0, sizeof(double2) * (size_t)nb * s * s);
   A((void**)&H, sizeof(double2) * (size_t)nb * (m + 1) * s * m * s);
@@ -551,6 +458,16 @@ void BlockGmres::release() {
   M = 0;
 }
 
+// Gram of k block vectors against W: gram[(i nsys + a) s + bi]
+static void bgram(BlockGmres& b, const float* V, int64_t vstride, int k, const float* W, cudaStream_t st) {
+  const int s = b.nsys / b.nshift;
+  const int npair = b.nsys * s;
+  bgram_partial_kernel<<<b.nblk, BG_THREADS, 0, st>>>(V, vstride, k, W, b.M, b.nsys, b.nshift, b.part);
+  TM_COUNT();
+  bgram_final_kernel<<<(k * npair + 127) / 128, 128, 0, st>>>(b.part, b.nblk, k, npair, b.gram);
+  TM_COUNT();
+}
+
 static void baxpy(BlockGmres& b, const float* V, int64_t vstride, int k, const double2* C, double sign, float* W,
                   cudaStream_t st) {
   const int nt = (b.nsys + 1) / 2;
@@ -559,29 +476,16 @@ static void baxpy(BlockGmres& b, const float* V, int64_t vstride, int k, const d
   TM_COUNT();
 }
 
-// One block step's reduction and update: with W in `w` and the basis blocks V_0 .. V_{k-1}, the
-// Grams V_i^+ W and W^+ W of every group in one reduction, then R (Racc), the Hessenberg column
-// (b.gram) and the coefficients, then V_k = (W - sum V_i H_i) R^{-1} written to `out` (k = 0:
-// V_0 = W R^{-1}, the start block).
-static void lowsync_step(BlockGmres& b, const float* V, int64_t vstride, int k, const float* w, float* out,
-                         cudaStream_t st) {
-  const int s = b.nsys / b.nshift;
-  const int nch = (s + 3) / 4;
-  const int nper = b.nshift * (k + 1) * s * s;
-  bg_gram_kernel<<<dim3(b.nblk, b.nshift, nch * nch), BG_THREADS, 0, st>>>(V, vstride, k, w, b.M, b.nsys, b.nshift,
-                                                                          b.part);
-  TM_COUNT();
-  bg_gram_final_kernel<<<(nper + 127) / 128, 128, 0, st>>>(b.part, b.nblk, nper, b.hgram);
-  TM_COUNT();
-  bg_lowsync_kernel<<<b.nshift, 32, 0, st>>>(b.hgram, k, b.nsys, b.nshift, b.coef, b.gram, b.Racc);
-  TM_COUNT();
-  const size_t smem = sizeof(float2) * (size_t)nper;
-  func_smem_optin((const void*)bg_update_kernel, (int)(smem > 48 * 1024 ? smem : 48 * 1024));
-  const int64_t total = b.M * b.nshift;
-  int grid = (int)((total + BG_THREADS - 1) / BG_THREADS);
-  if (grid > 152 * 8) grid = 152 * 8;
-  bg_update_kernel<<<grid, BG_THREADS, smem, st>>>(V, vstride, k, w, b.coef, b.M, b.nsys, b.nshift, out);
-  TM_COUNT();
+// W <- W R^{-1} twice (CholQR2); R_total of each block in b.Racc; dst: a second bundle
+static void cholqr2(BlockGmres& b, float* W, float* tmp, size_t bytes, cudaStream_t st) {
+  for (int pass = 0; pass < 2; ++pass) {
+    bgram(b, W, 0, 1, W, st);
+    bg_cholqr_kernel<<<b.nshift, 32, 0, st>>>(b.gram, b.nsys, b.nshift, b.coef, b.Racc, pass == 0);
+    TM_COUNT();
+    cudaMemsetAsync(tmp, 0, bytes, st);
+    baxpy(b, W, 0, 1, b.coef, 1.0, tmp, st);
+    cudaMemcpyAsync(W, tmp, bytes, cudaMemcpyDeviceToDevice, st);
+  }
 }
 
 // V0 = rc - V0 (all systems)
@@ -597,19 +501,16 @@ __global__ void rsub_kernel(const float* __restrict__ rc, float* __restrict__ v,
 int block_gmres_solve(BlockGmres& b, const std::function<void(const float*, float*)>& apply, const float* rc,
                       float* xc, float* V, int64_t vstride, float* tmp, size_t bundle_bytes, int m, int maxiter,
                       double tol, int* iters_done, cudaStream_t st) {
-  TM_PROF(st, "block_gmres");
   const int s = b.nsys / b.nshift;
   if (s > BG_MAXS || b.nsys % b.nshift || m > b.m) return -2;
-  // the update kernel keeps its coefficients in shared memory
-  if (sizeof(float2) * (size_t)b.nshift * (m + 1) * s * s > (size_t)device_smem_optin() - 4096) return -2;
   BGDense d{b.H, b.Gr, b.cs, b.sn, b.Y, b.res, b.tolabs, b.active, b.nactive};
   const int64_t n4 = (int64_t)(bundle_bytes / sizeof(float4));
   cudaMemsetAsync(xc, 0, bundle_bytes, st);
-  cudaMemcpyAsync(tmp, rc, bundle_bytes, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(V, rc, bundle_bytes, cudaMemcpyDeviceToDevice, st);
   int total = 0;
   for (int cycle = 0;; ++cycle) {
-    // V_0 S_0 = R (the residual is in tmp)
-    lowsync_step(b, V, vstride, 0, tmp, V, st);
+    // V_0 S_0 = R (the residual is in V_0)
+    cholqr2(b, V, tmp, bundle_bytes, st);
     cudaMemcpyAsync(b.S0, b.Racc, sizeof(double2) * b.nshift * s * s, cudaMemcpyDeviceToDevice, st);
     bg_start_kernel<<<b.nshift, 32, 0, st>>>(b.S0, d, m, b.nsys, b.nshift, tol, cycle == 0 ? 1 : 0);
     TM_COUNT();
@@ -623,11 +524,15 @@ int block_gmres_solve(BlockGmres& b, const std::function<void(const float*, floa
     bool converged = false;
     for (; j < m && total < maxiter; ++j) {
       float* vj = V + (int64_t)j * vstride;
-      apply(vj, tmp);                                                    // W = A V_j
-      lowsync_step(b, V, vstride, j + 1, tmp, V + (int64_t)(j + 1) * vstride, st);  // V_{j+1} R_{j+1} = W - sum V_i H_ij
+      float* w = V + (int64_t)(j + 1) * vstride;
+      apply(vj, w);
+      bgram(b, V, vstride, j + 1, w, st);                // H_ij = V_i^+ W
+      cudaMemcpyAsync(b.hgram, b.gram, sizeof(double2) * (size_t)(j + 1) * b.nsys * s, cudaMemcpyDeviceToDevice, st);
+      baxpy(b, V, vstride, j + 1, b.hgram, -1.0, w, st);  // W -= sum_i V_i H_ij (one CGS pass)
+      cholqr2(b, w, tmp, bundle_bytes, st);               // V_{j+1} R_{j+1} = W
       bg_steps_kernel<<<1, 32, 0, st>>>(b.active, b.steps, b.nshift, j);
       TM_COUNT();
-      bg_hessenberg_kernel<<<b.nshift, 32, 0, st>>>(b.gram, b.Racc, d, j, m, b.nsys, b.nshift);
+      bg_hessenberg_kernel<<<b.nshift, 32, 0, st>>>(b.hgram, b.Racc, d, j, m, b.nsys, b.nshift);
       TM_COUNT();
       bg_count_kernel<<<1, 32, 0, st>>>(d, b.nshift);
       TM_COUNT();
@@ -644,9 +549,9 @@ int block_gmres_solve(BlockGmres& b, const std::function<void(const float*, floa
     TM_COUNT();
     baxpy(b, V, vstride, j, b.coef, 1.0, xc, st);
     if (converged || total >= maxiter) break;
-    // restart from the true residual: tmp = rc - A x
-    apply(xc, tmp);
-    rsub_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(rc, tmp, n4);
+    // restart from the true residual: V_0 = rc - A x
+    apply(xc, V);
+    rsub_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(rc, V, n4);
     TM_COUNT();
   }
   if (iters_done) *iters_done = total;

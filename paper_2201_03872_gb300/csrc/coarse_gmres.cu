@@ -455,6 +455,7 @@ __device__ __forceinline__ bool cg_apply_tc(const CGArgs& p, CmShared& cs, unsig
   q.nsys = p.nsys;
   q.nstage = p.cm_nstage;
   q.err = p.err;
+  q.eps = nullptr;  // the persistent solver runs degenerate systems only
   return cm_apply(q, cs, dsm, pipe, cta, ncta);
 }
 

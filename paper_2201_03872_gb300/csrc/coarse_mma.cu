@@ -97,7 +97,7 @@ size_t cm_dyn_cap(const void* kernel) {
 }
 
 int coarse_apply_f16(const CoarseDims& cd, const __half* A16, const float* x, float* y, const double* mu, double dmu,
-                     int nsys, float* mx, __half* X16, int* err, cudaStream_t st) {
+                     int nsys, float* mx, __half* X16, int* err, cudaStream_t st, const double* eps) {
   TM_PROF(st, "coarse_apply_f16");
   const int sms = device_sms();
   const size_t cap = cm_dyn_cap((const void*)coarse_mma_kernel);
@@ -132,6 +132,7 @@ int coarse_apply_f16(const CoarseDims& cd, const __half* A16, const float* x, fl
   q.nsys = nsys;
   q.nstage = nstage;
   q.err = err;
+  q.eps = eps;
   const int64_t G = cd.Vc < sms ? cd.Vc : sms;
   coarse_mma_kernel<<<(unsigned)G, CM_THREADS, cm_smem_bytes(cd.nc, nsys, nstage), st>>>(q);
   TM_COUNT();

@@ -76,6 +76,7 @@ struct CmShared {
   // small fraction of the FP32 rate on this GPU)
   float so[CM_TAB];
   float tw[CM_TAB];
+  float ep[CM_TAB];  // doublet splitting times the input scale (0 unless q.eps)
 };
 
 // role-local pipeline position, carried from one stencil call to the next by the thread
@@ -109,6 +110,7 @@ struct CmArgs {
   int nsys;
   int nstage;         // stages of the shared-memory ring
   int* err;           // set to 2 when a bounded wait gives up
+  const double* eps;  // [ntile] doublet splittings (the tile's lanes are the flavours u, d), or null
 };
 
 __device__ __forceinline__ uint32_t cm_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -320,6 +322,7 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
     cm_sys_scale(q.scale, q.mode, n, si, so);
     cs.so[n] = so;
     cs.tw[n] = (float)(q.dmu * q.mu[n]) * si;
+    cs.ep[n] = q.eps ? (float)q.eps[n >> 1] * si : 0.f;
   }
   __syncthreads();
   const uint32_t s0 = cm_smem(dsm);
@@ -455,13 +458,15 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
             const int t = c * TP + tp;
             if (tp < TP && t < nt) {
               const int n0 = 2 * t;
-              float so0, so1 = 0.f, tw0, tw1 = 0.f;
+              float so0, so1 = 0.f, tw0, tw1 = 0.f, ep0, ep1 = 0.f;
               if (n0 + 1 < CM_TAB) {
                 so0 = cs.so[n0];
                 tw0 = g5 * cs.tw[n0];
+                ep0 = cs.ep[n0];
                 if (n0 + 1 < q.nsys) {
                   so1 = cs.so[n0 + 1];
                   tw1 = g5 * cs.tw[n0 + 1];
+                  ep1 = cs.ep[n0 + 1];
                 }
               } else {  // systems past the table: the factors computed here
                 float si0, si1 = 0.f;
@@ -469,12 +474,27 @@ static __device__ __forceinline__ bool cm_apply(const CmArgs& q, CmShared& cs, u
                 if (n0 + 1 < q.nsys) cm_sys_scale(q.scale, q.mode, n0 + 1, si1, so1);
                 tw0 = g5 * (float)(q.dmu * q.mu[n0]) * si0;
                 tw1 = n0 + 1 < q.nsys ? g5 * (float)(q.dmu * q.mu[n0 + 1]) * si1 : 0.f;
+                ep0 = q.eps ? (float)q.eps[t] * si0 : 0.f;
+                ep1 = q.eps ? (float)q.eps[t] * si1 : 0.f;
               }
+              // twist i dmu mu g5 x, and for a doublet -eps times the other lane (flavour); the
+              // coupling is skipped for degenerate systems, so that a non-finite system cannot
+              // reach its tile neighbour through 0 * inf
               float4 o;
-              o.x = so0 * (__uint_as_float(r[4 * tp]) - tw0 * xv[tp].z);
-              o.y = so1 * (__uint_as_float(r[4 * tp + 1]) - tw1 * xv[tp].w);
-              o.z = so0 * (__uint_as_float(r[4 * tp + 2]) + tw0 * xv[tp].x);
-              o.w = so1 * (__uint_as_float(r[4 * tp + 3]) + tw1 * xv[tp].y);
+              o.x = __uint_as_float(r[4 * tp]) - tw0 * xv[tp].z;
+              o.y = __uint_as_float(r[4 * tp + 1]) - tw1 * xv[tp].w;
+              o.z = __uint_as_float(r[4 * tp + 2]) + tw0 * xv[tp].x;
+              o.w = __uint_as_float(r[4 * tp + 3]) + tw1 * xv[tp].y;
+              if (q.eps) {
+                o.x -= ep0 * xv[tp].y;
+                o.y -= ep1 * xv[tp].x;
+                o.z -= ep0 * xv[tp].w;
+                o.w -= ep1 * xv[tp].z;
+              }
+              o.x *= so0;
+              o.y *= so1;
+              o.z *= so0;
+              o.w *= so1;
               *reinterpret_cast<float4*>(q.y + ((((int64_t)t * nc + i) * q.Vc) + a) * 4) = o;
             }
           }
@@ -497,7 +517,7 @@ void pack_coarse_f16(const CoarseDims& cd, const float2* A, __half* A16, cudaStr
 // scratch for the B images, err: device flag (set to 2 when a bounded wait gives up).
 // Returns 0, or -2 for unsupported sizes.
 int coarse_apply_f16(const CoarseDims& cd, const __half* A16, const float* x, float* y, const double* mu, double dmu,
-                     int nsys, float* mx, __half* X16, int* err, cudaStream_t st);
+                     int nsys, float* mx, __half* X16, int* err, cudaStream_t st, const double* eps = nullptr);
 // largest dynamic shared memory a CTA of 'kernel' may use next to its static shared memory
 size_t cm_dyn_cap(const void* kernel);
 

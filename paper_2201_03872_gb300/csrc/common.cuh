@@ -86,6 +86,9 @@ struct tmamg_ctx {
   // twisted masses on the device (per system), cached
   double* mu_dev = nullptr;
   int mu_cap = 0;
+  // doublet splittings on the device (per doublet), cached
+  double* eps_dev = nullptr;
+  int eps_cap = 0;
   // scratch for tmamg_apply
   void* scratch[2] = {nullptr, nullptr};
   size_t scratch_bytes = 0;
@@ -119,16 +122,18 @@ int upload_mu(tmamg_ctx* ctx, const double* mu, int nsys);
 void launch_build_clover(const Geom& g, const double2* U64, double kappa, double c_sw, double* C64, float* C32,
                          cudaStream_t st);
 void launch_convert_gauge(const Geom& g, const double* Uin, double2* U64, float2* U32, cudaStream_t st);
+// eps (optional): the non-degenerate doublet form, per doublet splittings (device): FP32 tiles hold the
+// flavours u, d of one doublet (eps per tile), FP64 tiles 2p and 2p + 1 those of doublet p
 template <typename real>
 void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu, int nsys,
-                  cudaStream_t st);
+                  cudaStream_t st, const double* eps = nullptr);
 // r = b - D(mu) x on FP32 bundles in one pass (b with the same tiles as x)
 void launch_residual32(const Geom& g, const float2* U, const float* C, const float* x, const float* b, float* r,
-                       const double* mu, int nsys, cudaStream_t st);
+                       const double* mu, int nsys, cudaStream_t st, const double* eps = nullptr);
 // r_n = b_{n / nshift} - D(mu_n) x_n on FP64 bundles (one system per tile), b holding one tile
 // per right-hand side: the outer residual of the solver without a separate product buffer
 void launch_residual64(const Geom& g, const double2* U, const double* C, const double* x, const double* b, int nshift,
-                       double* r, const double* mu, int nsys, cudaStream_t st);
+                       double* r, const double* mu, int nsys, cudaStream_t st, const double* eps = nullptr);
 template <typename real>
 void launch_pack(const Geom& g, const real* field, real* bundle, int nsys, cudaStream_t st);
 template <typename real>

@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dirac_kernel(const typename LinkT<
                                                     const real* __restrict__ C, const real* __restrict__ x,
                                                     real* y, const double* __restrict__ mu, int nsys,
                                                     int ntile, int Lx, int Ly, int Lz, int Lt, real bc_t,
-                                                    const real* bsub, int nshift) {
+                                                    const real* bsub, int nshift,
+                                                    const double* __restrict__ eps) {
   // y is not restrict-qualified: the residual form may run in place (bsub == y), every thread
   // reading b at its own site before it writes y there; x never overlaps y
   const int64_t V = (int64_t)Lx * Ly * Lz * Lt;
@@ -291,7 +292,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dirac_kernel(const typename LinkT<
 #undef TM_PHOP
     const int n0 = tile * 2;
     const float2 m2 = make_float2(n0 < nsys ? (float)mu[n0] : 0.f, n0 + 1 < nsys ? (float)mu[n0 + 1] : 0.f);
-    local2(acc, xt + s * 4, V, C, V, s, m2);
+    // eps (doublet form): the tile's two systems are the flavours u, d of one doublet
+    local2(acc, xt + s * 4, V, C, V, s, m2, eps ? (float)eps[tile] : 0.f);
     real* yo = y + tile * tstride + s * 4;
     if constexpr (RES) {
       // residual form y = b - D x (b tile tile / nshift)
@@ -332,11 +334,15 @@ __global__ void __launch_bounds__(MAXT, MINB) dirac_kernel(const typename LinkT<
       int n = tile * T + l;
       m[l] = n < nsys ? (real)mu[n] : real(0);
     }
-    local_term<real, T>(acc, xt + s * 2 * T, V, C, V, s, m);
+    // eps (doublet form, one system per tile): tiles 2p and 2p + 1 are the flavours u, d of doublet p
+    const real* xp = eps ? x + (int64_t)(tile ^ 1) * tstride + s * 2 * T : nullptr;
+    local_term<real, T>(acc, xt + s * 2 * T, V, C, V, s, m, xp, eps ? (real)eps[tile >> 1] : real(0));
     real* yo = y + tile * tstride + s * 2 * T;
     if constexpr (RES) {
-      // residual form y = b - D x, with b stored once per right-hand side (tile / nshift)
-      const real* bo = bsub + (int64_t)(tile / nshift) * tstride + s * 2 * T;
+      // residual form y = b - D x, with b stored once per right-hand side (tile / nshift; for a
+      // doublet, once per right-hand side and flavour: tile (p / nshift) 2 + f of doublet p = tile / 2)
+      const int bt = eps ? ((tile >> 1) / nshift) * 2 + (tile & 1) : tile / nshift;
+      const real* bo = bsub + (int64_t)bt * tstride + s * 2 * T;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         CV<real, T> bv;
@@ -366,7 +372,7 @@ static inline int pick_ty(int nt, int bx, int maxthreads) {
 // warps, or 168 registers (about 100 bytes of spills) at 12 warps.
 template <typename real, bool RES, int BX, int MAXT, int MINB>
 static void launch_variant(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu,
-                           int nsys, const real* b, int nshift, cudaStream_t st) {
+                           int nsys, const real* b, int nshift, const double* eps, cudaStream_t st) {
   constexpr int T = Tile<real>::T;
   const int nt = ntiles(nsys, T);
   const int ty = pick_ty(nt, BX, MAXT);
@@ -374,24 +380,25 @@ static void launch_variant(const Geom& g, const void* U, const real* C, const re
   dim3 grid((unsigned)((g.V + BX - 1) / BX), (unsigned)(nt / ty));
   dirac_kernel<real, T, BX, RES, MAXT, MINB><<<grid, block, 0, st>>>(
       reinterpret_cast<const typename LinkT<real>::t*>(U), C, x, y, mu, nsys, nt, g.L[0], g.L[1], g.L[2], g.L[3],
-      (real)g.bc_t, b, nshift); TM_COUNT();
+      (real)g.bc_t, b, nshift, eps); TM_COUNT();
 }
 
 template <typename real, bool RES>
 static void launch_variant_k(int v, const Geom& g, const void* U, const real* C, const real* x, real* y,
-                             const double* mu, int nsys, const real* b, int nshift, cudaStream_t st) {
+                             const double* mu, int nsys, const real* b, int nshift, const double* eps,
+                             cudaStream_t st) {
   if constexpr (sizeof(real) == 4) {
     switch (v) {
-      case 1: launch_variant<real, RES, 32, 256, 2>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
-      case 2: launch_variant<real, RES, 64, 256, 2>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
-      case 3: launch_variant<real, RES, 32, 128, 4>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
-      default: launch_variant<real, RES, 32, 192, 2>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
+      case 1: launch_variant<real, RES, 32, 256, 2>(g, U, C, x, y, mu, nsys, b, nshift, eps, st); return;
+      case 2: launch_variant<real, RES, 64, 256, 2>(g, U, C, x, y, mu, nsys, b, nshift, eps, st); return;
+      case 3: launch_variant<real, RES, 32, 128, 4>(g, U, C, x, y, mu, nsys, b, nshift, eps, st); return;
+      default: launch_variant<real, RES, 32, 192, 2>(g, U, C, x, y, mu, nsys, b, nshift, eps, st); return;
     }
   } else {
     switch (v) {
-      case 1: launch_variant<real, RES, 64, 192, 2>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
-      case 2: launch_variant<real, RES, 32, 192, 2>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
-      default: launch_variant<real, RES, 64, 256, 1>(g, U, C, x, y, mu, nsys, b, nshift, st); return;
+      case 1: launch_variant<real, RES, 64, 192, 2>(g, U, C, x, y, mu, nsys, b, nshift, eps, st); return;
+      case 2: launch_variant<real, RES, 32, 192, 2>(g, U, C, x, y, mu, nsys, b, nshift, eps, st); return;
+      default: launch_variant<real, RES, 64, 256, 1>(g, U, C, x, y, mu, nsys, b, nshift, eps, st); return;
     }
   }
 }
@@ -405,46 +412,50 @@ static constexpr int n_variants() {
 // on this call's data) only when `may_tune`, i.e. when the launch is repeatable
 template <typename real, bool RES>
 static void launch_tuned(const char* family, bool may_tune, const Geom& g, const void* U, const real* C, const real* x,
-                         real* y, const double* mu, int nsys, const real* b, int nshift, cudaStream_t st) {
+                         real* y, const double* mu, int nsys, const real* b, int nshift, const double* eps,
+                         cudaStream_t st) {
   const int64_t key = g.V * 4096 + nsys;
   int v = 0;
   if (autotune_on()) {
     v = tune_lookup(family, key);
     if (v < 0)
       v = may_tune ? tune_run(family, key, n_variants<real>(),
-                              [&](int k) { launch_variant_k<real, RES>(k, g, U, C, x, y, mu, nsys, b, nshift, st); },
+                              [&](int k) {
+                                launch_variant_k<real, RES>(k, g, U, C, x, y, mu, nsys, b, nshift, eps, st);
+                              },
                               st)
                    : 0;
   }
-  launch_variant_k<real, RES>(v, g, U, C, x, y, mu, nsys, b, nshift, st);
+  launch_variant_k<real, RES>(v, g, U, C, x, y, mu, nsys, b, nshift, eps, st);
 }
 
 template <typename real>
 void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu, int nsys,
-                  cudaStream_t st) {
+                  cudaStream_t st, const double* eps) {
   TM_PROF(st, sizeof(real) == 4 ? "dirac_f32" : "dirac_f64");
   launch_tuned<real, false>(sizeof(real) == 4 ? "dirac_f32" : "dirac_f64", true, g, U, C, x, y, mu, nsys, nullptr, 1,
-                            st);
+                            eps, st);
 }
 
 void launch_residual32(const Geom& g, const float2* U, const float* C, const float* x, const float* b, float* r,
-                       const double* mu, int nsys, cudaStream_t st) {
+                       const double* mu, int nsys, cudaStream_t st, const double* eps) {
   TM_PROF(st, "residual_f32");
   // tuned only out of place (in place, b == r, the launch is not repeatable)
-  launch_tuned<float, true>("residual_f32", b != r, g, reinterpret_cast<const void*>(U), C, x, r, mu, nsys, b, 1, st);
+  launch_tuned<float, true>("residual_f32", b != r, g, reinterpret_cast<const void*>(U), C, x, r, mu, nsys, b, 1, eps,
+                            st);
 }
 
 void launch_residual64(const Geom& g, const double2* U, const double* C, const double* x, const double* b, int nshift,
-                       double* r, const double* mu, int nsys, cudaStream_t st) {
+                       double* r, const double* mu, int nsys, cudaStream_t st, const double* eps) {
   TM_PROF(st, "residual_f64");
   launch_tuned<double, true>("residual_f64", b != r, g, reinterpret_cast<const void*>(U), C, x, r, mu, nsys, b, nshift,
-                             st);
+                             eps, st);
 }
 
 template void launch_dirac<float>(const Geom&, const void*, const float*, const float*, float*, const double*, int,
-                                  cudaStream_t);
+                                  cudaStream_t, const double*);
 template void launch_dirac<double>(const Geom&, const void*, const double*, const double*, double*, const double*,
-                                   int, cudaStream_t);
+                                   int, cudaStream_t, const double*);
 
 // ---------------------------------------------------------------- pack / unpack
 // field: complex [nsys][V][12]; bundle: [ntile][12][V][2][T]

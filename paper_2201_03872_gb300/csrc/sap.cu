@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
                                                                 const float* __restrict__ C, float* __restrict__ r,
                                                                 float* __restrict__ delta, float* __restrict__ e,
                                                                 const double* __restrict__ mu, int nsys, SapDims d,
-                                                                int colour, int steps, int nitems, int ntile) {
+                                                                int colour, int steps, int nitems, int ntile,
+                                                                const double* __restrict__ eps) {
   constexpr int T = 2;  // systems per tile
   extern __shared__ float4 sm[];
   const int bv = d.bv;
@@ -216,6 +217,8 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
     sap_cp_async_wait();  // this thread's residual entries are in rho (the barrier below publishes them)
     const int n0 = tile * T;
     const float2 m2 = make_float2(n0 < nsys ? (float)mu[n0] : 0.f, n0 + 1 < nsys ? (float)mu[n0 + 1] : 0.f);
+    // doublet form (eps): the tile's two systems are the flavours of one doublet, one MR system
+    const float ep = eps ? (float)eps[tile] : 0.f;
     const float* rb = reinterpret_cast<const float*>(rho);
     for (int it = 0; it < steps; ++it) {
       __syncthreads();  // rho (and the staged links) complete
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
         TM_BHOP(2)
         TM_BHOP(3)
 #undef TM_BHOP
-        local2(q, rb + tid * 4, bv, Cs, bv, tid, m2);
+        local2(q, rb + tid * 4, bv, Cs, bv, tid, m2, ep);
         // partial <q, q> and <q, rho> per system (packed over the two systems)
         float2 qq = make_float2(0.f, 0.f), qr = qq, qi = qq;
 #pragma unroll
@@ -258,6 +261,14 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
         v[3] = qq.y; v[4] = qr.y; v[5] = qi.y;
       }
       block_reduce(v, red);  // contains the barrier: every q is computed, rho may change
+      if (eps) {  // one minimal-residual step for the doublet: the dots summed over both flavours
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const float t = v[u] + v[3 + u];
+          v[u] = t;
+          v[3 + u] = t;
+        }
+      }
       const float2 ar = make_float2(v[0] > 0.f ? v[1] / v[0] : 0.f, v[3] > 0.f ? v[4] / v[3] : 0.f);
       const float2 ai = make_float2(v[0] > 0.f ? v[2] / v[0] : 0.f, v[3] > 0.f ? v[5] / v[3] : 0.f);
       const float2 nai = make_float2(-ai.x, -ai.y);
@@ -390,7 +401,8 @@ int sap_check_blocks(const Geom& g, const int bs[4], std::string& why) {
 }
 
 void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C32, float* r, float* e, float* delta,
-               const double* mu, int nsys, int cycles, int steps, cudaStream_t st, bool accumulate) {
+               const double* mu, int nsys, int cycles, int steps, cudaStream_t st, bool accumulate,
+               const double* eps) {
   SapDims d;
   int nblocks = 1;
   for (int k = 0; k < 4; ++k) {
@@ -423,7 +435,8 @@ void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C
       if (nitems > 0) {
         const int grid = nitems < sms ? nitems : sms;
         TM_PROF(st, "sap_mr");
-        sap_mr_kernel<<<grid, nthreads, smem, st>>>(U32, C32, r, delta, e, mu, nsys, d, colour, steps, nitems, nt);
+        sap_mr_kernel<<<grid, nthreads, smem, st>>>(U32, C32, r, delta, e, mu, nsys, d, colour, steps, nitems, nt,
+                                                    eps);
         TM_COUNT();
       }
       bool last = (cy == cycles - 1) && colour == 1;

@@ -22,10 +22,6 @@
 
 namespace tmamg {
 
-template <typename real>
-void launch_dirac(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu, int nsys,
-                  cudaStream_t st);
-
 struct Workspace {
   int nsys = 0, m = 0, mc = 0;
   size_t fb32 = 0, fb64 = 0, cb32 = 0;  // bytes of one bundle
@@ -35,6 +31,8 @@ struct Workspace {
   double *x64 = nullptr, *r64 = nullptr;
   double* b64 = nullptr;  // right-hand sides, one FP64 tile each (grown on demand)
   size_t b64_bytes = 0;
+  double* epsd = nullptr;  // doublet splittings, one per doublet (grown on demand)
+  int eps_cap = 0;
   float* Vc = nullptr;  // mc + 1 coarse bundles
   float *xc = nullptr, *rc = nullptr;
   GmresState top, coarse;
@@ -67,7 +65,7 @@ static bool has_middle(const tmamg_ctx* ctx) { return ctx->levels.size() == 2; }
 
 static void ws_free(Workspace* w) {
   if (!w) return;
-  void* ptrs[] = {w->V, w->Z, w->t1, w->t2, w->t3, w->e32, w->x64, w->r64, w->b64, w->Vc, w->xc, w->rc,
+  void* ptrs[] = {w->V, w->Z, w->t1, w->t2, w->t3, w->e32, w->x64, w->r64, w->b64, w->epsd, w->Vc, w->xc, w->rc,
                   w->rel_top, w->rel_coarse, w->rn, w->bn, w->scale, w->beta0, w->tmpd, w->ones, w->mones, w->dot,
                   w->partial64, w->mask, w->mask2, w->flags, w->count, w->outer_it, w->inner_it, w->Vm, w->Zm, w->xm,
                   w->rm, w->sm1, w->sm2, w->rel_mid, w->beta0m, w->mra, w->mrd};
@@ -588,6 +586,7 @@ struct SolveCtx {
   bool launch_error = false;  // a cooperative launch was refused
   int nshift = 1;             // systems n = r * nshift + k (block GMRES groups the rhs of shift k)
   int nn = 0;                 // apply the learned step in the AMG cycle
+  const double* eps = nullptr;  // doublet solves: splitting per FP32 tile (the tile = one doublet), device
 };
 
 __global__ void restart_tol_kernel(const double2* dot, const double* beta0, double tol, double* rel, int n) {
@@ -605,7 +604,7 @@ __global__ void copy_beta_kernel(const double* b, double* dst, int n) {
 // y = D_c x on level l: FP16 operator on the tensor cores (precision 16, or 0 = default) or
 // the FP32 stencil (precision 32); false if the sizes are outside the tensor-core path
 static bool coarse_apply_level(CoarseLevel& l, int precision, const float* x, float* y, const double* mu, double dmu,
-                               int nsys, cudaStream_t st) {
+                               int nsys, cudaStream_t st, const double* eps = nullptr) {
   const CoarseDims cd = coarse_dims(l);
   if (precision != 32) {
     if (!l.A16 || nsys > CM_MAXSYS) return false;
@@ -618,9 +617,9 @@ static bool coarse_apply_level(CoarseLevel& l, int precision, const float* x, fl
       if (cudaMalloc(&l.x16, need) != cudaSuccess) return false;
       l.x16_bytes = need;
     }
-    return coarse_apply_f16(cd, l.A16, x, y, mu, dmu, nsys, l.cmax, l.x16, l.cerr, st) == 0;
+    return coarse_apply_f16(cd, l.A16, x, y, mu, dmu, nsys, l.cmax, l.x16, l.cerr, st, eps) == 0;
   }
-  coarse_apply(cd, l.A, x, y, mu, dmu, nsys, st);
+  coarse_apply(cd, l.A, x, y, mu, dmu, nsys, st, eps);
   return true;
 }
 
@@ -664,7 +663,7 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
     const int nsys = S.nsys;
     const int prec = S.sp->coarse_precision;
     auto apply = [&, dmu, mu, nsys, prec](const float* x, float* y) {
-      if (!coarse_apply_level(L1, prec, x, y, mu, dmu, nsys, st)) S.launch_error = true;
+      if (!coarse_apply_level(L1, prec, x, y, mu, dmu, nsys, st, S.eps)) S.launch_error = true;
     };
     int it = 0;
     const size_t cbytes = (size_t)ntiles(nsys, 2) * M * 4 * sizeof(float);  // the caller's bundles hold nsys systems
@@ -684,7 +683,7 @@ static void coarse_solve(SolveCtx& S, const float* rc, float* xc) {
   const double* mu = S.mu;
   const int prec = S.sp->coarse_precision;
   ops.A = [&, dmu, mu, nsys, prec](const float* x, float* y) {
-    if (!coarse_apply_level(L1, prec, x, y, mu, dmu, nsys, st)) S.launch_error = true;
+    if (!coarse_apply_level(L1, prec, x, y, mu, dmu, nsys, st, S.eps)) S.launch_error = true;
   };
   const size_t cbytes = (size_t)ntiles(nsys, 2) * M * 4 * sizeof(float);  // the caller's bundles hold nsys systems
   cudaMemsetAsync(xc, 0, cbytes, st);
@@ -738,7 +737,7 @@ static void mid_cycle(SolveCtx& S, const float* v, float* z) {
   const double dmu = S.sp->delta_mu;
   const int ns = w->nsys;
   auto apply = [&](const float* x, float* y) {
-    if (!coarse_apply_level(L1, prec, x, y, S.mu, dmu, nsys, st)) S.launch_error = true;
+    if (!coarse_apply_level(L1, prec, x, y, S.mu, dmu, nsys, st, S.eps)) S.launch_error = true;
   };
   float* rho = w->sm1;
   float* q = w->sm2;
@@ -775,7 +774,7 @@ static void mid_solve(SolveCtx& S, const float* rm, float* xm) {
   LevelOps ops;
   ops.M = M;
   ops.A = [&](const float* x, float* y) {
-    if (!coarse_apply_level(L1, prec, x, y, S.mu, dmu, nsys, st)) S.launch_error = true;
+    if (!coarse_apply_level(L1, prec, x, y, S.mu, dmu, nsys, st, S.eps)) S.launch_error = true;
   };
   ops.precond = [&](const float* v, float* z) { mid_cycle(S, v, z); };
   const size_t mbytes = (size_t)ntiles(nsys, 2) * M * 4 * sizeof(float);  // the caller's bundles hold nsys systems
@@ -817,10 +816,10 @@ static void amg_cycle(SolveCtx& S, const float* v, float* z) {
     coarse_solve(S, w->rc, w->xc);
     prolong_vec(ad, L1.P, w->xc, z, nv, 6, nsys, 0, st);
   }
-  launch_residual32(ctx->g, ctx->U32, ctx->C32, z, v, w->t1, S.mu, nsys, st);  // t1 = v - D z
+  launch_residual32(ctx->g, ctx->U32, ctx->C32, z, v, w->t1, S.mu, nsys, st, S.eps);  // t1 = v - D z
   // z += SAP(t1): the block solver adds its corrections to z directly
   sap_apply(ctx->g, ctx->sp.sap_block, ctx->U32, ctx->C32, w->t1, z, w->t3, S.mu, nsys, ctx->sp.sap_cycles,
-            ctx->sp.sap_mr_steps, st, true);
+            ctx->sp.sap_mr_steps, st, true, S.eps);
   if (S.nn && ctx->nn && ctx->nn->trained) {
     // learned step on the residual left by the smoother: z += N(v - D z)
     NNState& nns = *ctx->nn;
@@ -848,13 +847,15 @@ __global__ void expand_b_kernel(const double* __restrict__ b, double* __restrict
 }
 
 // r (FP64 bundle of nsys = nrhs * nshift systems) = the right-hand-side tiles b (one per rhs):
-// system n takes tile n / nshift; per = complex entries per tile
+// system n takes tile n / nshift; per = complex entries per tile. Doublets (pair): system
+// n = 2 (r nshift + k) + f takes the tile of rhs r, flavour f: 2 r + f
 __global__ void expand_rhs_kernel(const double2* __restrict__ b, double2* __restrict__ r, int nshift, int nsys,
-                                  int64_t per) {
+                                  int64_t per, int pair) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)nsys * per) return;
   const int n = (int)(t / per);
-  r[t] = b[(int64_t)(n / nshift) * per + t % per];
+  const int bt = pair ? ((n >> 1) / nshift) * 2 + (n & 1) : n / nshift;
+  r[t] = b[(int64_t)bt * per + t % per];
 }
 
 // norms -> masks, scales and inner tolerances; flags: 1 = non-finite
@@ -1120,12 +1121,26 @@ int do_solve64(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int 
   return all_ok ? TMAMG_OK : TMAMG_NOT_CONVERGED;
 }
 
+// eps_host (doublets): the splitting per shift; every (rhs, shift) is then a non-degenerate doublet whose
+// flavours u, d are the systems 2p, 2p + 1 (one FP32 tile), p = r nshift + k, twisted masses +mu_k, -mu_k
 int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int nshift, double* x, int on_device,
-             const tmamg_solve_params* sp, tmamg_system_stats* stats) {
+             const tmamg_solve_params* sp_in, tmamg_system_stats* stats, const double* eps_host) {
   cudaStream_t st = ctx->stream;
   const Geom& g = ctx->g;
-  const int nsys = nrhs * nshift;
+  const bool pair = eps_host != nullptr;
+  const int nsys = nrhs * nshift * (pair ? 2 : 1);
+  const int nfields = nrhs * (pair ? 2 : 1);  // right-hand-side fields
   if (nsys > 256) return set_err(ctx, TMAMG_ERR_ARG, "solve: at most 256 systems per call");
+  tmamg_solve_params spl = *sp_in;
+  if (pair) {
+    if (spl.precision != 32) return set_err(ctx, TMAMG_ERR_ARG, "solve: doublets run in the mixed-precision form");
+    if (spl.coarse_solver == 1) return set_err(ctx, TMAMG_ERR_ARG, "solve: no block GMRES for doublets");
+    if (spl.use_nn) return set_err(ctx, TMAMG_ERR_ARG, "solve: no learned step for doublets");
+    // the per-launch coarse GMRES: its reductions go through the folded dots (one system per doublet)
+    if (spl.coarse_solver == 0) spl.coarse_solver = 2;
+  }
+  const tmamg_solve_params* sp = &spl;
+  PairFold fold(pair);
   if (sp->restart < 1 || sp->restart > 64 || sp->coarse_restart < 1 || sp->coarse_restart > 128 ||
       sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1 || sp->inner_cycles < 1)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: bad parameters");
@@ -1145,26 +1160,46 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   if (sp->coarse_solver == 1 && nrhs > 16)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: block GMRES takes at most 16 right-hand sides per shift");
   int rc = ensure_ws(ctx, nsys, *sp);
-  if (!rc) rc = ensure_b64(ctx, nrhs);
+  if (!rc) rc = ensure_b64(ctx, nfields);
   if (rc) return rc;
   Workspace* w = ctx->ws;
   const int64_t V = g.V;
   const int64_t M = 12 * V;
-  // per-system twisted masses: system n = rhs (n / nshift), shift (n % nshift)
+  // per-system twisted masses: system n = rhs (n / nshift), shift (n % nshift); doublets: +mu, -mu
   std::vector<double> musys(nsys);
-  for (int n = 0; n < nsys; ++n) musys[n] = mu[n % nshift];
+  for (int n = 0; n < nsys; ++n)
+    musys[n] = pair ? ((n & 1) ? -mu[(n >> 1) % nshift] : mu[(n >> 1) % nshift]) : mu[n % nshift];
   rc = upload_mu(ctx, musys.data(), nsys);
   if (rc) return rc;
+  if (pair) {
+    const int np = nsys / 2;
+    if (np > w->eps_cap) {
+      cudaStreamSynchronize(st);
+      cudaFree(w->epsd);
+      w->epsd = nullptr;
+      w->eps_cap = 0;
+      rc = check_cuda(ctx, cudaMalloc(&w->epsd, sizeof(double) * np), "cudaMalloc(splittings)");
+      if (rc) return rc;
+      w->eps_cap = np;
+    }
+    std::vector<double> ep(np);
+    for (int q = 0; q < np; ++q) ep[q] = eps_host[q % nshift];
+    rc = check_cuda(ctx, cudaMemcpyAsync(w->epsd, ep.data(), sizeof(double) * np, cudaMemcpyHostToDevice, st),
+                    "upload splittings");
+    if (!rc) rc = check_cuda(ctx, cudaStreamSynchronize(st), "upload splittings");
+    if (rc) return rc;
+  }
   // b -> FP64 bundle with one tile per right-hand side (host input staged through x64, which
   // holds nsys >= nrhs fields and is cleared right after)
   const double* bsrc = b;
   if (!on_device) {
-    cudaMemcpyAsync(w->x64, b, sizeof(double) * 2 * M * nrhs, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(w->x64, b, sizeof(double) * 2 * M * nfields, cudaMemcpyHostToDevice, st);
     bsrc = w->x64;
   }
-  launch_pack<double>(g, bsrc, w->b64, nrhs, st);
+  launch_pack<double>(g, bsrc, w->b64, nfields, st);
   expand_rhs_kernel<<<(unsigned)(((int64_t)nsys * M + 255) / 256), 256, 0, st>>>(
-      reinterpret_cast<const double2*>(w->b64), reinterpret_cast<double2*>(w->r64), nshift, nsys, M); TM_COUNT();
+      reinterpret_cast<const double2*>(w->b64), reinterpret_cast<double2*>(w->r64), nshift, nsys, M, pair ? 1 : 0);
+  TM_COUNT();
   cudaMemsetAsync(w->x64, 0, w->fb64, st);
   cudaMemsetAsync(w->flags, 0, sizeof(int) * nsys, st);
   cudaMemsetAsync(w->outer_it, 0, sizeof(int) * nsys, st);
@@ -1173,6 +1208,7 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   sqrt_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->bn, nsys); TM_COUNT();
   SolveCtx S{ctx, sp, nsys, ctx->mu_dev, 0};
   S.nshift = nshift;
+  S.eps = pair ? w->epsd : nullptr;
   S.nn = sp->use_nn == 2 || (sp->use_nn == 1 && ctx->nn && ctx->nn->enabled);
   if (S.nn && (!ctx->nn || !ctx->nn->trained)) return set_err(ctx, TMAMG_ERR_STATE, "solve: no trained network");
   if (S.nn) {
@@ -1182,7 +1218,9 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   }
   LevelOps fine;
   fine.M = M;
-  fine.A = [&](const float* xx, float* yy) { launch_dirac<float>(g, ctx->U32, ctx->C32, xx, yy, ctx->mu_dev, nsys, st); };
+  fine.A = [&](const float* xx, float* yy) {
+    launch_dirac<float>(g, ctx->U32, ctx->C32, xx, yy, ctx->mu_dev, nsys, st, S.eps);
+  };
   fine.precond = [&](const float* v, float* z) { amg_cycle(S, v, z); };
   const size_t vstride = w->fb32 / sizeof(float);
   const double inner_min = 2e-6;
@@ -1209,13 +1247,13 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
       if (*w->h_count == 0) break;
       // restart from the FP32 residual of the inner problem: V0 = r / |r| - D e32
       f64_to_f32(w->r64, w->scale, w->V, M, nsys, st);
-      launch_residual32(g, ctx->U32, ctx->C32, w->e32, w->V, w->V, ctx->mu_dev, nsys, st);
+      launch_residual32(g, ctx->U32, ctx->C32, w->e32, w->V, w->V, ctx->mu_dev, nsys, st, S.eps);
       mdot<float>(w->V, 0, 1, w->V, M, nsys, w->dot, nsys, w->top.partial, st);
       inner_rel_kernel<<<(nsys + 127) / 128, 128, 0, st>>>(w->dot, w->tmpd, w->rel_top, nsys); TM_COUNT();
     }
     f32_axpy_f64(w->rn, w->e32, w->x64, M, nsys, w->mask, st);
     // r = b - D x in FP64 in one pass (the stencil's residual form)
-    launch_residual64(g, ctx->U64, ctx->C64, w->x64, w->b64, nshift, w->r64, ctx->mu_dev, nsys, st);
+    launch_residual64(g, ctx->U64, ctx->C64, w->x64, w->b64, nshift, w->r64, ctx->mu_dev, nsys, st, S.eps);
   }
   rc = check_cuda(ctx, cudaGetLastError(), "solve kernels");
   // final true residual per system (r64 holds b - D x for the current x)
@@ -1243,16 +1281,20 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   if (!rc && S.timeout) rc = set_err(ctx, TMAMG_ERR_TIMEOUT, "solve: a coarse-solver bounded wait timed out");
   if (rc) return rc;
   int all_ok = 1;
-  for (int n = 0; n < nsys; ++n) {
+  // doublets: one entry per doublet (both flavours carry the doublet's folded norms)
+  const int nout = pair ? nsys / 2 : nsys;
+  for (int q = 0; q < nout; ++q) {
+    const int n = pair ? 2 * q : q;
+    const int fl = pair ? (hflags[n] | hflags[n + 1]) : hflags[n];
     double rel = hbn[n] > 0 ? hrn[n] / hbn[n] : 0.0;
-    int status = hflags[n] ? TMAMG_ERR_NONFINITE : (rel <= sp->tol ? TMAMG_OK : TMAMG_NOT_CONVERGED);
+    int status = fl ? TMAMG_ERR_NONFINITE : (rel <= sp->tol ? TMAMG_OK : TMAMG_NOT_CONVERGED);
     if (status != TMAMG_OK) all_ok = 0;
     if (stats) {
-      stats[n].status = status;
-      stats[n].outer_iters = hout[n] - (capped && hmask[n] ? 1 : 0);
-      stats[n].inner_iters = hin[n];
-      stats[n].coarse_iters = S.coarse_iters;
-      stats[n].true_rel_res = hflags[n] ? NAN : rel;
+      stats[q].status = status;
+      stats[q].outer_iters = hout[n] - (capped && hmask[n] ? 1 : 0);
+      stats[q].inner_iters = hin[n];
+      stats[q].coarse_iters = S.coarse_iters;
+      stats[q].true_rel_res = fl ? NAN : rel;
     }
   }
   return all_ok ? TMAMG_OK : TMAMG_NOT_CONVERGED;
@@ -1289,7 +1331,18 @@ int tmamg_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int
   if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "solve: no multigrid setup");
   tmamg_solve_params def;
   tmamg_default_solve_params(&def);
-  return do_solve(ctx, b, nrhs, mu, nshift, x, on_device, p ? p : &def, stats);
+  return do_solve(ctx, b, nrhs, mu, nshift, x, on_device, p ? p : &def, stats, nullptr);
+}
+
+int tmamg_solve_doublet(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, const double* eps, int nshift,
+                        double* x, int on_device, const tmamg_solve_params* p, tmamg_system_stats* stats) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!b || !x || !mu || !eps || nrhs < 1 || nshift < 1)
+    return set_err(ctx, TMAMG_ERR_ARG, "solve_doublet: bad argument");
+  if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "solve_doublet: no multigrid setup");
+  tmamg_solve_params def;
+  tmamg_default_solve_params(&def);
+  return do_solve(ctx, b, nrhs, mu, nshift, x, on_device, p ? p : &def, stats, eps);
 }
 
 size_t tmamg_coarse_bundle_bytes(const tmamg_ctx* ctx, int level, int nsys) {
@@ -1676,7 +1729,7 @@ int tmamg_nn_train(tmamg_ctx* ctx, const tmamg_nn_params* p, tmamg_nn_report* re
     tmamg_solve_params gp;
     tmamg_default_solve_params(&gp);
     gp.use_nn = pass == 0 ? 0 : 2;
-    int r2 = do_solve(ctx, b64.data(), ng_sys, &gm, 1, x64.data(), 0, &gp, stats.data());
+    int r2 = do_solve(ctx, b64.data(), ng_sys, &gm, 1, x64.data(), 0, &gp, stats.data(), nullptr);
     if (r2 < 0) return r2;
     int mx = 0;
     bool conv = true;

@@ -168,9 +168,12 @@ __device__ __forceinline__ void hop(Spinor<real, T>& acc, const real* __restrict
 // acc holds the hop sum on entry. A_chi is the packed Hermitian 6x6 clover block with the
 // diagonal 1/(2 kappa) folded in (6 real diagonal entries, then the strict lower triangle).
 // xs: the site's own spinor, components strided by cstride entries; C: clover with stride V.
+// xp (optional): the doublet partner's spinor at the same site (same component stride), subtracted
+// with the splitting ep: acc <- ... - ep xp (the -eps tau1 term of the non-degenerate doublet)
 template <typename real, int T>
 __device__ __forceinline__ void local_term(Spinor<real, T>& acc, const real* __restrict__ x0, int64_t cstride,
-                                           const real* __restrict__ C, int64_t V, int64_t s, const real* mu) {
+                                           const real* __restrict__ C, int64_t V, int64_t s, const real* mu,
+                                           const real* __restrict__ xp = nullptr, real ep = real(0)) {
 #pragma unroll
   for (int chi = 0; chi < 2; ++chi) {
     const real* Cc = C + (int64_t)chi * 36 * V + s;
@@ -204,6 +207,15 @@ __device__ __forceinline__ void local_term(Spinor<real, T>& acc, const real* __r
         for (int l = 0; l < T; ++l) {
           o.re[l] += ar * xc[j].re[l] - ai * xc[j].im[l];
           o.im[l] += ar * xc[j].im[l] + ai * xc[j].re[l];
+        }
+      }
+      if (xp) {
+        CV<real, T> pv;
+        ldcv(pv, xp + (int64_t)(chi * 6 + i) * cstride * 2 * T);
+#pragma unroll
+        for (int l = 0; l < T; ++l) {
+          o.re[l] -= ep * pv.re[l];
+          o.im[l] -= ep * pv.im[l];
         }
       }
       CV<real, T>& hv = acc.c[chi * 6 + i];
@@ -381,9 +393,12 @@ __device__ __forceinline__ void mul_acc2(Spinor2& acc, const CV2 (&h)[2][3], con
 }
 
 // local_term<> for FP32 tiles of two systems in packed arithmetic: acc <- A_chi x_chi +
-// i s mu x_chi - 1/2 acc per chirality; mu: the two systems' twisted masses
+// i s mu x_chi - 1/2 acc per chirality; mu: the two systems' twisted masses. ep != 0: the tile's two
+// systems are the flavours of a non-degenerate doublet, coupled by -ep (each lane gets -ep times
+// the other lane's entry)
 __device__ __forceinline__ void local2(Spinor2& acc, const float* __restrict__ x0, int64_t cstride,
-                                       const float* __restrict__ C, int64_t V, int64_t s, float2 mu) {
+                                       const float* __restrict__ C, int64_t V, int64_t s, float2 mu,
+                                       float ep = 0.f) {
 #pragma unroll
   for (int chi = 0; chi < 2; ++chi) {
     const float* Cc = C + (int64_t)chi * 36 * V + s;
@@ -415,6 +430,10 @@ __device__ __forceinline__ void local2(Spinor2& acc, const float* __restrict__ x
         o.re = fma2(f2(-ai), xc[j].im, o.re);
         o.im = fma2(f2(ar), xc[j].im, o.im);
         o.im = fma2(f2(ai), xc[j].re, o.im);
+      }
+      if (ep != 0.f) {
+        o.re = fma2(f2(-ep), make_float2(xc[i].re.y, xc[i].re.x), o.re);
+        o.im = fma2(f2(-ep), make_float2(xc[i].im.y, xc[i].im.x), o.im);
       }
       CV2& hv = acc.c[chi * 6 + i];
       hv.re = fma2(f2(-0.5f), hv.re, o.re);

@@ -93,10 +93,12 @@ SIGNATURES = {
     "tmamg_pack": (I, [P, P, P, I, I]),
     "tmamg_unpack": (I, [P, P, P, I, I]),
     "tmamg_dirac": (I, [P, P, P, I, P, I]),
+    "tmamg_dirac_doublet": (I, [P, P, P, I, P, P, I]),
     "tmamg_apply": (I, [P, P, P, I, P, I]),
     "tmamg_setup": (I, [P, ctypes.POINTER(SetupParams), P]),
     "tmamg_setup_from_vectors": (I, [P, ctypes.POINTER(SetupParams), P]),
     "tmamg_solve": (I, [P, P, I, P, I, P, I, ctypes.POINTER(SolveParams), P]),
+    "tmamg_solve_doublet": (I, [P, P, I, P, P, I, P, I, ctypes.POINTER(SolveParams), P]),
     "tmamg_coarse_bundle_bytes": (ctypes.c_size_t, [P, I, I]),
     "tmamg_sap": (I, [P, P, P, I, P, ctypes.POINTER(ctypes.c_int), I, I]),
     "tmamg_sap_noalloc": (I, [P, P, P, I, P, ctypes.POINTER(ctypes.c_int), I, I]),
@@ -219,6 +221,14 @@ def tmamg_dirac(ctx, x_bundle, y_bundle, nsys, mu, prec):
                                                         int(prec)))
 
 
+def tmamg_dirac_doublet(ctx, x_bundle, y_bundle, npair, mu, eps, prec):
+    m = _f64(mu)
+    e = _f64(eps)
+    return _check("tmamg_dirac_doublet", ctx,
+                  lib().tmamg_dirac_doublet(ctx, _ptr(x_bundle), _ptr(y_bundle), int(npair), _ptr(m), _ptr(e),
+                                            int(prec)))
+
+
 def tmamg_apply(ctx, x_field, y_field, nsys, mu, prec):
     m = _f64(mu)
     return _check("tmamg_apply", ctx, lib().tmamg_apply(ctx, _ptr(x_field), _ptr(y_field), int(nsys), _ptr(m),
@@ -268,6 +278,18 @@ def tmamg_solve(ctx, b, nrhs, mu, nshift, x, on_device, params=None):
     rc = lib().tmamg_solve(ctx, _ptr(b), int(nrhs), _ptr(m), int(nshift), _ptr(x), int(on_device), pp,
                            ctypes.cast(stats, P))
     _check("tmamg_solve", ctx, rc)
+    return rc, list(stats)
+
+
+def tmamg_solve_doublet(ctx, b, nrhs, mu, eps, nshift, x, on_device, params=None):
+    """Returns (status, stats), one SystemStats per doublet (rhs, shift); raises on a negative status."""
+    m = _f64(mu)
+    e = _f64(eps)
+    stats = (SystemStats * (nrhs * nshift))()
+    pp = ctypes.byref(params) if params is not None else None
+    rc = lib().tmamg_solve_doublet(ctx, _ptr(b), int(nrhs), _ptr(m), _ptr(e), int(nshift), _ptr(x), int(on_device),
+                                   pp, ctypes.cast(stats, P))
+    _check("tmamg_solve_doublet", ctx, rc)
     return rc, list(stats)
 
 

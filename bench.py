@@ -39,11 +39,11 @@ WORKLOADS = {
         name="largest single-GPU: 40^3x80, eps 0.2, 4 Gaussian rhs x 4 twisted masses {0.0015,0.005,0.015,0.05}, "
              "3-level AMG",
         L=(40, 40, 40, 80), eps=0.2, c_sw=1.0, seed=1, nrhs=4, rhs="gaussian", mus=[0.0015, 0.005, 0.015, 0.05],
-        setup=dict(_AMG2, levels=3, agg2=(2, 2, 2, 2), nv2=32, setup_gmres_steps=20),
+        setup=dict(_AMG2, levels=3, agg2=(2, 2, 2, 2), nv2=32, setup_gmres_steps=20, sap_mr_steps=6),
         solve=dict(tol=1e-10, restart=5, inner_cycles=4, max_outer=60, coarse_tol=0.1, coarse_restart=40,
                    coarse_maxiter=400, mid_tol=7e-2, mid_restart=10, mid_maxiter=50, mid_smooth=3),
         amg="3-level: 4^4 aggregates Nv=24 (10^3x20 x 48), then 2^4 aggregates Nv=32 (5^3x10 x 64); 20 setup "
-            "iterations; SAP 4^4 blocks x 2 cycles x 3 MR; FGMRES(5) + FP64 refinement; middle FGMRES(10) to 7e-2 "
+            "iterations; SAP 4^4 blocks x 2 cycles x 6 MR; FGMRES(5) + FP64 refinement; middle FGMRES(10) to 7e-2 "
             "with 3 MR smoothing steps; bottom persistent GMRES(40) to 0.1; up to 4 FP32 FGMRES(5) cycles per FP64 "
             "residual"),
     "batched": dict(
@@ -58,9 +58,9 @@ WORKLOADS = {
     "precision": dict(
         name="precision-form 16^3x32, 12 point sources, mu=0.003",
         L=(16, 16, 16, 32), eps=0.25, c_sw=1.0, seed=1, nrhs=12, rhs="point", mus=[0.003],
-        setup=dict(_AMG2),
+        setup=dict(_AMG2, sap_mr_steps=6),
         solve=dict(tol=1e-10, restart=20, max_outer=40, coarse_tol=0.1, coarse_restart=40, coarse_maxiter=400),
-        amg="2-level: 4^4 aggregates Nv=24 (4^3x8 x 48); 20 setup iterations; SAP 4^4 x 2 x 3 MR; FGMRES(20) + "
+        amg="2-level: 4^4 aggregates Nv=24 (4^3x8 x 48); 20 setup iterations; SAP 4^4 x 2 x 6 MR; FGMRES(20) + "
             "FP64 refinement; persistent coarse GMRES(40) to 0.1"),
 }
 HEADLINE = "largest"
@@ -294,13 +294,17 @@ def run_dirac(args, world, rank, local):
 
 
 def run_sap(args, world, rank, local):
-    """The SAP smoother alone on the precision-form lattice and systems (diagnostic mode: one colour
-    sweep pair per cycle, 4^4 blocks, 2 cycles, 3 MR steps), for profiling the block solver."""
+    """The SAP smoother alone on the precision-form lattice with the largest workload's system count
+    and SAP settings (diagnostic mode: one colour sweep pair per cycle), for profiling the block
+    solver: per block and system tile it does the work of one SAP of that workload, so its DRAM
+    traffic scales to it by the lattice volume."""
     import torch
     from paper_2201_03872_gb300 import tmamg as T
     wl = WORKLOADS["precision"]
     L = wl["L"]
-    nsys = wl["nrhs"]
+    big = WORKLOADS[HEADLINE]
+    nsys = big["nrhs"] * len(big["mus"])
+    cyc, mr = big["setup"]["sap_cycles"], big["setup"]["sap_mr_steps"]
     kappa, _ = kappa_for(L, wl["eps"], wl["seed"])
     stream = torch.cuda.current_stream()
     ctx = T.tmamg_create(L, -1, stream.cuda_stream)
@@ -314,18 +318,18 @@ def run_sap(args, world, rank, local):
     blk = wl["setup"]["sap_block"]
     for _ in range(args.warmup):
         r.copy_(r0)
-        T.tmamg_sap(ctx, r, e, nsys, mu, blk, 2, 3)
+        T.tmamg_sap(ctx, r, e, nsys, mu, blk, cyc, mr)
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(args.steps):
         r.copy_(r0)
-        T.tmamg_sap(ctx, r, e, nsys, mu, blk, 2, 3)
+        T.tmamg_sap(ctx, r, e, nsys, mu, blk, cyc, mr)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t) * 1e3 / args.steps
     T.tmamg_destroy(ctx)
     return {"metric": "SAP smoother applications/s (diagnostic)", "value": 1e3 / ms, "unit": "applications/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "data": "synthetic", "config": {"workload": "SAP 4^4 blocks x 2 cycles x 3 MR on 16^3x32, 12 systems"}}
+            "data": "synthetic", "config": {"workload": f"SAP 4^4 blocks x {cyc} cycles x {mr} MR on 16^3x32, {nsys} systems"}}
 
 
 def measure_dirac(T, ctx, nsys, mu, steps, stream):
@@ -683,7 +687,8 @@ def cores_used(fn):
 def oracle_amg_iteration(wl, Ls):
     """Closure timing one fine-level AMG iteration of the FP64 numpy oracle for one system on lattice Ls
     with the workload's gauge recipe: the FGMRES operator application, restriction and prolongation with a
-    random P (Nv = 24, 4^4 aggregates), the residual and the SAP smoother (4^4 blocks, 2 cycles, 3 MR)."""
+    random P (Nv = 24, 4^4 aggregates), the residual and the SAP smoother with the workload's settings
+    (4^4 blocks, its cycles and MR steps)."""
     from oracle import dirac, sap as osap, amg
     kappa, _ = kappa_for(wl["L"], wl["eps"], wl["seed"])
     U = synth.gauge_field(Ls, wl["eps"], seed=wl["seed"])
@@ -699,7 +704,8 @@ def oracle_amg_iteration(wl, Ls):
         rc = P.restrict(amg.FineLevel.to_chi(y))
         e = amg.FineLevel.to_spin(P.prolong(rc))
         r2 = y - op.apply(e, mu)
-        return e + osap.sap(op, r2, mu, (4, 4, 4, 4), cycles=2, mr_steps=3, bop=bop)
+        return e + osap.sap(op, r2, mu, (4, 4, 4, 4), cycles=wl["setup"]["sap_cycles"],
+                            mr_steps=wl["setup"]["sap_mr_steps"], bop=bop)
 
     return it, op, x, mu
 
@@ -792,7 +798,7 @@ def cpu_dirac_baseline(steps=0, warmup=0):
 
 # FGMRES iterations per solve of the GPU solver on each workload (the CPU extrapolation of the
 # reference arm uses them when it runs without a GPU measurement beside it)
-ITERS_PER_SOLVE = {"largest": 30, "batched": 25, "precision": 21}
+ITERS_PER_SOLVE = {"largest": 16, "batched": 25, "precision": 15}
 
 
 def main():

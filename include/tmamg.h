@@ -79,7 +79,8 @@ typedef struct {
   int coarse_maxiter;  /* coarse iterations per cycle, upper bound */
   int coarse_solver;   /* 0: persistent GMRES (one cooperative launch per coarse solve, all systems);
                           1: block GMRES over the rhs of each shift; 2: GMRES with one launch per step */
-  double delta_mu;     /* coarse twisted-mass factor (paper Fig. 6 caption), 1 = none */
+  double delta_mu;     /* twisted-mass factor of the bottom level's operator, D_c + i delta_mu mu gamma5_c
+                          (paper Fig. 6 caption); the finer levels keep mu. 1 = none */
   int precision;       /* 32: the batched mixed-precision solver (FP32 inner FGMRES and AMG cycle, FP16 coarse
                           operands, FP64 refinement); 64: the plain comparator, FGMRES(restart) with the same
                           two-level AMG cycle where every vector, operator and reduction is FP64 (coarse GMRES
@@ -327,6 +328,11 @@ int tmamg_coarse_solve(tmamg_ctx* ctx, int level, const void* rc_bundle, void* x
  * call of each shape therefore synchronises its stream once. on = 0 uses the default variant
  * everywhere. Every call clears the recorded choices. Always returns TMAMG_OK. */
 int tmamg_autotune(int on);
+
+/* Holds every tuned kernel family to launch variant `variant` (a family with fewer variants uses
+ * its default, variant 0), bypassing the tuner; variant < 0 returns to tuning. For checking that
+ * the variants agree and for timing one variant. Always returns TMAMG_OK. */
+int tmamg_autotune_force(int variant);
 
 /* Writes the choices as NUL-terminated JSON text {"family/devD/key": {"choice": v, "ms": [per
  * variant]}, ...} (key = volume * 4096 + systems). Returns the text length, or TMAMG_ERR_ARG if buf

@@ -15,6 +15,7 @@ namespace tmamg {
 
 namespace {
 std::atomic<bool> g_on{true};
+std::atomic<int> g_force{-1};
 std::mutex g_mu;
 struct Entry {
   int choice = -1;
@@ -30,6 +31,8 @@ int device() {
 }  // namespace
 
 bool autotune_on() { return g_on.load(std::memory_order_relaxed); }
+
+int tune_forced() { return g_force.load(std::memory_order_relaxed); }
 
 int tune_lookup(const char* family, int64_t key) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -70,6 +73,11 @@ int tune_run(const char* family, int64_t key, int nvar, const std::function<void
 using namespace tmamg;
 
 extern "C" {
+
+int tmamg_autotune_force(int variant) {
+  g_force.store(variant < 0 ? -1 : variant);
+  return TMAMG_OK;
+}
 
 int tmamg_autotune(int on) {
   std::lock_guard<std::mutex> lk(g_mu);

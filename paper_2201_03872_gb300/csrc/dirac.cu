@@ -416,7 +416,9 @@ static void launch_tuned(const char* family, bool may_tune, const Geom& g, const
                          cudaStream_t st) {
   const int64_t key = g.V * 4096 + nsys;
   int v = 0;
-  if (autotune_on()) {
+  if (tune_forced() >= 0) {
+    v = tune_forced() < n_variants<real>() ? tune_forced() : 0;
+  } else if (autotune_on()) {
     v = tune_lookup(family, key);
     if (v < 0)
       v = may_tune ? tune_run(family, key, n_variants<real>(),

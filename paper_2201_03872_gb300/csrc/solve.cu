@@ -734,7 +734,7 @@ static void mid_cycle(SolveCtx& S, const float* v, float* z) {
   const int steps = S.sp->mid_smooth;
   if (steps < 1) return;
   const int prec = S.sp->coarse_precision;
-  const double dmu = S.sp->delta_mu;
+  const double dmu = 1.0;  // the twisted-mass factor delta_mu belongs to the bottom level only
   const int ns = w->nsys;
   auto apply = [&](const float* x, float* y) {
     if (!coarse_apply_level(L1, prec, x, y, S.mu, dmu, nsys, st, S.eps)) S.launch_error = true;
@@ -770,7 +770,7 @@ static void mid_solve(SolveCtx& S, const float* rm, float* xm) {
   }
   const size_t vstride = w->mb32 / sizeof(float);
   const int prec = S.sp->coarse_precision;
-  const double dmu = S.sp->delta_mu;
+  const double dmu = 1.0;  // the twisted-mass factor delta_mu belongs to the bottom level only
   LevelOps ops;
   ops.M = M;
   ops.A = [&](const float* x, float* y) {

@@ -116,6 +116,7 @@ SIGNATURES = {
     "tmamg_debug_bounded_wait": (I, [ctypes.c_longlong, I]),
     "tmamg_profile_enable": (I, [I]),
     "tmamg_autotune": (I, [I]),
+    "tmamg_autotune_force": (I, [I]),
     "tmamg_autotune_report": (I, [ctypes.c_char_p, ctypes.c_size_t]),
     "tmamg_profile_report": (I, [ctypes.c_char_p, ctypes.c_size_t]),
 }
@@ -342,6 +343,10 @@ def tmamg_coarse_solve(ctx, level, rc_bundle, xc_bundle, nrhs, mu, nshift, param
 def tmamg_autotune(on):
     """Launch-shape autotuning on (default) or off (process-wide); clears the recorded choices."""
     return lib().tmamg_autotune(int(bool(on)))
+
+
+def tmamg_autotune_force(variant):
+    return lib().tmamg_autotune_force(int(variant))
 
 
 def tmamg_autotune_report():

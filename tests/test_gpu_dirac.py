@@ -98,31 +98,44 @@ def test_dirac_precision_form_lattice_full_compare():
 
 
 def test_autotuned_stencil_variants_agree_bitwise():
-    # the launch variants differ only in CTA shape and register budget: the tuned launch and the
-    # default one give the same bits, and the tuner records a time for every variant
+    # the launch variants differ only in CTA shape and register budget: every variant
+    # (forced one by one) gives the same bits in FP32 and FP64, and the tuner records a time for
+    # every FP32 variant
     torch = torch_cuda()
     L = (8, 8, 8, 16)
     U = synth.gauge_field(L, 0.3, seed=12)
     T, ctx = _ctx(L, U, 0.124, 1.0)
     try:
         nsys = 6
-        x = synth.gaussian_spinors(L, nsys, seed=13).astype(np.complex64)
+        x = synth.gaussian_spinors(L, nsys, seed=13)
         mu = np.linspace(0.0, 0.1, nsys)
-        nb = T.tmamg_bundle_bytes(ctx, nsys, 32)
-        xb = torch.empty(nb // 4, dtype=torch.float32, device="cuda")
-        T.tmamg_pack(ctx, to_dev(x), xb, nsys, 32)
-        out = []
-        for on in (0, 1):
-            T.tmamg_autotune(on)
-            yb = torch.zeros_like(xb)
-            T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32)
-            torch.cuda.synchronize()
-            out.append(yb.cpu().numpy())
-        assert np.array_equal(out[0], out[1])
+        for prec, nvar in ((32, 4), (64, 3)):
+            cdt = np.complex64 if prec == 32 else np.complex128
+            rdt = torch.float32 if prec == 32 else torch.float64
+            nb = T.tmamg_bundle_bytes(ctx, nsys, prec) // (4 if prec == 32 else 8)
+            xb = torch.empty(nb, dtype=rdt, device="cuda")
+            T.tmamg_pack(ctx, to_dev(x.astype(cdt)), xb, nsys, prec)
+            out = []
+            for v in range(nvar):
+                T.tmamg_autotune_force(v)
+                yb = torch.zeros_like(xb)
+                T.tmamg_dirac(ctx, xb, yb, nsys, mu, prec)
+                torch.cuda.synchronize()
+                out.append(yb.cpu().numpy())
+            T.tmamg_autotune_force(-1)
+            for v in range(1, nvar):
+                assert np.array_equal(out[0], out[v]), (prec, v)
+        T.tmamg_autotune(1)
+        nb = T.tmamg_bundle_bytes(ctx, nsys, 32) // 4
+        xb = torch.empty(nb, dtype=torch.float32, device="cuda")
+        T.tmamg_pack(ctx, to_dev(x.astype(np.complex64)), xb, nsys, 32)
+        T.tmamg_dirac(ctx, xb, torch.zeros_like(xb), nsys, mu, 32)
+        torch.cuda.synchronize()
         rep = T.tmamg_autotune_report()
         ent = [v for k, v in rep.items() if k.startswith("dirac_f32/")]
         assert len(ent) == 1 and len(ent[0]["ms"]) == 4 and 0 <= ent[0]["choice"] < 4
         assert all(t > 0 for t in ent[0]["ms"])
     finally:
+        T.tmamg_autotune_force(-1)
         T.tmamg_autotune(1)
         T.tmamg_destroy(ctx)

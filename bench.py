@@ -64,7 +64,8 @@ WORKLOADS = {
             "FP64 refinement; persistent coarse GMRES(40) to 0.1"),
 }
 HEADLINE = "largest"
-DIRAC_WORKLOAD = "fine twisted-mass Wilson-clover stencil, 16^3x32, 12 systems (FP32 bundle)"
+def dirac_workload(L, nsys):
+    return "fine twisted-mass Wilson-clover stencil, %dx%dx%dx%d, %d systems (FP32 bundle)" % (tuple(L) + (nsys,))
 
 
 def rhs_for(wl, rank=0):
@@ -94,21 +95,26 @@ def dirac_bytes_per_site(nsys, prec):
     return (4 * 18 + 72) * es + nsys * 2 * 24 * es
 
 
-# DRAM bytes (read + write) of one fine-stencil launch at 16^3x32 x 12 systems, from an ncu
-# capture of that kernel; valid only for the kernel sources it was taken on (SHA-1 of dirac.cu
-# and stencil.cuh), else reported as null
-DIRAC_TRAFFIC = {"bytes": 237310464 + 121262080,
-                 "sha1": {"dirac.cu": "871752da5cf290ad9f1436f55402167b7898c48a",
-                          "stencil.cuh": "05b2e5366b623651c2f5dfec54e20b5ae49291c7"}}
+# DRAM bytes (read + write) of one launch of a kernel, from an ncu capture on a lattice whose
+# working set is far larger than the L2 (24^3x48, 16 systems; the commands are in profiles/).
+# The bytes of one launch grow with the lattice volume at a fixed system count, so a launch of
+# the same kernel on another volume is reported as the captured bytes times the volume ratio.
+# Valid only for the kernel sources the capture was taken on (SHA-1 of the files), else null.
+KERNEL_TRAFFIC = {}
 
 
-def dirac_traffic():
+def kernel_traffic(kernel, L, nsys):
+    """Captured DRAM bytes of one launch of `kernel` scaled to lattice L, or None (no capture for
+    this system count, or the kernel's sources changed since the capture)."""
     import hashlib
-    for name, want in DIRAC_TRAFFIC["sha1"].items():
+    e = KERNEL_TRAFFIC.get(kernel)
+    if e is None or e["nsys"] != nsys:
+        return None
+    for name, want in e["sha1"].items():
         path = os.path.join(ROOT, "paper_2201_03872_gb300", "csrc", name)
         if not os.path.exists(path) or hashlib.sha1(open(path, "rb").read()).hexdigest() != want:
             return None
-    return DIRAC_TRAFFIC["bytes"]
+    return int(e["bytes"] * float(np.prod(L)) / float(np.prod(e["L"])))
 
 
 def read_peaks():
@@ -217,10 +223,10 @@ def run_dirac(args, world, rank, local):
     import torch
     from paper_2201_03872_gb300 import tmamg as T
 
-    wl = WORKLOADS["precision"]
+    wl = WORKLOADS[args.workload or "precision"]
     L = wl["L"]
     V = int(np.prod(L))
-    nsys = wl["nrhs"]
+    nsys = args.nsys or wl["nrhs"]
     kappa, ksrc = kappa_for(L, wl["eps"], wl["seed"])
     U = synth.gauge_field(L, wl["eps"], seed=wl["seed"] + rank)
     stream = torch.cuda.current_stream()
@@ -279,11 +285,11 @@ def run_dirac(args, world, rank, local):
         "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": DIRAC_WORKLOAD,
+        "config": {"workload": dirac_workload(L, nsys),
                    "kappa": kappa, "kappa_source": ksrc, "nsys": nsys,
-                   "l2": "working set 378 MB > 129 MB L2; back-to-back applications"},
+                   "l2": "working set %.0f MB > 129 MB L2; back-to-back applications" % (bytes_per_apply / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": dirac_traffic(), "peak_source": peak_src,
+                     "traffic": kernel_traffic("dirac_f32", L, nsys), "peak_source": peak_src,
                      "kernel": "dirac_kernel<float,2>", "algorithmic_bytes_per_launch": bytes_per_apply},
         "e2e": {"value": whole_job_rate(bytes_per_apply * args.steps, world, e2e_ms) / 1e9, "unit": "GB/s",
                 "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(x.nbytes)},
@@ -300,10 +306,10 @@ def run_sap(args, world, rank, local):
     traffic scales to it by the lattice volume."""
     import torch
     from paper_2201_03872_gb300 import tmamg as T
-    wl = WORKLOADS["precision"]
+    wl = WORKLOADS[args.workload or "precision"]
     L = wl["L"]
     big = WORKLOADS[HEADLINE]
-    nsys = big["nrhs"] * len(big["mus"])
+    nsys = args.nsys or big["nrhs"] * len(big["mus"])
     cyc, mr = big["setup"]["sap_cycles"], big["setup"]["sap_mr_steps"]
     kappa, _ = kappa_for(L, wl["eps"], wl["seed"])
     stream = torch.cuda.current_stream()
@@ -329,7 +335,8 @@ def run_sap(args, world, rank, local):
     T.tmamg_destroy(ctx)
     return {"metric": "SAP smoother applications/s (diagnostic)", "value": 1e3 / ms, "unit": "applications/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "data": "synthetic", "config": {"workload": f"SAP 4^4 blocks x {cyc} cycles x {mr} MR on 16^3x32, {nsys} systems"}}
+            "data": "synthetic", "config": {"workload": "SAP 4^4 blocks x %d cycles x %d MR on %dx%dx%dx%d, %d systems"
+                                                     % ((cyc, mr) + tuple(L) + (nsys,))}}
 
 
 def measure_dirac(T, ctx, nsys, mu, steps, stream):
@@ -475,6 +482,7 @@ def kernel_rooflines(pb, rec, total_ms, stats):
         if "achieved" in e:
             e["frac"] = e["achieved"] / e["peak"]
             e.setdefault("peak_source", peak_src)
+            e["traffic"] = kernel_traffic(name, pb.L, N)
         out[name] = e
     return out
 
@@ -549,7 +557,7 @@ def run_solve(args, world, rank, local):
                    "l2": "inputs larger than the 129 MB L2 (one FP32 bundle %.1f GB)" % (fb32 / 1e9)},
         "roofline": dominant_roofline(kernels),
         "dirac_op": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": dirac_traffic() if args.workload == "precision" else None, "peak_source": peak_src,
+                     "traffic": kernel_traffic("dirac_f32", pb.L, nsys), "peak_source": peak_src,
                      "kernel": "dirac_kernel<float,2> (fine stencil, %d systems, timed alone)" % nsys,
                      "algorithmic_bytes_per_launch": bytes_per_apply, "launch_ms": kern_ms},
         "kernels": {"profiled_solve_ms": prof_ms, "by_kernel": kernels},
@@ -578,7 +586,7 @@ def dominant_roofline(kernels):
     e = kernels[best]
     r = {k: e[k] for k in ("bound", "achieved", "peak", "unit", "frac", "peak_source")}
     r.update(kernel=best, share_of_solve=e["share"], launches_in_solve=e["launches"], launch_ms=e["ms_per_launch"],
-             traffic=None)
+             traffic=e.get("traffic"))
     for k in ("algorithmic_bytes_per_launch", "algorithmic_flops_per_launch"):
         if k in e:
             r[k] = e[k]
@@ -808,25 +816,31 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--what", default="solve", choices=["solve", "dirac", "sap"])
-    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help="solve: default the largest workload; dirac/sap: the lattice, default 16^3x32")
+    ap.add_argument("--nsys", type=int, default=None,
+                    help="dirac/sap diagnostic modes: systems per launch (default 12 for dirac, 16 for sap)")
     ap.add_argument("--variant-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the other workloads and forms of the method")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.what == "solve" and args.workload is None:
+        args.workload = HEADLINE
     world, rank, local = dist_init()
     if args.impl == "reference":
         if rank != 0:
             return
-        wl = WORKLOADS[args.workload]
+        wl = WORKLOADS[args.workload or "precision"]
         cb = (cpu_solve_baseline(wl, ITERS_PER_SOLVE[args.workload], wl["nrhs"] * len(wl["mus"]), steps=args.steps,
                                  warmup=args.warmup) if args.what == "solve"
               else cpu_dirac_baseline(steps=args.steps, warmup=args.warmup))
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"], "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": wl["name"] if args.what == "solve" else DIRAC_WORKLOAD},
+                "config": {"workload": wl["name"] if args.what == "solve"
+                           else dirac_workload(WORKLOADS["precision"]["L"], WORKLOADS["precision"]["nrhs"])},
                 "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -844,7 +858,7 @@ def main():
     line = run(args, world, rank, local)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1 and args.what != "sap":
-            wl = WORKLOADS[args.workload]
+            wl = WORKLOADS[args.workload or "precision"]
             line["cpu_baseline"] = (cpu_solve_baseline(wl, line["config"]["iterations"]["fgmres"],
                                                        line["config"]["systems_per_step"])
                                     if args.what == "solve" else cpu_dirac_baseline())

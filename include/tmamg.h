@@ -254,7 +254,7 @@ size_t tmamg_coarse_bundle_bytes(const tmamg_ctx* ctx, int level, int nsys);
 /* e = SAP(r) on FP32 fine bundles (paper Sec. 2, red-black Schwarz alternating procedure):
  * block extents block[4] (an even number of blocks, or one, per dimension; block volume
  * <= 256), `cycles` red+black sweeps, `mr_steps` minimal-residual steps per block solve,
- * zero start. r is overwritten (partially updated residual). mu: host [nsys]. */
+ * zero start. r is overwritten (partially updated residual). mu: host [nsys], nsys <= 256. */
 int tmamg_sap(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const double* mu, const int block[4],
               int cycles, int mr_steps);
 

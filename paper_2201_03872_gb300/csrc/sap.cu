@@ -52,6 +52,8 @@ template <int N>
 __device__ __forceinline__ void block_reduce(float (&v)[N], float* red) {
   // sums v[0..N) over the CTA; every thread gets the totals (N <= 8); blockDim.x is a
   // multiple of 32, so every warp is full. Fixed-size and fully unrolled, so v stays in registers.
+  // One barrier: the caller alternates between two scratch buffers `red`, so a buffer is written
+  // again only after a later barrier that every reader of its previous contents has passed.
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -72,7 +74,6 @@ __device__ __forceinline__ void block_reduce(float (&v)[N], float* red) {
     for (int w = 0; w < nw; ++w) s += red[w * 8 + i];
     v[i] = s;
   }
-  __syncthreads();
 }
 
 __device__ __forceinline__ void sap_cp_async16(void* smem, const void* gmem) {
@@ -93,8 +94,9 @@ __device__ __forceinline__ void sap_cp_async_wait() {
 // part in the reductions and barriers).
 //
 // shared memory: links [4 nu][9][bv] float2, clover [72][bv] float, rho [12][bv] float4,
-// reduction scratch [nwarps][8] float
+// reduction scratch [2][nwarps][8] float
 constexpr int SAP_THREADS = 256;
+constexpr int SAP_MAX_TILES = 128;  // system tiles per call (256 systems)
 
 __device__ __forceinline__ int colour_block(const SapDims& d, int colour, int k) {
   if (d.pdim < 0) return k;  // one block covers the lattice (colour 0 only)
@@ -141,6 +143,15 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
   const bool act = tid < bv;
   const int64_t V = (int64_t)d.L[0] * d.L[1] * d.L[2] * d.L[3];
   const int64_t tstride = (int64_t)12 * V * 2 * T;
+  // every tile's twisted masses (and doublet splitting) in shared memory once per CTA
+  __shared__ float2 mu_s[SAP_MAX_TILES];
+  __shared__ float ep_s[SAP_MAX_TILES];
+  for (int t = tid; t < ntile; t += blockDim.x) {
+    const int n0 = t * T;
+    mu_s[t] = make_float2(n0 < nsys ? (float)mu[n0] : 0.f, n0 + 1 < nsys ? (float)mu[n0 + 1] : 0.f);
+    ep_s[t] = eps ? (float)eps[t] : 0.f;
+  }
+  const int nwarps = (int)((blockDim.x + 31) >> 5);
   const int per = (nitems + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * per;
   const int i1 = i0 + per < nitems ? i0 + per : nitems;
@@ -215,10 +226,9 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
       eb[k2].im = make_float2(0.f, 0.f);
     }
     sap_cp_async_wait();  // this thread's residual entries are in rho (the barrier below publishes them)
-    const int n0 = tile * T;
-    const float2 m2 = make_float2(n0 < nsys ? (float)mu[n0] : 0.f, n0 + 1 < nsys ? (float)mu[n0 + 1] : 0.f);
+    const float2 m2 = mu_s[tile];
     // doublet form (eps): the tile's two systems are the flavours of one doublet, one MR system
-    const float ep = eps ? (float)eps[tile] : 0.f;
+    const float ep = ep_s[tile];
     const float* rb = reinterpret_cast<const float*>(rho);
     for (int it = 0; it < steps; ++it) {
       __syncthreads();  // rho (and the staged links) complete
@@ -260,7 +270,7 @@ __global__ void __launch_bounds__(SAP_THREADS, 1) sap_mr_kernel(const float2* __
         v[0] = qq.x; v[1] = qr.x; v[2] = qi.x;
         v[3] = qq.y; v[4] = qr.y; v[5] = qi.y;
       }
-      block_reduce(v, red);  // contains the barrier: every q is computed, rho may change
+      block_reduce(v, red + (it & 1) * 8 * nwarps);  // its barrier: every q is computed, rho may change
       if (eps) {  // one minimal-residual step for the doublet: the dots summed over both flavours
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
@@ -422,18 +432,24 @@ void sap_apply(const Geom& g, const int bs[4], const float2* U32, const float* C
   if (!accumulate) cudaMemsetAsync(e, 0, M * sizeof(float), st);
   const int nthreads = (d.bv + 31) / 32 * 32;  // one thread per block site
   const int nwarps = nthreads / 32;
-  // links [4][9][bv] float2 + clover [72][bv] + rho [12][bv] float4 + reduction scratch
+  if (nt > SAP_MAX_TILES) return;  // callers check (at most 256 systems)
+  // links [4][9][bv] float2 + clover [72][bv] + rho [12][bv] float4 + reduction scratch (two buffers)
   size_t smem = sizeof(float2) * 36 * d.bv + sizeof(float) * 72 * d.bv + sizeof(float4) * 12 * d.bv +
-                sizeof(float) * 8 * nwarps;
+                sizeof(float) * 2 * 8 * nwarps;
   const int sms = device_sms();
   func_smem_optin((const void*)sap_mr_kernel, 200 * 1024);
+  // persistent grid: as many CTAs as fit on the device at once (smaller blocks fit two per SM)
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sap_mr_kernel, nthreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
   const int per_colour = d.pdim < 0 ? 1 : nblocks / 2;
   for (int cy = 0; cy < cycles; ++cy) {
     for (int colour = 0; colour < 2; ++colour) {
       const int nb_c = d.pdim < 0 ? (colour == 0 ? 1 : 0) : per_colour;
       const int nitems = nb_c * nt;
       if (nitems > 0) {
-        const int grid = nitems < sms ? nitems : sms;
+        const int grid = nitems < sms * per_sm ? nitems : sms * per_sm;
         TM_PROF(st, "sap_mr");
         sap_mr_kernel<<<grid, nthreads, smem, st>>>(U32, C32, r, delta, e, mu, nsys, d, colour, steps, nitems, nt,
                                                     eps);

@@ -1354,7 +1354,7 @@ size_t tmamg_coarse_bundle_bytes(const tmamg_ctx* ctx, int level, int nsys) {
 int tmamg_sap(tmamg_ctx* ctx, void* r_bundle, void* e_bundle, int nsys, const double* mu, const int block[4],
               int cycles, int mr_steps) {
   if (!ctx) return TMAMG_ERR_ARG;
-  if (!r_bundle || !e_bundle || !mu || !block || nsys < 1 || cycles < 1 || mr_steps < 1)
+  if (!r_bundle || !e_bundle || !mu || !block || nsys < 1 || nsys > 256 || cycles < 1 || mr_steps < 1)
     return set_err(ctx, TMAMG_ERR_ARG, "sap: bad argument");
   if (!ctx->have_op) return set_err(ctx, TMAMG_ERR_STATE, "sap: operator not set");
   std::string why;

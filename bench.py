@@ -100,7 +100,11 @@ def dirac_bytes_per_site(nsys, prec):
 # The bytes of one launch grow with the lattice volume at a fixed system count, so a launch of
 # the same kernel on another volume is reported as the captured bytes times the volume ratio.
 # Valid only for the kernel sources the capture was taken on (SHA-1 of the files), else null.
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {
+    "dirac_f32": {"bytes": 1974789888 + 1003945472, "L": (24, 24, 24, 48), "nsys": 16,
+                  "sha1": {"dirac.cu": "12f89d25e3a45b15f4f4277b40587ba3f9cd98b6",
+                           "stencil.cuh": "bbe52b7b1bde87326034de584ba1950fba6a7d1b"}},
+}
 
 
 def kernel_traffic(kernel, L, nsys):
@@ -474,6 +478,20 @@ def kernel_rooflines(pb, rec, total_ms, stats):
             # P (FP32 complex, 12 Nv per site) plus the fine vectors (FP32, 96 B per site and system)
             b = V * (12 * nv * 8 + 96 * N)
             e.update(bound="hbm", algorithmic_bytes_per_launch=b, achieved=b / per / 1e9, peak=hbm, unit="GB/s")
+        elif name == "coarse_gmres":
+            # the bottom level's operator stream per Arnoldi step: 5 stored n_c x n_c FP16 complex blocks
+            # per coarse site (self + 4 forward hops; the backward hops follow by gamma5-hermiticity),
+            # times the Arnoldi steps of one launch (the solve's bottom iterations over its launches)
+            lv = st.get("levels", 2)
+            Lc = [a // b for a, b in zip(pb.L, st["agg"])]
+            nc = 2 * nv
+            if lv == 3:
+                Lc = [a // b for a, b in zip(Lc, st["agg2"])]
+                nc = 2 * st["nv2"]
+            steps_per_launch = stats[0].coarse_iters / max(cnt, 1)
+            b = int(np.prod(Lc)) * 5 * nc * nc * 4 * steps_per_launch
+            e.update(bound="hbm", algorithmic_bytes_per_launch=b, achieved=b / per / 1e9, peak=hbm, unit="GB/s",
+                     arnoldi_steps_per_launch=steps_per_launch)
         elif name == "sap_mr":
             # one colour sweep: half the sites, `steps` block-operator applications per system
             f = DIRAC_FLOP_PER_SITE_SYSTEM * (V // 2) * N * steps
@@ -648,6 +666,40 @@ def run_variants(args, rank, stream):
                        gate_enabled=bool(rep.enabled))
 
             guarded("learned_step", learned)
+
+            def doublet():
+                # the non-degenerate doublet on the same lattice and setup: the 12 point sources as 6 flavour
+                # pairs (u, d), twisted mass mu and splitting eps = 2/3 mu, one doublet solve per pair
+                nd = pb.nrhs // 2
+                eps = [2.0 * m / 3.0 for m in pb.mus]
+                xd = torch.zeros(nd * len(pb.mus) * 2 * pb.V * 24, dtype=torch.float64, device="cuda")
+                sp = pb.params()
+
+                def solve_d():
+                    rc, st = T.tmamg_solve_doublet(pb.ctx, pb.bd, nd, pb.mus, eps, len(pb.mus), xd, 1, sp)
+                    ok = rc == 0 and all(q.status == 0 and q.true_rel_res <= pb.wl["solve"]["tol"] for q in st)
+                    return ok, st
+
+                solve_d()
+                torch.cuda.synchronize()
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ok = True
+                for _ in range(steps):
+                    okk, st_ = solve_d()
+                    ok &= okk
+                z.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(z) / steps
+                n = nd * len(pb.mus)
+                out["doublet_6_pairs"] = {"workload": pb.wl["name"] + "; as 6 non-degenerate doublets, eps = 2/3 mu",
+                                          "doublets_per_step": n, "doublet_solves_per_s": n / (ms * 1e-3),
+                                          "flavour_fields_per_s": 2 * n / (ms * 1e-3), "ms_per_step": ms,
+                                          "steps": steps, "all_converged": bool(ok),
+                                          "iterations": stats_summary(st_)}
+                del xd
+
+            guarded("doublet_6_pairs", doublet)
         finally:
             pb.close()
 

@@ -40,11 +40,11 @@ WORKLOADS = {
              "3-level AMG",
         L=(40, 40, 40, 80), eps=0.2, c_sw=1.0, seed=1, nrhs=4, rhs="gaussian", mus=[0.0015, 0.005, 0.015, 0.05],
         setup=dict(_AMG2, levels=3, agg2=(2, 2, 2, 2), nv2=32, setup_gmres_steps=20, sap_mr_steps=6, setup_iters=40),
-        solve=dict(tol=1e-10, restart=5, inner_cycles=4, max_outer=60, coarse_tol=0.1, coarse_restart=40,
+        solve=dict(tol=1e-10, restart=5, inner_cycles=4, max_outer=60, coarse_tol=0.2, coarse_restart=40,
                    coarse_maxiter=400, mid_tol=7e-2, mid_restart=10, mid_maxiter=50, mid_smooth=3),
         amg="3-level: 4^4 aggregates Nv=24 (10^3x20 x 48), then 2^4 aggregates Nv=32 (5^3x10 x 64); 40 setup "
             "iterations; SAP 4^4 blocks x 2 cycles x 6 MR; FGMRES(5) + FP64 refinement; middle FGMRES(10) to 7e-2 "
-            "with 3 MR smoothing steps; bottom persistent GMRES(40) to 0.1; up to 4 FP32 FGMRES(5) cycles per FP64 "
+            "with 3 MR smoothing steps; bottom persistent GMRES(40) to 0.2; up to 4 FP32 FGMRES(5) cycles per FP64 "
             "residual"),
     "batched": dict(
         name="batched multi-shift: 24^3x48, eps 0.25, 4 complex Z2-noise rhs x 10 twisted masses log-spaced "

@@ -789,6 +789,13 @@ __device__ __forceinline__ void cg_body(const CGArgs& p, CmShared& cs, float4* d
       p.kconv[n] = 0;
     }
     if (!grid_barrier(p)) return;
+    if (p.A16) {
+      // B images of the new V0 for the first product of the cycle (the last images were of x)
+      for (int n = threadIdx.x; n < p.nsys; n += CG_THREADS) cvs[n] = (float)ldx(p.sc + n);
+      __syncthreads();
+      cg_convert(p, p.V, cvs);
+      if (!grid_barrier(p)) return;
+    }
   }
   if (gtid == 0) *p.iters = total;
 }

@@ -89,6 +89,27 @@ def test_gmres_k_steps_match_oracle(coarse, solver, prec):
         assert relerr(x[n].ravel(), xr) < bar, (n, relerr(x[n].ravel(), xr))
 
 
+@pytest.mark.parametrize("solver,prec", [(0, 32), (2, 32), (0, 16), (2, 16)])
+def test_restarted_gmres_k_steps_match_oracle(coarse, solver, prec):
+    # k = 10 steps with restart length 4: two restarts from the true residual inside the solve (the
+    # persistent solver rebuilds its first Krylov vector, and on the tensor-core path its FP16
+    # images, at each restart)
+    lat, cl, P = coarse
+    nrhs, mus = 2, [0.01, 0.2]
+    nsys = nrhs * len(mus)
+    Vc, nc = int(np.prod(cl.L)), 2 * NV
+    rc = synth.complex_normal(106, 1, (nsys, Vc, nc))
+    k, m = 10, 4
+    x, it = _run(lat, cl, rc, nrhs, mus, solver, 1e-30, m, k, prec)
+    assert it == k
+    bar = 1e-4 if prec == 32 else 1e-3
+    for n in range(nsys):
+        mu = mus[n % len(mus)]
+        A = _operator(cl, mu, prec)
+        xr, _ = krylov.fgmres(A, rc[n].ravel(), tol=1e-30, restart=m, maxiter=k)
+        assert relerr(x[n].ravel(), xr) < bar, (n, relerr(x[n].ravel(), xr))
+
+
 @pytest.mark.parametrize("prec", [32, 16])
 def test_block_gmres_k_steps_match_oracle(coarse, prec):
     lat, cl, P = coarse

@@ -104,6 +104,9 @@ KERNEL_TRAFFIC = {
     "dirac_f32": {"bytes": 1974789888 + 1003945472, "L": (24, 24, 24, 48), "nsys": 16,
                   "sha1": {"dirac.cu": "12f89d25e3a45b15f4f4277b40587ba3f9cd98b6",
                            "stencil.cuh": "bbe52b7b1bde87326034de584ba1950fba6a7d1b"}},
+    "sap_mr": {"bytes": 3087883264 + 1500493824, "L": (24, 24, 24, 48), "nsys": 16,
+               "sha1": {"sap.cu": "f57da3cd9bff38252df3a6da1a335eaf2ab9f83a",
+                        "stencil.cuh": "bbe52b7b1bde87326034de584ba1950fba6a7d1b"}},
 }
 
 
@@ -527,9 +530,11 @@ def run_solve(args, world, rank, local):
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
+        torch.cuda.nvtx.range_push("timed")  # ncu --nvtx --nvtx-include timed/ selects the timed solves
         for k in range(args.steps):
             okk, stats = pb.solve(sp)
             ok &= okk
+        torch.cuda.nvtx.range_pop()
         t1.record(stream)
         torch.cuda.synchronize()
         clk.mark(h0, time.time())

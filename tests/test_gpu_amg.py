@@ -17,7 +17,10 @@ TOL32 = 2e-5
 
 
 @pytest.mark.parametrize("L,bs", [((8, 4, 4, 8), (4, 2, 2, 4)), ((8, 8, 8, 8), (4, 4, 4, 4)),
-                                  ((4, 4, 4, 4), (2, 2, 2, 2))])
+                                  ((4, 4, 4, 4), (2, 2, 2, 2)),
+                                  # 256-site blocks take the face-by-face update: one block along x
+                                  # (no x faces), and an 8 x 4 x 4 x 2 block (faces of 32 to 128 sites)
+                                  ((4, 8, 8, 8), (4, 4, 4, 4)), ((16, 8, 8, 8), (8, 4, 4, 2))])
 def test_sap_matches_oracle(L, bs):
     U = synth.gauge_field(L, 0.3, seed=51)
     kappa, c_sw = 0.124, 1.0

@@ -41,9 +41,11 @@ WORKLOADS = {
         L=(40, 40, 40, 80), eps=0.2, c_sw=1.0, seed=1, nrhs=4, rhs="gaussian", mus=[0.0015, 0.005, 0.015, 0.05],
         setup=dict(_AMG2, levels=3, agg2=(2, 2, 2, 2), nv2=32, setup_gmres_steps=20, sap_mr_steps=6, setup_iters=40),
         solve=dict(tol=1e-10, restart=5, inner_cycles=4, max_outer=60, coarse_tol=0.2, coarse_restart=40,
-                   coarse_maxiter=400, mid_tol=7e-2, mid_restart=10, mid_maxiter=50, mid_smooth=3),
+                   coarse_maxiter=400, mid_tol=7e-2, mid_restart=10, mid_maxiter=50, mid_smooth=3,
+                   sap_cycles=2, sap_mr_steps=4),
         amg="3-level: 4^4 aggregates Nv=24 (10^3x20 x 48), then 2^4 aggregates Nv=32 (5^3x10 x 64); 40 setup "
-            "iterations; SAP 4^4 blocks x 2 cycles x 6 MR; FGMRES(5) + FP64 refinement; middle FGMRES(10) to 7e-2 "
+            "iterations; SAP 4^4 blocks x 2 cycles x 6 MR in the setup, x 4 MR in the solve; FGMRES(5) + FP64 "
+            "refinement; middle FGMRES(10) to 7e-2 "
             "with 3 MR smoothing steps; bottom persistent GMRES(40) to 0.2; up to 4 FP32 FGMRES(5) cycles per FP64 "
             "residual"),
     "batched": dict(
@@ -465,7 +467,7 @@ def kernel_rooflines(pb, rec, total_ms, stats):
     st = pb.wl["setup"]
     nv = st["nv"]
     asz = int(np.prod(st["agg"]))
-    steps = pb.wl["setup"].get("sap_mr_steps", 3)
+    steps = pb.wl["solve"].get("sap_mr_steps") or pb.wl["setup"].get("sap_mr_steps", 3)
     out = {}
     for name, (cnt, ms) in sorted(rec.items(), key=lambda kv: -kv[1][1]):
         e = {"launches": cnt, "ms": ms, "share": ms / total_ms, "ms_per_launch": ms / max(cnt, 1)}
@@ -753,7 +755,7 @@ def oracle_amg_iteration(wl, Ls):
     """Closure timing one fine-level AMG iteration of the FP64 numpy oracle for one system on lattice Ls
     with the workload's gauge recipe: the FGMRES operator application, restriction and prolongation with a
     random P (Nv = 24, 4^4 aggregates), the residual and the SAP smoother with the workload's settings
-    (4^4 blocks, its cycles and MR steps)."""
+    (4^4 blocks, the solve's cycles and MR steps)."""
     from oracle import dirac, sap as osap, amg
     kappa, _ = kappa_for(wl["L"], wl["eps"], wl["seed"])
     U = synth.gauge_field(Ls, wl["eps"], seed=wl["seed"])
@@ -769,8 +771,9 @@ def oracle_amg_iteration(wl, Ls):
         rc = P.restrict(amg.FineLevel.to_chi(y))
         e = amg.FineLevel.to_spin(P.prolong(rc))
         r2 = y - op.apply(e, mu)
-        return e + osap.sap(op, r2, mu, (4, 4, 4, 4), cycles=wl["setup"]["sap_cycles"],
-                            mr_steps=wl["setup"]["sap_mr_steps"], bop=bop)
+        return e + osap.sap(op, r2, mu, (4, 4, 4, 4),
+                            cycles=wl["solve"].get("sap_cycles") or wl["setup"]["sap_cycles"],
+                            mr_steps=wl["solve"].get("sap_mr_steps") or wl["setup"]["sap_mr_steps"], bop=bop)
 
     return it, op, x, mu
 
@@ -863,7 +866,7 @@ def cpu_dirac_baseline(steps=0, warmup=0):
 
 # FGMRES iterations per solve of the GPU solver on each workload (the CPU extrapolation of the
 # reference arm uses them when it runs without a GPU measurement beside it)
-ITERS_PER_SOLVE = {"largest": 14, "batched": 25, "precision": 15}
+ITERS_PER_SOLVE = {"largest": 15, "batched": 25, "precision": 15}
 
 
 def main():

@@ -102,6 +102,10 @@ typedef struct {
   int inner_cycles;    /* FP32 FGMRES(restart) cycles per FP64 refinement cycle (>= 1): after each cycle the
                           systems that missed the inner goal restart from their FP32 residual, so the FP64
                           residual (the expensive product on GB300) is formed only once per inner_cycles cycles */
+  int sap_cycles;      /* SAP smoother of the solve's AMG cycle: red+black cycles and MR steps per block solve;
+                          0 takes the setup's values (tmamg_setup_params sap_cycles, sap_mr_steps), which the
+                          setup's own smoothing of the test vectors always uses */
+  int sap_mr_steps;
 } tmamg_solve_params;
 
 typedef struct {

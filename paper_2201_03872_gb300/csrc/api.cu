@@ -142,6 +142,8 @@ void tmamg_default_solve_params(tmamg_solve_params* p) {
   p->mid_maxiter = 50;
   p->mid_smooth = 3;
   p->inner_cycles = 1;
+  p->sap_cycles = 0;
+  p->sap_mr_steps = 0;
 }
 
 int tmamg_create(const int L[4], int bc_t, void* cuda_stream, tmamg_ctx** out) {

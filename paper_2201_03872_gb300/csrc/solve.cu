@@ -818,8 +818,9 @@ static void amg_cycle(SolveCtx& S, const float* v, float* z) {
   }
   launch_residual32(ctx->g, ctx->U32, ctx->C32, z, v, w->t1, S.mu, nsys, st, S.eps);  // t1 = v - D z
   // z += SAP(t1): the block solver adds its corrections to z directly
-  sap_apply(ctx->g, ctx->sp.sap_block, ctx->U32, ctx->C32, w->t1, z, w->t3, S.mu, nsys, ctx->sp.sap_cycles,
-            ctx->sp.sap_mr_steps, st, true, S.eps);
+  const int cyc = S.sp->sap_cycles > 0 ? S.sp->sap_cycles : ctx->sp.sap_cycles;
+  const int mrs = S.sp->sap_mr_steps > 0 ? S.sp->sap_mr_steps : ctx->sp.sap_mr_steps;
+  sap_apply(ctx->g, ctx->sp.sap_block, ctx->U32, ctx->C32, w->t1, z, w->t3, S.mu, nsys, cyc, mrs, st, true, S.eps);
   if (S.nn && ctx->nn && ctx->nn->trained) {
     // learned step on the residual left by the smoother: z += N(v - D z)
     NNState& nns = *ctx->nn;
@@ -1016,8 +1017,9 @@ static void amg_cycle64(tmamg_ctx* ctx, const tmamg_solve_params* sp, int nsys, 
   prolong64(ad, L1.P64, w->xc, z, L1.nv, 6, nsys, st);
   launch_dirac<double>(ctx->g, ctx->U64, ctx->C64, z, w->t1, mu, nsys, st);
   axpby<double>(w->ones, 2, v, w->mones, 2, w->t1, M, nsys, nullptr, st);  // t1 = v - D z
-  sap_apply64(ctx->g, ctx->sp.sap_block, ctx->U64, ctx->C64, w->t1, w->t2, w->t3, mu, nsys, ctx->sp.sap_cycles,
-              ctx->sp.sap_mr_steps, st);
+  sap_apply64(ctx->g, ctx->sp.sap_block, ctx->U64, ctx->C64, w->t1, w->t2, w->t3, mu, nsys,
+              sp->sap_cycles > 0 ? sp->sap_cycles : ctx->sp.sap_cycles,
+              sp->sap_mr_steps > 0 ? sp->sap_mr_steps : ctx->sp.sap_mr_steps, st);
   axpby<double>(w->ones, 2, w->t2, w->ones, 2, z, M, nsys, nullptr, st);  // z += SAP
 }
 
@@ -1142,7 +1144,8 @@ int do_solve(tmamg_ctx* ctx, const double* b, int nrhs, const double* mu, int ns
   const tmamg_solve_params* sp = &spl;
   PairFold fold(pair);
   if (sp->restart < 1 || sp->restart > 64 || sp->coarse_restart < 1 || sp->coarse_restart > 128 ||
-      sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1 || sp->inner_cycles < 1)
+      sp->coarse_maxiter < 1 || !(sp->tol > 0) || sp->max_outer < 1 || sp->inner_cycles < 1 || sp->sap_cycles < 0 ||
+      sp->sap_mr_steps < 0)
     return set_err(ctx, TMAMG_ERR_ARG, "solve: bad parameters");
   if (has_middle(ctx) &&
       (sp->mid_restart < 1 || sp->mid_restart > 64 || sp->mid_maxiter < 1 || !(sp->mid_tol > 0) || sp->mid_smooth < 0))

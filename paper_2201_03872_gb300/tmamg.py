@@ -39,7 +39,8 @@ class SolveParams(ctypes.Structure):
                 ("coarse_solver", ctypes.c_int), ("delta_mu", ctypes.c_double), ("precision", ctypes.c_int),
                 ("use_nn", ctypes.c_int), ("poll", ctypes.c_int), ("coarse_precision", ctypes.c_int),
                 ("mid_tol", ctypes.c_double), ("mid_restart", ctypes.c_int), ("mid_maxiter", ctypes.c_int),
-                ("mid_smooth", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+                ("mid_smooth", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("sap_cycles", ctypes.c_int),
+                ("sap_mr_steps", ctypes.c_int)]
 
 
 class SystemStats(ctypes.Structure):

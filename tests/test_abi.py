@@ -52,7 +52,8 @@ def _c_layout(tmp_path):
                                "mu_setup", "seed", "setup_gmres_steps"],
         "tmamg_solve_params": ["tol", "restart", "max_outer", "coarse_tol", "coarse_restart", "coarse_maxiter",
                                "coarse_solver", "delta_mu", "precision", "use_nn", "poll", "coarse_precision",
-                               "mid_tol", "mid_restart", "mid_maxiter", "mid_smooth", "inner_cycles"],
+                               "mid_tol", "mid_restart", "mid_maxiter", "mid_smooth", "inner_cycles", "sap_cycles",
+                               "sap_mr_steps"],
         "tmamg_system_stats": ["status", "outer_iters", "inner_iters", "coarse_iters", "true_rel_res"],
         "tmamg_nn_params": ["pairs", "batch", "epochs", "lr", "pair_tol", "mu", "seed", "gate_systems"],
         "tmamg_nn_report": ["loss_first", "loss_last", "iters_plain", "iters_nn", "enabled"],

@@ -272,3 +272,35 @@ def test_inner_fp32_cycles_cut_fp64_refinements():
                 assert res <= 1e-10, (ic, r, k, res)
         outer[ic] = max(s.outer_iters for s in stats)
     assert outer[4] < outer[1], outer
+
+
+def test_solve_time_sap_settings_override_the_setup():
+    # the AMG cycle's SAP takes its cycles and MR steps from the solve parameters when they are set
+    # (the setup's smoothing keeps its own): both forms reach 1e-10, the iteration counts differ, and
+    # negative values are rejected
+    L = (8, 4, 4, 8)
+    U = synth.gauge_field(L, 0.3, seed=3)
+    kappa = 0.126
+    b = synth.gaussian_spinors(L, 2, seed=4)
+    mus = [0.001, 0.05]
+    lat = Lattice(L, U, kappa, 1.0)
+    T = lat.T
+    try:
+        T.tmamg_setup(lat.ctx, T.setup_params(agg=(4, 2, 2, 4), nv=12, sap_block=(2, 2, 2, 2), setup_iters=4,
+                                              sap_mr_steps=6))
+        its = []
+        for kw in (dict(), dict(sap_cycles=1, sap_mr_steps=1)):
+            x = np.zeros((2, 2) + b.shape[1:], dtype=np.complex128)
+            rc, stats = T.tmamg_solve(lat.ctx, b, 2, mus, 2, x, 0, T.solve_params(restart=10, tol=1e-10, **kw))
+            assert rc == 0 and all(s.status == 0 for s in stats)
+            op = dirac.Operator(U, kappa, 1.0)
+            for r in range(2):
+                for k, mu in enumerate(mus):
+                    assert np.linalg.norm(b[r] - op.apply(x[r, k], mu)) / np.linalg.norm(b[r]) <= 1e-10
+            its.append(max(s.inner_iters for s in stats))
+        assert its[1] > its[0], its
+        x = np.zeros((2, 2) + b.shape[1:], dtype=np.complex128)
+        with pytest.raises(T.TmamgError):
+            T.tmamg_solve(lat.ctx, b, 2, mus, 2, x, 0, T.solve_params(sap_mr_steps=-1))
+    finally:
+        lat.close()

@@ -32,9 +32,9 @@ namespace tmamg {
 
 constexpr int CG_THREADS = 256;
 constexpr int CG_TCH = 8;    // system tiles per shared-memory chunk in the stencil phase
-constexpr int CG_IVEC = 8;   // basis vectors per register chunk in the dot phase
+constexpr int CG_IVEC = 4;   // basis vectors per register chunk in the dot phase
 constexpr int CG_MAXM = 64;  // largest restart length
-constexpr int CG_EPT = 4;    // entries per thread held in registers in the vector phases
+constexpr int CG_EPT = 8;    // entries per thread held in registers in the vector phases
 constexpr int CG_MAXNC = 64; // largest coarse site dimension 2 Nv
 constexpr int CG_AJC = 16;   // stencil columns per asynchronous chunk
 // per-warp shared memory of the stencil phase, in float4 units (vector staging + 2 chunks)

@@ -67,6 +67,14 @@ WORKLOADS = {
         amg="2-level: 4^4 aggregates Nv=24 (4^3x8 x 48); 20 setup iterations; SAP 4^4 x 2 x 6 MR in the setup, x 4 MR "
             "in the solve; FGMRES(20) + "
             "FP64 refinement; persistent coarse GMRES(40) to 0.1"),
+    "learned": dict(
+        name="learned-step form: 32^3x64, eps 0.2, 8 Gaussian rhs, mu=0.002",
+        L=(32, 32, 32, 64), eps=0.2, c_sw=1.0, seed=1, nrhs=8, rhs="gaussian", mus=[0.002],
+        setup=dict(_AMG2, sap_mr_steps=6),
+        solve=dict(tol=1e-10, restart=10, inner_cycles=2, max_outer=60, coarse_tol=0.1, coarse_restart=40,
+                   coarse_maxiter=400, sap_mr_steps=4),
+        amg="2-level: 4^4 aggregates Nv=24 (8^3x16 x 48); 20 setup iterations; SAP 4^4 x 2 x 6 MR in the setup, "
+            "x 4 MR in the solve; FGMRES(10) + FP64 refinement; persistent coarse GMRES(40) to 0.1"),
 }
 HEADLINE = "largest"
 def dirac_workload(L, nsys):
@@ -740,9 +748,33 @@ def run_variants(args, rank, stream):
         finally:
             pb.close()
 
+    def learned_c4():
+        # the learned step at its stated size: 4096 (residual, error) pairs from the plain solver on the same
+        # field, collected and trained 16 batches of 8 at a time (a full set of pairs would not fit in HBM),
+        # then the gate and the same solve with and without the step (opt-in: pair collection and training
+        # take about 17 minutes on one GB300)
+        pb = Problem(WORKLOADS["learned"], rank, stream)
+        try:
+            ms, ok, st_ = timed_solves(pb, pb.params(), steps, stream)
+            record("learned_config4_plain", pb, ms, ok, st_, setup_seconds=pb.setup_seconds)
+            t = time.time()
+            rep = T.tmamg_nn_train(pb.ctx, T.tmamg_default_nn_params(pairs=4096, batch=8, window=16, epochs=2,
+                                                                      lr=2e-3, pair_tol=1e-3, mu=pb.mus[0],
+                                                                      gate_systems=8))
+            torch.cuda.synchronize()
+            train_s = time.time() - t
+            record("learned_config4_with_step", pb, *timed_solves(pb, pb.params(use_nn=2), steps, stream),
+                   train_seconds=train_s, pairs=4096, loss_first=rep.loss_first, loss_last=rep.loss_last,
+                   gate_iterations_plain=rep.iters_plain, gate_iterations_with_step=rep.iters_nn,
+                   gate_enabled=bool(rep.enabled))
+        finally:
+            pb.close()
+
     guarded("batched_multishift_40_systems", batched)
     guarded("precision_form", precision)
     guarded("largest_plain_fp64_single_system", largest_fp64)
+    if args.learned_c4:
+        guarded("learned_config4", learned_c4)
     return out
 
 
@@ -869,7 +901,7 @@ def cpu_dirac_baseline(steps=0, warmup=0):
 
 # FGMRES iterations per solve of the GPU solver on each workload (the CPU extrapolation of the
 # reference arm uses them when it runs without a GPU measurement beside it)
-ITERS_PER_SOLVE = {"largest": 15, "batched": 21, "precision": 16}
+ITERS_PER_SOLVE = {"largest": 15, "batched": 21, "precision": 16, "learned": 16}
 
 
 def main():
@@ -887,6 +919,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the other workloads and forms of the method")
+    ap.add_argument("--learned-c4", action="store_true",
+                    help="add the learned step at 32^3x64 with 4096 training pairs to the variants (about 20 minutes)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.what == "solve" and args.workload is None:

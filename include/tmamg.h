@@ -226,10 +226,14 @@ typedef struct {
   double mu;         /* twisted mass of the training pairs and of the gate solve */
   uint64_t seed;
   int gate_systems;  /* right-hand sides of the gate solve (<= 16) */
+  int window;        /* training batches resident at once (0 = all): the pairs are collected and trained
+                        window by window, `epochs` Adam passes over each window, so the pair count is not
+                        bounded by device memory */
 } tmamg_nn_params;
 
 typedef struct {
-  double loss_first, loss_last;  /* mean loss per pair in the first and last epoch */
+  double loss_first, loss_last;  /* mean loss per pair in the first pass over the first window and in the
+                                    last pass over the last window (the first and last epoch if one window) */
   int iters_plain, iters_nn;     /* FGMRES iterations of the gate solve without / with the step */
   int enabled;                   /* 1 if the step lowered the iteration count and stays on */
 } tmamg_nn_report;

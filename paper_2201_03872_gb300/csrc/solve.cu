@@ -1652,7 +1652,7 @@ int tmamg_nn_train(tmamg_ctx* ctx, const tmamg_nn_params* p, tmamg_nn_report* re
   if (!ctx || !p) return set_err(ctx, TMAMG_ERR_ARG, "nn_train: null argument");
   if (!ctx->have_setup) return set_err(ctx, TMAMG_ERR_STATE, "nn_train: no multigrid setup");
   if (p->batch < 1 || p->batch > 16 || p->pairs < p->batch || p->epochs < 1 || !(p->lr > 0) || p->gate_systems < 1 ||
-      p->gate_systems > 16)
+      p->gate_systems > 16 || p->window < 0)
     return set_err(ctx, TMAMG_ERR_ARG, "nn_train: bad parameters");
   cudaStream_t st = ctx->stream;
   if (!ctx->nn || !ctx->nn->trained) {
@@ -1672,44 +1672,61 @@ int tmamg_nn_train(tmamg_ctx* ctx, const tmamg_nn_params* p, tmamg_nn_report* re
   std::vector<double> mus(nsys, p->mu);
   rc = upload_mu(ctx, mus.data(), nsys);
   if (rc) return rc;
-  // ---- training pairs: r = residual the plain cycle leaves, e = D^{-1} r
+  // ---- training pairs: r = residual the plain cycle leaves, e = D^{-1} r, collected and trained
+  // window by window (all batches in one window unless p->window limits it)
   const int nb = p->pairs / nsys;
+  const int win = p->window > 0 && p->window < nb ? p->window : nb;
   float *R = nullptr, *E = nullptr;
-  rc = check_cuda(ctx, cudaMalloc(&R, w->fb32 * nb), "cudaMalloc(pairs)");
-  if (!rc) rc = check_cuda(ctx, cudaMalloc(&E, w->fb32 * nb), "cudaMalloc(pairs)");
+  rc = check_cuda(ctx, cudaMalloc(&R, w->fb32 * win), "cudaMalloc(pairs)");
+  if (!rc) rc = check_cuda(ctx, cudaMalloc(&E, w->fb32 * win), "cudaMalloc(pairs)");
   if (rc) {
     cudaFree(R);
     return rc;
   }
   const int64_t M = 12 * ctx->g.V;
   SolveCtx S{ctx, &sp, nsys, ctx->mu_dev, 0};
-  for (int b = 0; b < nb; ++b) {
-    float* rb = R + (w->fb32 / sizeof(float)) * b;
-    float* eb = E + (w->fb32 / sizeof(float)) * b;
-    rc = random_bundle(ctx, p->seed * 1000003ULL + b, nsys, w->t3);  // v
-    if (rc) break;
-    cudaMemcpyAsync(w->Z, w->t3, w->fb32, cudaMemcpyDeviceToDevice, st);  // keep v
-    amg_cycle(S, w->Z, w->e32);                                            // z = M v (plain)
-    launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, w->e32, rb, S.mu, nsys, st);
-    axpby<float>(w->ones, 2, w->Z, w->mones, 2, rb, M, nsys, nullptr, st);  // r = v - D z
-    solve32(S, rb, eb, p->pair_tol, 3);
-  }
   NNGeom ng = nn_geom(ctx);
   double first = 0, last = 0;
   int step = 0;
-  for (int ep = 0; ep < p->epochs && !rc; ++ep) {
-    double tot = 0;
-    for (int b = 0; b < nb; ++b) {
-      const float* rb = R + (w->fb32 / sizeof(float)) * b;
-      const float* eb = E + (w->fb32 / sizeof(float)) * b;
-      nn_forward(nns, ng, ctx->U32, rb, w->t1, nsys, false, st);
-      if (ep == 0 || ep == p->epochs - 1) tot += nn_loss(ctx, w->t1, eb, w->t2, nsys);
-      nn_backward(nns, ng, ctx->U32, rb, w->t1, eb, nsys, w->top.partial, st);
-      nn_adam(nns, (float)p->lr, ++step, 1.0 / nsys, st);
+  int nfirst = 0, nlast = 0;
+  for (int b0 = 0; b0 < nb && !rc; b0 += win) {
+    const int nw = nb - b0 < win ? nb - b0 : win;
+    for (int k = 0; k < nw; ++k) {
+      float* rb = R + (w->fb32 / sizeof(float)) * k;
+      float* eb = E + (w->fb32 / sizeof(float)) * k;
+      rc = random_bundle(ctx, p->seed * 1000003ULL + b0 + k, nsys, w->t3);  // v
+      if (rc) break;
+      cudaMemcpyAsync(w->Z, w->t3, w->fb32, cudaMemcpyDeviceToDevice, st);  // keep v
+      amg_cycle(S, w->Z, w->e32);                                            // z = M v (plain)
+      launch_dirac<float>(ctx->g, ctx->U32, ctx->C32, w->e32, rb, S.mu, nsys, st);
+      axpby<float>(w->ones, 2, w->Z, w->mones, 2, rb, M, nsys, nullptr, st);  // r = v - D z
+      solve32(S, rb, eb, p->pair_tol, 3);
     }
-    if (ep == 0) first = tot / (nb * nsys);
-    if (ep == p->epochs - 1) last = tot / (nb * nsys);
+    for (int ep = 0; ep < p->epochs && !rc; ++ep) {
+      // the loss of the first window's first pass and of the last window's last pass
+      const bool lf = b0 == 0 && ep == 0, ll = b0 + nw >= nb && ep == p->epochs - 1;
+      for (int k = 0; k < nw; ++k) {
+        const float* rb = R + (w->fb32 / sizeof(float)) * k;
+        const float* eb = E + (w->fb32 / sizeof(float)) * k;
+        nn_forward(nns, ng, ctx->U32, rb, w->t1, nsys, false, st);
+        if (lf || ll) {
+          const double l = nn_loss(ctx, w->t1, eb, w->t2, nsys);
+          if (lf) {
+            first += l;
+            nfirst += nsys;
+          }
+          if (ll) {
+            last += l;
+            nlast += nsys;
+          }
+        }
+        nn_backward(nns, ng, ctx->U32, rb, w->t1, eb, nsys, w->top.partial, st);
+        nn_adam(nns, (float)p->lr, ++step, 1.0 / nsys, st);
+      }
+    }
   }
+  if (nfirst) first /= nfirst;
+  if (nlast) last /= nlast;
   cudaStreamSynchronize(st);
   cudaFree(R);
   cudaFree(E);

@@ -51,7 +51,7 @@ class SystemStats(ctypes.Structure):
 class NNParams(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int), ("batch", ctypes.c_int), ("epochs", ctypes.c_int), ("lr", ctypes.c_double),
                 ("pair_tol", ctypes.c_double), ("mu", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("gate_systems", ctypes.c_int)]
+                ("gate_systems", ctypes.c_int), ("window", ctypes.c_int)]
 
 
 class NNReport(ctypes.Structure):

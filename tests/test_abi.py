@@ -55,7 +55,8 @@ def _c_layout(tmp_path):
                                "mid_tol", "mid_restart", "mid_maxiter", "mid_smooth", "inner_cycles", "sap_cycles",
                                "sap_mr_steps"],
         "tmamg_system_stats": ["status", "outer_iters", "inner_iters", "coarse_iters", "true_rel_res"],
-        "tmamg_nn_params": ["pairs", "batch", "epochs", "lr", "pair_tol", "mu", "seed", "gate_systems"],
+        "tmamg_nn_params": ["pairs", "batch", "epochs", "lr", "pair_tol", "mu", "seed", "gate_systems",
+                            "window"],
         "tmamg_nn_report": ["loss_first", "loss_last", "iters_plain", "iters_nn", "enabled"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]

@@ -74,3 +74,27 @@ def test_training_lowers_loss_and_gate_is_consistent():
               f"loss {rep.loss_first:.3f} -> {rep.loss_last:.3f}, enabled {rep.enabled}")
     finally:
         lat.close()
+
+
+def test_windowed_training_matches_single_window_and_lowers_loss():
+    # pairs collected and trained window by window (4 batches resident at a time over 12 batches):
+    # the loss falls, and with one window covering every batch the windowed form is the plain one
+    U = synth.gauge_field(L, 0.3, seed=307)
+    lat = Lattice(L, U, 0.126, 1.0)
+    T = lat.T
+    try:
+        T.tmamg_setup(lat.ctx, T.setup_params(agg=(4, 2, 2, 4), nv=12, sap_block=(2, 2, 2, 2), setup_iters=4))
+        kw = dict(pairs=24, batch=2, epochs=4, lr=3e-3, mu=0.001, gate_systems=2, seed=11)
+        T.tmamg_nn_init(lat.ctx, 7)
+        rep = T.tmamg_nn_train(lat.ctx, T.tmamg_default_nn_params(window=4, **kw))
+        assert rep.loss_last < rep.loss_first, (rep.loss_first, rep.loss_last)
+        w_win = T.tmamg_nn_get_weights(lat.ctx)
+        out = []
+        for window in (0, 12):
+            T.tmamg_nn_init(lat.ctx, 7)
+            T.tmamg_nn_train(lat.ctx, T.tmamg_default_nn_params(window=window, **kw))
+            out.append(T.tmamg_nn_get_weights(lat.ctx))
+        assert np.array_equal(out[0], out[1])
+        assert not np.array_equal(out[0], w_win)
+    finally:
+        lat.close()

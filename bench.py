@@ -359,6 +359,52 @@ def run_sap(args, world, rank, local):
                                                      % ((cyc, mr) + tuple(L) + (nsys,))}}
 
 
+def run_eo(args, world, rank, local):
+    """The even-odd Schur complement operator M_ee alone (diagnostic mode): CUDA-event time per application
+    against one full stencil application on the same bundle, and the site-local solve's own launch time."""
+    import torch
+    from paper_2201_03872_gb300 import tmamg as T
+    wl = WORKLOADS[args.workload or "precision"]
+    L = wl["L"]
+    big = WORKLOADS[HEADLINE]
+    nsys = args.nsys or big["nrhs"] * len(big["mus"])
+    kappa, _ = kappa_for(L, wl["eps"], wl["seed"])
+    stream = torch.cuda.current_stream()
+    ctx = T.tmamg_create(L, -1, stream.cuda_stream)
+    T.tmamg_load_gauge(ctx, synth.gauge_field(L, wl["eps"], seed=wl["seed"] + rank))
+    T.tmamg_set_operator(ctx, kappa, wl["c_sw"])
+    nb = T.tmamg_bundle_bytes(ctx, nsys, 32)
+    xb = torch.randn(nb // 4, dtype=torch.float32, device="cuda")
+    yb = torch.empty_like(xb)
+    mu = np.full(nsys, wl["mus"][0])
+    out = {}
+    for name, fn in (("schur", lambda: T.tmamg_dirac_eo(ctx, xb, yb, nsys, mu, 32)),
+                     ("dirac", lambda: T.tmamg_dirac(ctx, xb, yb, nsys, mu, 32))):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        z.record(stream)
+        torch.cuda.synchronize()
+        out[name] = a.elapsed_time(z) / args.steps
+    T.tmamg_profile_enable(1)
+    T.tmamg_dirac_eo(ctx, xb, yb, nsys, mu, 32)
+    torch.cuda.synchronize()
+    rec = T.tmamg_profile_report()
+    T.tmamg_profile_enable(0)
+    T.tmamg_destroy(ctx)
+    ms = out["schur"]
+    return {"metric": "even-odd Schur operator applications/s (diagnostic)", "value": 1e3 / ms,
+            "unit": "applications/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "data": "synthetic", "dirac_ms": out["dirac"],
+            "eo_solve_ms": rec.get("eo_solve", [0, 0.0])[1],
+            "config": {"workload": "M_ee = A_ee - H_eo A_oo^-1 H_oe (two stencils + site solves) on %dx%dx%dx%d, "
+                                   "%d systems, FP32" % (tuple(L) + (nsys,))}}
+
+
 def measure_dirac(T, ctx, nsys, mu, steps, stream):
     """CUDA-event time of the fine FP32 stencil on a bundle of nsys systems (same stream)."""
     import torch
@@ -910,7 +956,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--what", default="solve", choices=["solve", "dirac", "sap"])
+    ap.add_argument("--what", default="solve", choices=["solve", "dirac", "sap", "eo"])
     ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
                     help="solve: default the largest workload; dirac/sap: the lattice, default 16^3x32")
     ap.add_argument("--nsys", type=int, default=None,
@@ -951,10 +997,10 @@ def main():
         torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
-    run = {"solve": run_solve, "dirac": run_dirac, "sap": run_sap}[args.what]
+    run = {"solve": run_solve, "dirac": run_dirac, "sap": run_sap, "eo": run_eo}[args.what]
     line = run(args, world, rank, local)
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1 and args.what != "sap":
+        if not args.no_cpu_baseline and world == 1 and args.what in ("solve", "dirac"):
             wl = WORKLOADS[args.workload or "precision"]
             line["cpu_baseline"] = (cpu_solve_baseline(wl, line["config"]["iterations"]["fgmres"],
                                                        line["config"]["systems_per_step"])

@@ -160,6 +160,15 @@ int tmamg_dirac(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int nsys, 
 int tmamg_dirac_doublet(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int npair, const double* mu,
                         const double* eps, int prec);
 
+/* The even-odd (Schur complement) form of D(mu) (the standard reduction of the DDalphaAMG family the
+ * paper builds on, Sec. 2): with the sites split by parity (x + y + z + t) mod 2 the hops connect
+ * opposite parities only, and y_n = M_ee(mu_n) x_n = A_ee x_e - H_eo A_oo(mu_n)^{-1} H_oe x_e on the
+ * even sites, A the site-local part (diagonal, clover, twist) and H the hops; y is zero on the odd
+ * sites and x's odd entries are ignored. The inverse of M_ee is the even block of D^{-1}. Bundles on
+ * the device as for tmamg_dirac (nsys systems, prec 32 or 64, mu host [nsys]); uses the context's two
+ * scratch bundles; x and y must not overlap. */
+int tmamg_dirac_eo(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int nsys, const double* mu, int prec);
+
 /* Convenience: y = D(mu_n) x_n on user fields (device pointers), packing through
  * internal scratch bundles. */
 int tmamg_apply(tmamg_ctx* ctx, const void* x_field, void* y_field, int nsys, const double* mu, int prec);

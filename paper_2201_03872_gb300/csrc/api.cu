@@ -319,6 +319,24 @@ int tmamg_dirac_doublet(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, in
   return check_cuda(ctx, cudaGetLastError(), "dirac_doublet launch");
 }
 
+int tmamg_dirac_eo(tmamg_ctx* ctx, const void* x_bundle, void* y_bundle, int nsys, const double* mu, int prec) {
+  if (!ctx) return TMAMG_ERR_ARG;
+  if (!x_bundle || !y_bundle || !mu || nsys <= 0 || (prec != 32 && prec != 64))
+    return set_err(ctx, TMAMG_ERR_ARG, "dirac_eo: bad argument");
+  if (x_bundle == y_bundle) return set_err(ctx, TMAMG_ERR_ARG, "dirac_eo: x and y must not overlap");
+  if (!ctx->have_op) return set_err(ctx, TMAMG_ERR_STATE, "dirac_eo: operator not set");
+  int rc = upload_mu(ctx, mu, nsys);
+  if (!rc) rc = ensure_scratch(ctx, tmamg_bundle_bytes(ctx, nsys, prec));
+  if (rc) return rc;
+  if (prec == 32)
+    launch_dirac_eo<float>(ctx->g, ctx->U32, ctx->C32, (const float*)x_bundle, (float*)y_bundle, ctx->mu_dev, nsys,
+                           (float*)ctx->scratch[0], (float*)ctx->scratch[1], ctx->stream);
+  else
+    launch_dirac_eo<double>(ctx->g, ctx->U64, ctx->C64, (const double*)x_bundle, (double*)y_bundle, ctx->mu_dev,
+                            nsys, (double*)ctx->scratch[0], (double*)ctx->scratch[1], ctx->stream);
+  return check_cuda(ctx, cudaGetLastError(), "dirac_eo launch");
+}
+
 int tmamg_apply(tmamg_ctx* ctx, const void* x_field, void* y_field, int nsys, const double* mu, int prec) {
   if (!ctx) return TMAMG_ERR_ARG;
   if (!x_field || !y_field || !mu || nsys <= 0 || (prec != 32 && prec != 64))

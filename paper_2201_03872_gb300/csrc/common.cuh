@@ -134,6 +134,11 @@ void launch_residual32(const Geom& g, const float2* U, const float* C, const flo
 // per right-hand side: the outer residual of the solver without a separate product buffer
 void launch_residual64(const Geom& g, const double2* U, const double* C, const double* x, const double* b, int nshift,
                        double* r, const double* mu, int nsys, cudaStream_t st, const double* eps = nullptr);
+// y = M_ee(mu) x on the even sites (the even-odd Schur complement), y = 0 on the odd sites; x's odd
+// entries are ignored; s0, s1: two scratch bundles of the same size
+template <typename real>
+void launch_dirac_eo(const Geom& g, const void* U, const real* C, const real* x, real* y, const double* mu, int nsys,
+                     real* s0, real* s1, cudaStream_t st);
 template <typename real>
 void launch_pack(const Geom& g, const real* field, real* bundle, int nsys, cudaStream_t st);
 template <typename real>

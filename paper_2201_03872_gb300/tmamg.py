@@ -95,6 +95,7 @@ SIGNATURES = {
     "tmamg_unpack": (I, [P, P, P, I, I]),
     "tmamg_dirac": (I, [P, P, P, I, P, I]),
     "tmamg_dirac_doublet": (I, [P, P, P, I, P, P, I]),
+    "tmamg_dirac_eo": (I, [P, P, P, I, P, I]),
     "tmamg_apply": (I, [P, P, P, I, P, I]),
     "tmamg_setup": (I, [P, ctypes.POINTER(SetupParams), P]),
     "tmamg_setup_from_vectors": (I, [P, ctypes.POINTER(SetupParams), P]),
@@ -229,6 +230,12 @@ def tmamg_dirac_doublet(ctx, x_bundle, y_bundle, npair, mu, eps, prec):
     return _check("tmamg_dirac_doublet", ctx,
                   lib().tmamg_dirac_doublet(ctx, _ptr(x_bundle), _ptr(y_bundle), int(npair), _ptr(m), _ptr(e),
                                             int(prec)))
+
+
+def tmamg_dirac_eo(ctx, x_bundle, y_bundle, nsys, mu, prec):
+    m = _f64(mu)
+    return _check("tmamg_dirac_eo", ctx, lib().tmamg_dirac_eo(ctx, _ptr(x_bundle), _ptr(y_bundle), int(nsys), _ptr(m),
+                                                              int(prec)))
 
 
 def tmamg_apply(ctx, x_field, y_field, nsys, mu, prec):
